@@ -1,0 +1,316 @@
+"""Pins of the FP64 oracle against routes that do not share its arithmetic.
+
+Each test names the passage of the paper (or the piece of mathematics) it
+checks.  Sizes are small so the whole CPU suite runs in a few minutes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense(n, seed, s_lo=0.1, s_hi=10.0):
+    A, Q, s = wl.spd_matrix(seed, seed + 1, n, s_lo, s_hi)
+    Ainv = (Q / s) @ Q.T
+    return A, Ainv
+
+
+# ---- P1: closed forms ------------------------------------------------------
+
+def test_workload1_closed_form(orc):
+    """Workload 1 (n = 8, diagonal A, H = l1, FP64, tol 1e-10): the oracle
+    agrees with phi = sum shrink_1(x_i,t)^2/(2 a_i) - 1/2 and
+    grad = shrink_1(x,t)/a (decoupled minimisation of Section 1)."""
+    d = wl.diag_l1_fp64()
+    P = orc.Problem(d["a"], orc.H_L1, tol=d["tol"], max_iter=d["max_iter"])
+    r = P.eval(d["x"], d["t"])
+    assert r["converged"].all()
+    for q in range(len(d["t"])):
+        phi, g = pins.closed_diag_wl1(d["x"][q], d["t"][q], d["a"])
+        assert abs(r["phi"][q] - phi) <= 1e-8 * max(1, abs(phi))
+        # the stop rule leaves steps |d^K - d^{K-1}| <= 1e-5; with a_i in
+        # [0.5, 2] and lambda = 1 the iteration contracts by about 1/3 per step,
+        # so the distance to the fixed point is below 5e-5
+        assert np.abs(r["grad"][q] - g).max() <= 5e-5
+        # the returned iterate is d^K: exact zeros where |x_i| <= t
+        assert np.all(r["grad"][q][np.abs(d["x"][q]) <= d["t"][q]] == 0.0)
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 2.0])
+def test_paper_example_l1_ellipsoid(orc, lam):
+    """Section 1 worked example: J = 1/2 (sum x_i^2/a_i^2 - 1), H = l1, i.e.
+    A = diag(a^2).  lambda != 1 catches a lambda dropped from one of
+    eq. 3.4(a)-(b) (the fixed point does not depend on lambda)."""
+    rng = np.random.default_rng(1)
+    n = 6
+    a = rng.uniform(0.5, 2.0, n)
+    x = rng.uniform(-4, 4, (50, n))
+    t = rng.uniform(0.1, 2.0, 50)
+    P = orc.Problem(a ** 2, orc.H_L1, lam=lam, tol=1e-26, max_iter=5000)
+    r = P.eval(x, t)
+    for q in range(50):
+        phi, g = pins.paper_example_l1(x[q], t[q], a)
+        assert abs(r["phi"][q] - phi) <= 1e-10 * max(1, abs(phi))
+        assert np.abs(r["grad"][q] - g).max() <= 1e-10
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 3.0])
+def test_weighted_l1_with_centre(orc, lam):
+    """Weighted l1 with a centre c: v_i = shrink_1(y_i, t w_i)/a_i, y = x - c."""
+    rng = np.random.default_rng(2)
+    n = 9
+    a = rng.uniform(0.3, 3.0, n)
+    w = rng.uniform(0.5, 1.5, n)
+    c = rng.normal(size=n)
+    x = rng.normal(scale=3, size=(40, n))
+    t = rng.uniform(0.05, 2.0, 40)
+    P = orc.Problem(a, orc.H_WL1, w=w, centre=c, lam=lam, tol=1e-26, max_iter=5000)
+    r = P.eval(x, t)
+    for q in range(40):
+        phi, g = pins.closed_diag_wl1(x[q] - c, t[q], a, w)
+        assert abs(r["phi"][q] - phi) <= 1e-10 * max(1, abs(phi))
+        assert np.abs(r["grad"][q] - g).max() <= 1e-10
+        assert abs(r["dphidt"][q] + (w * np.abs(g)).sum()) <= 1e-9
+
+
+def test_paper_example_sphere(orc):
+    """Section 1: the unit sphere moved outward by H = l2 (A = I, c0 = 1/2)."""
+    rng = np.random.default_rng(3)
+    n = 5
+    x = rng.normal(scale=2, size=(60, n))
+    t = rng.uniform(0.1, 4.0, 60)
+    P = orc.Problem(np.ones(n), orc.H_L2, tol=1e-26, max_iter=5000)
+    r = P.eval(x, t)
+    for q in range(60):
+        phi = pins.paper_example_sphere(x[q], t[q])
+        assert abs(r["phi"][q] - phi) <= 1e-10 * max(1, abs(phi))
+        assert np.abs(r["grad"][q] - pins.shrink2(x[q], t[q])).max() <= 1e-10
+
+
+@pytest.mark.parametrize("lam", [0.7, 1.0])
+def test_diag_l2_secular(orc, lam):
+    """Diagonal A with H = l2 (every part of the ellipsoid-union workload):
+    the secular-equation solution by bisection."""
+    rng = np.random.default_rng(4)
+    n = 16
+    a = rng.uniform(0.04, 25.0, n)
+    c = rng.normal(scale=3, size=n)
+    x = rng.normal(scale=5, size=(40, n))
+    t = rng.uniform(0.0, 2.0, 40)
+    P = orc.Problem(a, orc.H_L2, centre=c, lam=lam, tol=1e-28, max_iter=20000)
+    r = P.eval(x, t)
+    for q in range(40):
+        phi, v = pins.diag_l2_secular(x[q] - c, t[q], a)
+        assert abs(r["phi"][q] - phi) <= 1e-9 * max(1, abs(phi))
+        assert np.abs(r["grad"][q] - v).max() <= 1e-8 * max(1, np.abs(v).max())
+
+
+# ---- P3 / P4: dense A, certificates -----------------------------------------
+
+@pytest.mark.parametrize("lam", [1.0, 2.5])
+def test_dense_wl1_kkt_certificate(orc, lam):
+    """Dense SPD A, weighted l1 (the n = 1024 workload's form at n = 48): the
+    oracle's support and signs give an exact active-set solution that satisfies
+    the optimality conditions of eq. 3.3, and the oracle matches it."""
+    n = 48
+    A, Ainv = _dense(n, 7001)
+    w = wl.uniform(7003, n, 0.5, 1.5)
+    x = wl.normal(7004, 30 * n, 2.0).reshape(30, n)
+    t = wl.uniform(7005, 30, 0.1, 3.0)
+    P = orc.Problem(A, orc.H_WL1, w=w, lam=lam, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    assert r["converged"].all()
+    for q in range(30):
+        v, ok = pins.kkt_active_set(A, x[q], t[q], w, r["grad"][q])
+        assert ok, q
+        assert np.abs(r["grad"][q] - v).max() <= 1e-10 * max(1, np.abs(v).max())
+        phi = pins.objective_neg(A, x[q], t[q], w, v)
+        assert abs(r["phi"][q] - phi) <= 1e-11 * max(1, abs(phi))
+
+
+@pytest.mark.parametrize("h", ["wl1", "l2"])
+def test_dense_duality_gap(orc, h):
+    """Lower bound -F(v) <= phi <= J(x - t c) for any c in C (Hopf-Lax form of
+    Section 2.2); at the oracle's answer the gap closes to rounding level."""
+    n = 40
+    A, Ainv = _dense(n, 7101)
+    w = wl.uniform(7103, n, 0.5, 1.5) if h == "wl1" else None
+    x = wl.normal(7104, 25 * n, 2.0).reshape(25, n)
+    t = wl.uniform(7105, 25, 0.1, 3.0)
+    kind = orc.H_WL1 if h == "wl1" else orc.H_L2
+    P = orc.Problem(A, kind, w=w, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    for q in range(25):
+        v = r["grad"][q]
+        lower = pins.objective_neg(A, x[q], t[q], w, v, h=h)
+        upper = pins.hopf_lax_upper(Ainv, A, x[q], t[q], w, v, h=h)
+        assert lower <= r["phi"][q] + 1e-12 * max(1, abs(lower))
+        assert upper - lower <= 1e-9 * max(1, abs(upper)), (q, upper - lower)
+
+
+# ---- P5: brute-force Hopf-Lax at n = 2 ---------------------------------------
+
+@pytest.mark.parametrize("h", ["l1", "wl1", "l2"])
+def test_hopf_lax_bruteforce_n2(orc, h):
+    rng = np.random.default_rng(11)
+    for trial in range(12):
+        G = rng.normal(size=(2, 2))
+        A = G @ G.T + 0.3 * np.eye(2)
+        Ainv = np.linalg.inv(A)
+        w = rng.uniform(0.5, 1.5, 2) if h == "wl1" else np.ones(2)
+        x = rng.normal(scale=2, size=2)
+        t = rng.uniform(0.1, 2.0)
+        kind = {"l1": orc.H_L1, "wl1": orc.H_WL1, "l2": orc.H_L2}[h]
+        P = orc.Problem(A, kind, w=w if h == "wl1" else None, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+        r = P.eval(x[None], [t])
+        bf = pins.hopf_lax_bruteforce_2d(Ainv, x, t, w, h="l2" if h == "l2" else "wl1")
+        assert abs(r["phi"][0] - bf) <= 1e-9 * max(1, abs(bf)), (trial, r["phi"][0], bf)
+
+
+# ---- P6: invariants -------------------------------------------------------
+
+def test_initial_condition_and_shift(orc):
+    """phi(x, 0) = J(x) (eq. 1.1b) and phi(x; c) = phi(x - c; 0)."""
+    n = 20
+    A, Ainv = _dense(n, 7201)
+    c = wl.normal(7206, n, 1.0)
+    x = wl.normal(7204, 10 * n, 2.0).reshape(10, n)
+    P = orc.Problem(A, orc.H_L2, centre=c, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+    r0 = P.eval(x, np.zeros(10))
+    for q in range(10):
+        J = pins.J_value(Ainv, x[q] - c)
+        assert abs(r0["phi"][q] - J) <= 1e-11 * max(1, abs(J))
+    t = np.full(10, 0.8)
+    r1 = P.eval(x, t)
+    P0 = orc.Problem(A, orc.H_L2, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+    r2 = P0.eval(x - c, t)
+    assert np.allclose(r1["phi"], r2["phi"], rtol=1e-12, atol=1e-12)
+
+
+def test_time_derivative_and_gradient_fd(orc):
+    """d phi/dt = -H(grad phi) (the PDE, eq. 1.1a) and grad_x phi = d^K, both
+    by FP64 central differences; phi is non-increasing in t (H >= 0)."""
+    n = 12
+    A, Ainv = _dense(n, 7301)
+    w = wl.uniform(7303, n, 0.5, 1.5)
+    P = orc.Problem(A, orc.H_WL1, w=w, tol=1e-30, max_iter=50000, stop_rule=orc.STOP_UREL)
+    x = wl.normal(7304, n, 2.0)
+    t = 0.9
+    h = 1e-5
+    r = P.eval(x[None], [t])
+    rp, rm = P.eval(x[None], [t + h]), P.eval(x[None], [t - h])
+    fd_t = (rp["phi"][0] - rm["phi"][0]) / (2 * h)
+    assert abs(fd_t - r["dphidt"][0]) <= 1e-6 * max(1, abs(fd_t))
+    assert rp["phi"][0] <= r["phi"][0] <= rm["phi"][0]
+    X = np.repeat(x[None], 2 * n, 0)
+    for i in range(n):
+        X[2 * i, i] += h
+        X[2 * i + 1, i] -= h
+    rr = P.eval(X, np.full(2 * n, t))
+    fd_x = (rr["phi"][0::2] - rr["phi"][1::2]) / (2 * h)
+    assert np.abs(fd_x - r["grad"][0]).max() <= 1e-6 * max(1, np.abs(fd_x).max())
+
+
+# ---- P7: union and closest point --------------------------------------------
+
+def _union_parts(orc, K, n, seed, tol=1e-28):
+    semi = wl.log_uniform(seed, K * n, 0.2, 5.0).reshape(K, n)
+    cen = wl.normal(seed + 4, K * n, 3.0).reshape(K, n)
+    parts = [orc.Problem(semi[k] ** 2, orc.H_L2, centre=cen[k], tol=tol, max_iter=50000,
+                         stop_rule=orc.STOP_UREL) for k in range(K)]
+    return semi, cen, parts
+
+
+def test_union_min_rule(orc):
+    """phi = min_i phi_i (Section 2.2) with each phi_i from the secular
+    equation; at t = 0 it is min_i J_i(x)."""
+    K, n = 4, 10
+    semi, cen, parts = _union_parts(orc, K, n, 7401)
+    x = wl.normal(7404, 20 * n, 5.0).reshape(20, n)
+    t = wl.uniform(7405, 20, 0.0, 2.0)
+    t[:3] = 0.0
+    r = orc.union_eval(parts, x, t)
+    for q in range(20):
+        vals = [pins.diag_l2_secular(x[q] - cen[k], t[q], semi[k] ** 2)[0] for k in range(K)]
+        k = int(np.argmin(vals))
+        assert r["argmin"][q] == k
+        assert abs(r["phi"][q] - vals[k]) <= 1e-9 * max(1, abs(vals[k]))
+        if t[q] == 0:
+            J = min(0.5 * (((x[q] - cen[j]) / semi[j]) ** 2).sum() - 0.5 for j in range(K))
+            assert abs(r["phi"][q] - J) <= 1e-11 * max(1, abs(J))
+
+
+def test_closest_point_against_ellipsoid_projection(orc):
+    """Distance and closest point by Newton on s over the eikonal solution
+    (Section 3.2) agree with the ellipsoid projection of Section 4.3."""
+    K, n = 3, 8
+    semi, cen, parts = _union_parts(orc, K, n, 7501, tol=1e-28)
+    x = wl.normal(7504, 40 * n, 5.0).reshape(40, n)
+    inside = np.zeros(40, bool)
+    for k in range(K):
+        inside |= (((x - cen[k]) / semi[k]) ** 2).sum(1) <= 1
+    x = x[~inside][:12]
+    r = orc.union_closest(parts, x, s_tol=1e-13, max_newton=100)
+    assert r["newton_fail"] == 0
+    for q in range(len(x)):
+        best, bk, bp = np.inf, -1, None
+        for k in range(K):
+            p, _ = pins.ellipsoid_projection(x[q] - cen[k], semi[k])
+            dk = np.linalg.norm(x[q] - cen[k] - p)
+            if dk < best:
+                best, bk, bp = dk, k, p + cen[k]
+        assert r["argmin"][q] == bk
+        assert abs(r["dist"][q] - best) <= 1e-9 * max(1, best)
+        assert np.abs(r["closest"][q] - bp).max() <= 1e-7 * max(1, np.abs(bp).max())
+
+
+# ---- P8: envelope gradients ---------------------------------------------------
+
+def test_backward_envelope_fd(orc):
+    """dphi/dA = -1/2 v v^T, dphi/dx = v, dphi/dt = -H(v) (envelope theorem on
+    eq. 3.3), by central differences of exact active-set values (symmetric
+    perturbation of A_ij and A_ji together gives twice the (i,j) entry)."""
+    n = 10
+    A, Ainv = _dense(n, 7601)
+    w = np.ones(n)
+    x = wl.normal(7604, n, 2.0)
+    t = 0.7
+    P = orc.Problem(A, orc.H_L1, tol=1e-30, max_iter=50000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x[None], [t])
+    v = r["grad"][0]
+    b = orc.backward(n, orc.A_DENSE, orc.H_L1, None, [1.0], v[None], [t])
+    h = 1e-6
+
+    def phi_exact(Am):
+        vv, ok = pins.kkt_active_set(Am, x, t, w, v)
+        assert ok
+        return pins.objective_neg(Am, x, t, w, vv)
+
+    for (i, j) in [(0, 0), (3, 3), (1, 4), (2, 7), (9, 5)]:
+        E = np.zeros((n, n))
+        E[i, j] += h
+        E[j, i] += h if i != j else 0.0
+        fd = (phi_exact(A + E) - phi_exact(A - E)) / (2 * h)
+        expect = b["g_A"][i, j] * (1 if i == j else 2)
+        assert abs(fd - expect) <= 1e-6 * max(1, abs(expect)), (i, j, fd, expect)
+    assert np.allclose(b["g_x"][0], v)
+    assert abs(b["g_t"][0] + np.abs(v).sum()) <= 1e-12
+
+
+def test_golden_section1_example(orc):
+    """A fixed worked instance of the Section 1 example (values written by
+    tests/golden/make_golden.py from the closed form, not from the oracle)."""
+    path = os.path.join(GOLDEN, "section1_l1_ellipsoid.txt")
+    rows = np.loadtxt(path, comments="#")
+    n = (rows.shape[1] - 2) // 3
+    for row in rows:
+        a = row[:n]; x = row[n:2 * n]; t = row[2 * n]; phi = row[2 * n + 1]; g = row[2 * n + 2:]
+        P = orc.Problem(a ** 2, orc.H_L1, tol=1e-28, max_iter=20000)
+        r = P.eval(x[None], [t])
+        assert abs(r["phi"][0] - phi) <= 1e-10 * max(1, abs(phi))
+        assert np.abs(r["grad"][0] - g).max() <= 1e-10
