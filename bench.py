@@ -1,0 +1,295 @@
+"""Throughput of the Hopf-formula evaluator on GB300.
+
+Workload (default): dense SPD A = Q diag(s) Q^T, n = 1024, s log-uniform in
+[0.1, 10], H = sum w_i |p_i| with w ~ U[0.5, 1.5], 65,536 queries per GPU with
+x ~ N(0, 4I), t ~ U[0.1, 3]; lambda = 1, relative stop 1e-14 on |u^k - u^{k-1}|^2.
+One step = one hopf_eval of the whole batch: every split Bregman iteration,
+the final phi pass and the reductions.  Metric: evaluations (phi, grad phi,
+d phi/dt) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant mixed|fp32|bf16]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+For N > 1 launch under torch.distributed.run: every rank evaluates its own
+65,536 queries (weak scaling, no collective on the data path); the time is the
+maximum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hopf evals/s (phi, grad phi at 1e-6 rel), n=1024, batch 64K, dense A, weighted l1"
+TOL = 1e-14
+MAX_ITER = 1000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--variant", default="mixed", choices=["mixed", "fp32", "bf16"])
+    p.add_argument("--n", type=int, default=1024)
+    p.add_argument("--batch", type=int, default=65536)
+    p.add_argument("--cpu-sample", type=int, default=192)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n, batch, rank):
+    import workloads as wl
+    A, Q, s = wl.spd_matrix(2001, 2002, n)
+    w = wl.uniform(2003, n, 0.5, 1.5)
+    x, t = wl.queries_dense(n, batch, offset=rank * batch)
+    return A, w, x, t
+
+
+def sample_clocks(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200",
+                                 "-f", path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def read_clocks(path, gpu_index):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def oracle_sample(A, w, x, t, count, tol):
+    """The FP64 oracle as it stands on `count` queries; returns (evals/s, threads, result)."""
+    import oracle
+    oracle.build()
+    P = oracle.Problem(A, oracle.H_WL1, w=w, tol=tol, max_iter=MAX_ITER, stop_rule=oracle.STOP_UREL)
+    xs = x[:count].astype(np.float64)
+    ts = t[:count].astype(np.float64)
+    t0 = time.perf_counter()
+    r = P.eval(xs, ts)
+    dt = time.perf_counter() - t0
+    return count / dt, oracle.num_threads(), r, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    A, w, x, t = workload(args.n, max(args.cpu_sample, 64), 0)
+    per_step = max(32, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        oracle_sample(A, w, x, t, 8, TOL)
+    total, evals, threads = 0.0, 0, 1
+    for s in range(args.steps):
+        rate, threads, _, dt = oracle_sample(A, w, x, t, per_step, TOL)
+        total += dt
+        evals += per_step
+    value = evals / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dense_wl1_n%d" % args.n, "n": args.n, "batch_per_step": per_step,
+                       "note": "FP64 C oracle (plain loops, OpenMP over queries) on a bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d queries of the n=%d workload per step" % (per_step, args.n)},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1605_01799_gb300 as hg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = {"mixed": hg.P_MIXED, "fp32": hg.P_FP32, "bf16": hg.P_BF16}[args.variant]
+    n, B = args.n, args.batch
+    A, w, x, t = workload(n, B, rank)
+    h = hg.Hopf(A, hg.H_WL1, w=w, tol=TOL, max_iter=MAX_ITER, precision=prec)
+    xd = torch.from_numpy(x).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    out = None
+    wsbuf = h.workspace(B)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        out = h.eval(xd, td, out=out, workspace=wsbuf)
+    torch.cuda.synchronize()
+    iters = out["iters"].cpu().numpy().astype(np.int64)
+    status = out["status"].cpu().numpy()
+
+    # timed region: device-resident inputs (256 MiB per step, larger than L2)
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk_path = tempfile.mktemp(suffix=".csv")
+    clk = sample_clocks(clk_path)
+    time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(args.steps):
+        h.profile_events(*ev_k[s])
+        out = h.eval(xd, td, out=out, workspace=wsbuf)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    h.profile_events(None, None)
+    if clk:
+        clk.terminate()
+        clk.wait()
+    ms = e0.elapsed_time(e1) / args.steps
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_k]))
+    if ws > 1:
+        tt = torch.tensor([ms, kern_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms, kern_ms = tt.tolist()
+    clocks = read_clocks(clk_path, local)
+    value = ws * B / (ms * 1e-3)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        th = torch.from_numpy(t).pin_memory()
+        phih = torch.empty(B, dtype=torch.float64).pin_memory()
+        gradh = torch.empty(B, n, dtype=torch.float32).pin_memory()
+        dth = torch.empty(B, dtype=torch.float32).pin_memory()
+        steps_e2e = max(2, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(steps_e2e):
+            xd.copy_(xh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            out = h.eval(xd, td, out=out, workspace=wsbuf)
+            phih.copy_(out["phi"], non_blocking=True)
+            gradh.copy_(out["grad"], non_blocking=True)
+            dth.copy_(out["dphidt"], non_blocking=True)
+        f1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = f0.elapsed_time(f1) / steps_e2e
+        if ws > 1:
+            tt = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ems = tt.item()
+        e2e = {"value": ws * B / (ems * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+               "d2h_bytes_per_step": int(phih.numel() * 8 + gradh.numel() * 4 + dth.numel() * 4),
+               "ms_per_step": ems}
+
+    # roofline of the dominant kernel (the persistent solver)
+    pk = peaks()
+    K = iters.astype(np.float64)
+    if prec == hg.P_FP32:
+        # one n x n FP32 product per iteration plus the final A p pass
+        flops = float(np.sum(2.0 * n * n * (K + 1)))
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12  # FFMA lanes x 2 flop x max SM clock
+        roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
+        dtype = "f32"
+    else:
+        terms = 4.0 if prec == hg.P_MIXED else 1.0  # MMA passes of n x n per iteration
+        flops = float(np.sum(2.0 * n * n * (terms * K + 3)))
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
+        dtype = "bf16+f16 (fp32 accumulate)" if prec == hg.P_MIXED else "bf16 (fp32 accumulate)"
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops})
+
+    cpu = None
+    accuracy = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, threads, r, dt = oracle_sample(A, w, x, t, args.cpu_sample, TOL)
+        cpu = {"value": rate, "unit": "evals/s", "cores": threads, "kind": "oracle",
+               "sample": "first %d queries of the same workload, FP64 oracle, same stop rule (%.1f s)"
+                         % (args.cpu_sample, dt)}
+        # accuracy of the timed outputs on a few queries against a tight oracle run
+        import oracle
+        m = 24
+        P = oracle.Problem(A, oracle.H_WL1, w=w, tol=1e-28, max_iter=20000, stop_rule=oracle.STOP_UREL)
+        ref = P.eval(x[:m].astype(np.float64), t[:m].astype(np.float64))
+        phi = out["phi"][:m].cpu().numpy()
+        g = out["grad"][:m].cpu().numpy().astype(np.float64)
+        ep = np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+        eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+        accuracy = {"queries": m, "phi_rel_max": float(ep.max()), "grad_rel_max": float(eg.max()),
+                    "grad_rel_median": float(np.median(eg))}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": "dense_wl1_n%d_b%d" % (n, B), "n": n, "batch_per_gpu": B,
+                           "variant": args.variant, "tol_urel": TOL, "max_iter": MAX_ITER,
+                           "parallelism": "replicas" if ws == 1 else "dp%d (independent query shards)" % ws,
+                           "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
+                "iters": {"mean": float(K.mean()), "max": int(K.max()), "min": int(K.min())},
+                "status_ok_frac": float((status == 0).mean()),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 3 * args.steps, "accuracy": accuracy}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * hopf.h - C ABI of the GB300 (sm_103a) Hopf-formula evaluator.
+ *
+ * The library evaluates, for many queries (x, t) at once, the viscosity
+ * solution of the Hamilton-Jacobi initial value problem
+ *     d phi/dt + H(grad_x phi) = 0,  phi(x, 0) = J(x)       (eqs. 1.1a-1.1b)
+ * through the Hopf formula
+ *     phi(x, t) = -min_v { J*(v) + t H(v) - <x, v> }         (eq. 1.2, eq. 3.3)
+ * of Darbon & Osher, "Algorithms for overcoming the curse of dimensionality
+ * for certain Hamilton-Jacobi equations arising in control theory and
+ * elsewhere".  The minimisation runs split Bregman (eq. 3.4(a)-(c)).
+ *
+ * Initial data (quadratic, Section 4: J = 1/2 <., D^{-1} .> generalised):
+ *     J(x) = 1/2 (x - c)^T A^{-1} (x - c) - c0,
+ *     J*(v) = 1/2 v^T A v + <c, v> + c0,
+ * with A symmetric positive definite, given either by its diagonal or as a
+ * dense matrix.  Hamiltonians (positively 1-homogeneous, Section 2.1):
+ *     H(p) = sum |p_i| (l1), sum w_i |p_i| (weighted l1, w_i > 0), |p|_2 (l2).
+ * Outputs per query: phi, grad_x phi = the minimiser v* (Section 1: the
+ * gradient is the unique minimiser of eq. 1.2), d phi/dt = -H(v*) (eq. 1.1a),
+ * the split Bregman iteration count and a status byte.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments of hopf_eval* / hopf_union_* / hopf_backward are
+ *     DEVICE pointers owned by the caller, row-major, query-major: x[q*n + i].
+ *     hopf_desc arrays are HOST pointers, read during hopf_create only.
+ *   - Work is enqueued on `stream`; calls return once the work is enqueued.
+ *     The caller synchronises the stream before reading results.
+ *   - Errors in arguments or CUDA calls return a non-OK status; the message
+ *     is in hopf_last_error() (thread-local).  Numerical outcomes per query
+ *     (no convergence, non-finite values) never fail the call: they are
+ *     reported in qstatus.
+ *   - batch == 0 is a valid no-op.
+ *   - No entry point below allocates memory except hopf_create (the handle's
+ *     own copies of the data); scratch comes from the caller's workspace,
+ *     whose size hopf_workspace_size reports.
+ */
+#ifndef HOPF_GB300_H
+#define HOPF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hopf_handle_s* hopf_handle;
+
+typedef enum {
+  HOPF_OK = 0,
+  HOPF_EINVAL = 1,        /* bad argument (null pointer, size, t < 0, ...) */
+  HOPF_ENOMEM = 2,        /* device allocation failed in hopf_create */
+  HOPF_ECUDA = 3,         /* a CUDA runtime or driver call failed */
+  HOPF_ENOTSPD = 4,       /* A + lambda I is not symmetric positive definite */
+  HOPF_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+  HOPF_ETIMEOUT = 6       /* a bounded device-side wait gave up (no hang) */
+} hopf_status;
+
+enum { HOPF_A_DIAG = 0, HOPF_A_DENSE = 1 };
+enum { HOPF_H_L1 = 0, HOPF_H_WL1 = 1, HOPF_H_L2 = 2 };
+
+/* Arithmetic of the v-update (eq. 3.4(a)).
+ *   FP64   diagonal A only; use hopf_eval_f64.
+ *   FP32   diagonal: FP32 per-query kernel.  Dense: the paper's form
+ *          v = (A + lambda I)^{-1} r as an FP32 CUDA-core GEMM per iteration.
+ *   BF16   dense: the same form with M = (A + lambda I)^{-1} and r in BF16 on
+ *          the tensor cores (tcgen05), FP32 accumulation.  Fast, ~1e-2 error.
+ *   MIXED  dense: tensor-core defect-correction form u <- u + M g(u) with
+ *          g = y - A p - lambda (u - p), A p from a two-term FP16 split with
+ *          an exactly scaled correction accumulator, M g in BF16.  Its fixed
+ *          point depends only on the accuracy of g: FP32-class results.
+ */
+enum { HOPF_P_FP64 = 0, HOPF_P_FP32 = 1, HOPF_P_BF16 = 2, HOPF_P_MIXED = 5 };
+
+/* Stopping rules.
+ *   PAPER: |v^k - v^{k-1}|^2, |d^k - d^{k-1}|^2, |d^k - v^k|^2 all <= tol
+ *          (Section 4.5).  Diagonal A only.
+ *   UREL:  |u^k - u^{k-1}|^2 <= tol * max(1, |u^k|^2) for k >= 2, where
+ *          u^k = v^k + b^{k-1} is the argument of the d-update. */
+enum { HOPF_STOP_PAPER = 0, HOPF_STOP_UREL = 1 };
+
+/* Per-query status bytes.  ABORTED: a bounded device-side wait of the dense
+ * solver gave up (it never hangs); every query of that call carries it. */
+enum { HOPF_Q_OK = 0, HOPF_Q_NOT_CONVERGED = 1, HOPF_Q_NONFINITE = 2, HOPF_Q_ABORTED = 3 };
+
+/* Problem description for hopf_create (host memory, copied).
+ *   n          dimension, 1 <= n <= 8192 (diagonal) or 4096 (dense)
+ *   a_kind     HOPF_A_DIAG: A points to n doubles > 0;
+ *              HOPF_A_DENSE: A points to n*n doubles, row-major, symmetric
+ *   centre     n doubles, or NULL for c = 0
+ *   c0         constant of J
+ *   h_kind     HOPF_H_L1 / HOPF_H_WL1 / HOPF_H_L2
+ *   w          n doubles > 0 for HOPF_H_WL1, else ignored (may be NULL)
+ *   lambda     split Bregman parameter, > 0 (the paper uses 1)
+ *   tol        stopping tolerance for stop_rule, > 0
+ *   max_iter   cap on split Bregman iterations, >= 1
+ *   precision  HOPF_P_*
+ *   stop_rule  HOPF_STOP_* */
+typedef struct {
+  int32_t n;
+  int32_t a_kind;
+  const double* A;
+  const double* centre;
+  double c0;
+  int32_t h_kind;
+  const double* w;
+  double lambda;
+  double tol;
+  int32_t max_iter;
+  int32_t precision;
+  int32_t stop_rule;
+} hopf_desc;
+
+/* Build a handle: copies A, c, w to the device and, for dense A, forms
+ * M = (A + lambda I)^{-1} in FP64 on the GPU (the prox of the quadratic J*,
+ * Section 3.1 / Section 4.1: (I + alpha A)^{-1}) with the casts the chosen
+ * precision needs.  Returns HOPF_ENOTSPD when a pivot of A + lambda I is not
+ * positive.  The handle is immutable afterwards: hopf_eval may run on several
+ * streams at once with distinct workspaces.  Synchronises `stream`. */
+hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t stream);
+
+/* Release the handle and its device memory (NULL is a no-op). */
+void hopf_destroy(hopf_handle h);
+
+/* Bytes of device workspace hopf_eval / hopf_eval_f64 need for `batch`
+ * queries (256-byte aligned pointer expected). */
+hopf_status hopf_workspace_size(hopf_handle h, int64_t batch, size_t* bytes);
+
+/* Evaluate `batch` queries (FP32 interface; any precision but FP64).
+ *   x       [batch][n] float, device      t      [batch] float >= 0, device
+ *   phi     [batch] double (FP64-accumulated phi), device
+ *   grad    [batch][n] float: grad_x phi = d^K (eq. 3.4(b) iterate), device
+ *   dphidt  [batch] float: -H(grad), device, may be NULL
+ *   iters   [batch] int32: split Bregman iterations, device, may be NULL
+ *   qstatus [batch] uint8: HOPF_Q_*, device, may be NULL
+ * t must be >= 0; t = 0 gives phi = J(x) (eq. 1.1b).  The split Bregman start
+ * is v^0 = d^0 = x - c, b^0 = 0 (Section 3.1). */
+hopf_status hopf_eval(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                      float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
+                      cudaStream_t stream);
+
+/* Same with FP64 queries and gradients; requires precision HOPF_P_FP64 and a
+ * diagonal A (the paper's own setting: FP64, n = 4..16, Section 4.5). */
+hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
+                          double* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
+                          cudaStream_t stream);
+
+/* Union of initial data (Section 2.2: the pointwise minimum of the solutions
+ * for convex J_i solves the problem with initial data min_i J_i).
+ * parts: K handles, all diagonal FP32 with the same n and h_kind.
+ *   phi [batch] double = min_i phi_i; grad [batch][n] float = grad of the
+ *   minimising part; argmin [batch] int32 (ties -> smallest i); iters [batch]
+ *   (iterations of the minimising part), qstatus [batch]; all device.
+ * workspace: hopf_union_workspace_size bytes. */
+hopf_status hopf_union_workspace_size(const hopf_handle* parts, int32_t K, int64_t batch, size_t* bytes);
+hopf_status hopf_union_eval(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, const float* t,
+                            double* phi, float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus,
+                            void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Distance and closest point to the union of the sets {J_i <= 0}
+ * (Section 3.2).  For each part, Newton's method on s for psi_i(y, s) = 0,
+ * psi_i the eikonal (H = l2) solution with initial data J_i:
+ *     s <- s + psi_i(y, s) / |grad psi_i(y, s)|   (eq. Newton_zero with
+ *     d psi/ds = -|grad psi|), s_0 = 0,
+ * stopping when |delta s| <= s_tol * max(1, s) or after max_newton steps, each
+ * step one split Bregman solve warm-started from the previous one.  Then
+ * dist = min_i s_i and closest = y - s grad psi / |grad psi| for the nearest
+ * part (eq. projection_when_s_known).  parts: diagonal, h_kind HOPF_H_L2, same
+ * n.  Queries must lie outside every set (J_i(x) > 0).
+ *   dist [batch] float, closest [batch][n] float (may be NULL), argmin [batch]
+ *   int32, newton [batch] int32 Newton steps of the nearest part (may be
+ *   NULL), qstatus [batch] (may be NULL); all device. */
+hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, float s_tol,
+                               int32_t max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                               uint8_t* qstatus, void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Gradients of phi with respect to the data by the envelope theorem applied
+ * to eq. 3.3 (v* = grad, the minimiser): with upstream weights g_phi[q],
+ *   g_x[q]  = g_phi[q] v*_q                  ([batch][n] float, may be NULL)
+ *   g_t[q]  = -g_phi[q] H(v*_q)              ([batch] float, may be NULL)
+ *   g_A     = -1/2 sum_q g_phi[q] v*_q v*_q^T   (dense: [n][n] float; diagonal:
+ *             [n] float, the diagonal only; may be NULL; overwritten)
+ * All device pointers.  Dense g_A is a batched outer-product GEMM. */
+hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
+                          float* g_t, float* g_A, cudaStream_t stream);
+
+/* Instrumentation: when `start` and `stop` are non-NULL CUDA events, every
+ * later hopf_eval on this handle records `start` on its stream immediately
+ * before the main solver kernel and `stop` immediately after it, so a caller
+ * can time that kernel alone (cudaEventElapsedTime).  NULL, NULL turns it off.
+ * Not thread-safe with concurrent hopf_eval calls on the same handle. */
+hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t stop);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hopf_last_error(void);
+
+/* Library version string. */
+const char* hopf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOPF_GB300_H */

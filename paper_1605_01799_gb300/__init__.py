@@ -1,0 +1,260 @@
+"""Python binding of libhopf_gb300 (the C ABI declared in include/hopf.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  There is no
+CPU fallback: if the shared library is missing or fails to load, every call
+raises.
+
+Low-level names mirror the C ABI (``hopf_create``, ``hopf_eval``, ...); the
+``Hopf`` class and the ``union_eval`` / ``union_closest`` / ``HopfFn`` helpers
+wrap them for torch tensors.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhopf_gb300.so")
+
+# constants of include/hopf.h
+HOPF_OK, HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA, HOPF_ENOTSPD, HOPF_EUNSUPPORTED, HOPF_ETIMEOUT = range(7)
+A_DIAG, A_DENSE = 0, 1
+H_L1, H_WL1, H_L2 = 0, 1, 2
+P_FP64, P_FP32, P_BF16, P_MIXED = 0, 1, 2, 5
+STOP_PAPER, STOP_UREL = 0, 1
+Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
+
+EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
+           "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_backward",
+           "hopf_profile_events", "hopf_last_error", "hopf_version"]
+
+
+class HopfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("hopf status %d: %s" % (status, msg))
+        self.status = status
+
+
+class hopf_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("a_kind", ctypes.c_int32), ("A", ctypes.c_void_p),
+                ("centre", ctypes.c_void_p), ("c0", ctypes.c_double), ("h_kind", ctypes.c_int32),
+                ("w", ctypes.c_void_p), ("lam", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32), ("stop_rule", ctypes.c_int32)]
+
+
+_lib = None
+_vp, _i64, _i32, _f32, _sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhopf_gb300.so is not built (run: python -m paper_1605_01799_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "hopf_create": ([ctypes.POINTER(hopf_desc), ctypes.POINTER(_vp), _vp], ctypes.c_int),
+            "hopf_destroy": ([_vp], None),
+            "hopf_workspace_size": ([_vp, _i64, ctypes.POINTER(_sz)], ctypes.c_int),
+            "hopf_eval": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_eval_f64": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_union_workspace_size": ([_vp, _i32, _i64, ctypes.POINTER(_sz)], ctypes.c_int),
+            "hopf_union_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_union_closest": ([_vp, _i32, _i64, _vp, _f32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+                                   ctypes.c_int),
+            "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
+            "hopf_last_error": ([], ctypes.c_char_p),
+            "hopf_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != HOPF_OK:
+        raise HopfError(status, lib().hopf_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def version():
+    return lib().hopf_version().decode()
+
+
+class Hopf:
+    """One problem instance J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0 with A diagonal
+    (1-D ``A``) or dense (2-D ``A``), H in {l1, weighted l1, l2}."""
+
+    def __init__(self, A, h_kind, w=None, centre=None, c0=0.5, lam=1.0, tol=1e-14, max_iter=1000,
+                 precision=P_FP32, stop_rule=STOP_UREL, stream=None):
+        import torch  # noqa: F401  (device context)
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        self.n = A.shape[0]
+        self.a_kind = A_DIAG if A.ndim == 1 else A_DENSE
+        self.h_kind, self.precision = int(h_kind), int(precision)
+        self._keep = [A]
+        wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        cv = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
+        self._keep += [wv, cv]
+        d = hopf_desc(self.n, self.a_kind, A.ctypes.data, None if cv is None else cv.ctypes.data, float(c0),
+                      self.h_kind, None if wv is None else wv.ctypes.data, float(lam), float(tol), int(max_iter),
+                      self.precision, int(stop_rule))
+        h = ctypes.c_void_p()
+        _check(lib().hopf_create(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hopf_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def workspace_size(self, batch):
+        b = ctypes.c_size_t()
+        _check(lib().hopf_workspace_size(self.handle, int(batch), ctypes.byref(b)))
+        return b.value
+
+    def workspace(self, batch):
+        import torch
+        need = self.workspace_size(batch)
+        if need == 0:
+            return None
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def eval(self, x, t, out=None, workspace=None, stream=None):
+        """x: [B, n] float32 cuda, t: [B] float32 cuda.  Returns a dict of
+        phi (float64), grad, dphidt, iters (int32), status (uint8)."""
+        import torch
+        fp64 = self.precision == P_FP64
+        dt = torch.float64 if fp64 else torch.float32
+        assert x.dtype == dt and t.dtype == dt and x.is_cuda and x.is_contiguous() and t.is_contiguous()
+        B = x.shape[0]
+        if out is None:
+            out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
+                   "grad": torch.empty(B, self.n, dtype=dt, device=x.device),
+                   "dphidt": torch.empty(B, dtype=dt, device=x.device),
+                   "iters": torch.empty(B, dtype=torch.int32, device=x.device),
+                   "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+        ws = workspace if workspace is not None else self.workspace(B)
+        nbytes = 0 if ws is None else ws.numel()
+        f = lib().hopf_eval_f64 if fp64 else lib().hopf_eval
+        _check(f(self.handle, B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]), _ptr(out.get("dphidt")),
+                 _ptr(out.get("iters")), _ptr(out.get("status")), _ptr(ws), nbytes, _stream(stream)))
+        return out
+
+    def profile_events(self, start=None, stop=None):
+        """Record torch.cuda.Event pair around the main solver kernel of later
+        eval calls (None, None turns it off)."""
+        sp = None if start is None else ctypes.c_void_p(start.cuda_event)
+        ep = None if stop is None else ctypes.c_void_p(stop.cuda_event)
+        _check(lib().hopf_profile_events(self.handle, sp, ep))
+
+    def backward(self, g_phi, vstar, want_x=True, want_t=True, want_A=True, stream=None):
+        import torch
+        B = vstar.shape[0]
+        gx = torch.empty_like(vstar) if want_x else None
+        gt = torch.empty(B, dtype=torch.float32, device=vstar.device) if want_t else None
+        gA = None
+        if want_A:
+            shape = (self.n, self.n) if self.a_kind == A_DENSE else (self.n,)
+            gA = torch.empty(shape, dtype=torch.float32, device=vstar.device)
+        _check(lib().hopf_backward(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
+                                   _stream(stream)))
+        return gx, gt, gA
+
+
+def _parts_array(parts):
+    arr = (ctypes.c_void_p * len(parts))(*[p.handle.value for p in parts])
+    return arr
+
+
+def union_eval(parts, x, t, stream=None):
+    """phi = min_i phi_i over diagonal parts (Section 2.2)."""
+    import torch
+    B, n = x.shape
+    arr = _parts_array(parts)
+    b = ctypes.c_size_t()
+    _check(lib().hopf_union_workspace_size(arr, len(parts), B, ctypes.byref(b)))
+    ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
+    out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
+           "grad": torch.empty(B, n, dtype=torch.float32, device=x.device),
+           "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
+           "iters": torch.empty(B, dtype=torch.int32, device=x.device),
+           "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    _check(lib().hopf_union_eval(arr, len(parts), B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]),
+                                 _ptr(out["argmin"]), _ptr(out["iters"]), _ptr(out["status"]), _ptr(ws), ws.numel(),
+                                 _stream(stream)))
+    return out
+
+
+def union_closest(parts, x, s_tol=1e-6, max_newton=50, stream=None):
+    """Distance and closest point to the union of {J_i <= 0} (Section 3.2)."""
+    import torch
+    B, n = x.shape
+    arr = _parts_array(parts)
+    b = ctypes.c_size_t()
+    _check(lib().hopf_union_workspace_size(arr, len(parts), B, ctypes.byref(b)))
+    ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
+    out = {"dist": torch.empty(B, dtype=torch.float32, device=x.device),
+           "closest": torch.empty(B, n, dtype=torch.float32, device=x.device),
+           "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
+           "newton": torch.empty(B, dtype=torch.int32, device=x.device),
+           "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    _check(lib().hopf_union_closest(arr, len(parts), B, _ptr(x), float(s_tol), int(max_newton), _ptr(out["dist"]),
+                                    _ptr(out["closest"]), _ptr(out["argmin"]), _ptr(out["newton"]),
+                                    _ptr(out["status"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def _autograd():
+    import torch
+
+    class HopfFn(torch.autograd.Function):
+        """phi(x, t; A) with the hand-written envelope-theorem backward.
+        ``A_param`` is the tensor the caller differentiates with respect to;
+        ``hopf`` must be a handle built from its current value."""
+
+        @staticmethod
+        def forward(ctx, x, t, A_param, hopf):
+            out = hopf.eval(x, t)
+            ctx.hopf = hopf
+            ctx.save_for_backward(out["grad"])
+            return out["phi"].to(torch.float32), out["grad"]
+
+        @staticmethod
+        def backward(ctx, g_phi, g_grad):
+            (vstar,) = ctx.saved_tensors
+            need_x, need_t, need_A = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            gx, gt, gA = ctx.hopf.backward(g_phi.contiguous().to(torch.float32), vstar, need_x, need_t, need_A)
+            return gx, gt, gA, None
+
+    return HopfFn
+
+
+_HopfFn = None
+
+
+def HopfFn():
+    global _HopfFn
+    if _HopfFn is None:
+        _HopfFn = _autograd()
+    return _HopfFn

@@ -1,0 +1,123 @@
+// Backward pass by the envelope theorem.
+//
+// phi(x, t; A) = max_v -F(v; x, t, A) with F the objective of eq. 3.3, and the
+// maximiser v* is grad_x phi (Section 1).  Differentiating at fixed v*:
+//   d phi/dx = v*,  d phi/dt = -H(v*),  d phi/dA = -1/2 v* v*^T
+// (J*(v) = 1/2 v^T A v + ...).  With upstream weights g_q per query:
+//   g_x[q] = g_q v*_q,  g_t[q] = -g_q H(v*_q),
+//   g_A = -1/2 sum_q g_q v*_q v*_q^T = -1/2 V^T diag(g) V   (V = [B][n])
+// and for diagonal A only the diagonal -1/2 sum_q g_q v*_{qi}^2.
+#include "common.cuh"
+#include "hopf_internal.h"
+
+namespace hopf {
+namespace {
+
+// g_x and g_t: one warp per query.
+__global__ void k_bwd_xt(const float* __restrict__ g, const float* __restrict__ V, const float* __restrict__ w,
+                         int n, int64_t B, int h_kind, float* __restrict__ gx, float* __restrict__ gt) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= B) return;
+  const float gq = g[q];
+  double h = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const float v = V[q * n + i];
+    if (gx) gx[q * n + i] = gq * v;
+    h += h_kind == H_L2 ? (double)v * v : (double)w[i] * fabs((double)v);
+  }
+  h = warp_sum(h);
+  if (lane == 0 && gt) gt[q] = (float)(-(double)gq * (h_kind == H_L2 ? sqrt(h) : h));
+}
+
+// Diagonal g_A: column sums over the batch.
+__global__ void k_bwd_diagA(const float* __restrict__ g, const float* __restrict__ V, int n, int64_t B,
+                            float* __restrict__ gA) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t q = 0; q < B; ++q) {
+    const double v = V[q * n + i];
+    s += (double)g[q] * v * v;
+  }
+  gA[i] = (float)(-0.5 * s);
+}
+
+// Dense g_A: 128 x 128 output tile per CTA, K = the batch.  Both operands are
+// rows of V (contiguous along the output index), so no transpose is needed.
+constexpr int BM = 128, BK = 16, NT = 256, PADS = 4;
+
+__global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ g, const float* __restrict__ V, int n,
+                                                      int64_t B, float* __restrict__ gA) {
+  __shared__ __align__(16) float As[BK][BM + PADS];
+  __shared__ __align__(16) float Bs[BK][BM + PADS];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BM;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  for (int64_t q0 = 0; q0 < B; q0 += BK) {
+    // each thread loads 8 elements of each operand tile (16 rows of the batch x 128)
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int f = tid + h * NT, kk = f >> 7, col = f & 127;
+      const int64_t q = q0 + kk;
+      const bool okq = q < B;
+      const float gq = okq ? g[q] : 0.f;
+      const int ia = i0 + col, jb = j0 + col;
+      As[kk][col] = (okq && ia < n) ? V[q * n + ia] * gq : 0.f;
+      Bs[kk][col] = (okq && jb < n) ? V[q * n + jb] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + a - 4);
+    if (i >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int j = j0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
+      if (j < n) gA[(int64_t)i * n + j] = -0.5f * acc[a][b];
+    }
+  }
+}
+
+}  // namespace
+
+hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,
+                     float* g_A, cudaStream_t stream) {
+  const int n = h->n;
+  if (g_x || g_t) {
+    k_bwd_xt<<<(unsigned)((batch * 32 + 255) / 256), 256, 0, stream>>>(g_phi, vstar, h->d_wf, n, batch, h->h_kind,
+                                                                        g_x, g_t);
+    HOPF_CUDA(cudaGetLastError());
+  }
+  if (g_A) {
+    if (h->a_kind == HOPF_A_DIAG) {
+      k_bwd_diagA<<<(n + 255) / 256, 256, 0, stream>>>(g_phi, vstar, n, batch, g_A);
+    } else {
+      dim3 grd((n + BM - 1) / BM, (n + BM - 1) / BM);
+      k_bwd_denseA<<<grd, NT, 0, stream>>>(g_phi, vstar, n, batch, g_A);
+    }
+    HOPF_CUDA(cudaGetLastError());
+  }
+  return HOPF_OK;
+}
+
+}  // namespace hopf

@@ -1,0 +1,543 @@
+// Diagonal-A path: the whole split Bregman iteration of one query on chip.
+//
+// For A = diag(a) the v-update of eq. 3.4(a) is elementwise,
+//   v_i = (y_i + lambda (d_i - b_i)) / (a_i + lambda),
+// the d-update (eq. 3.4(b)) is shrink_1 with threshold (t/lambda) w_i or
+// shrink_2 with threshold t/lambda, and the b-update (eq. 3.4(c)) is
+// b = b + v - d.  A group of G threads owns one query; each thread keeps VPT
+// coordinates of y, v, d, b in registers (index i = lane + G * j), so the state
+// never leaves the SM (the paper's "very low memory" remark, Section 4.5).
+// G = 1 is the paper's own setting (n = 4..16, one evaluation per core);
+// G = 32 is a warp per query; G = 256 / 512 is a CTA per query for large n
+// (n <= 8192).
+#include <cmath>
+
+#include "common.cuh"
+#include "hopf_internal.h"
+
+namespace hopf {
+
+template <typename T>
+struct DiagPart {
+  const T* a;    // [n] diagonal of A
+  const T* c;    // [n] centre or null
+  const T* w;    // [n] weights (ones when unweighted)
+  double c0;
+  T lam, tol;
+  int max_iter, stop_rule, h_kind;
+};
+
+// Sum of three values over the G threads of a query group.
+template <int G, typename T>
+struct Group {
+  __device__ static void sum3(T& a, T& b, T& c) {
+    if constexpr (G == 1) {
+      return;
+    } else if constexpr (G == 32) {
+      a = warp_sum(a);
+      b = warp_sum(b);
+      c = warp_sum(c);
+    } else {
+      __shared__ T s[3][G / 32];
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      a = warp_sum(a);
+      b = warp_sum(b);
+      c = warp_sum(c);
+      __syncthreads();
+      if (lane == 0) {
+        s[0][wid] = a;
+        s[1][wid] = b;
+        s[2][wid] = c;
+      }
+      __syncthreads();
+      a = T(0);
+      b = T(0);
+      c = T(0);
+#pragma unroll
+      for (int k = 0; k < G / 32; ++k) {
+        a += s[0][k];
+        b += s[1][k];
+        c += s[2][k];
+      }
+    }
+  }
+  __device__ static T sum(T a) {
+    T b = T(0), c = T(0);
+    sum3(a, b, c);
+    return a;
+  }
+};
+
+template <int G>
+__device__ __forceinline__ int group_lane() {
+  if constexpr (G == 1) return 0;
+  else if constexpr (G == 32) return threadIdx.x & 31;
+  else return threadIdx.x;
+}
+
+template <typename T, int G, int VPT>
+struct Query {
+  T y[VPT], ia[VPT], v[VPT], d[VPT], b[VPT];  // ia = 1 / (a_i + lambda)
+  const T* a;
+  const T* w;
+  int n;
+
+  __device__ void load(const DiagPart<T>& P, const T* x, int n_) {
+    n = n_;
+    a = P.a;
+    w = P.w;
+    const int l = group_lane<G>();
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const int i = l + G * j;
+      const bool in = i < n;
+      const T xi = in ? x[i] : T(0);
+      y[j] = in ? xi - (P.c ? P.c[i] : T(0)) : T(0);
+      ia[j] = in ? T(1) / (P.a[i] + P.lam) : T(0);
+    }
+  }
+  __device__ T wt(int j) const {
+    const int i = group_lane<G>() + G * j;
+    return i < n ? __ldg(w + i) : T(1);
+  }
+  __device__ T at(int j) const {
+    const int i = group_lane<G>() + G * j;
+    return i < n ? __ldg(a + i) : T(0);
+  }
+  // The paper's start: v^0 = d^0 = y, b^0 = 0 (Section 3.1).
+  __device__ void cold_start() {
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      v[j] = y[j];
+      d[j] = y[j];
+      b[j] = T(0);
+    }
+  }
+
+  // Runs split Bregman at time t from the current (v, d, b); returns the
+  // iteration count, sets *conv.
+  __device__ int solve(const DiagPart<T>& P, T t, bool* conv) {
+    const T lam = P.lam, tau = t / P.lam;
+    int k;
+    *conv = false;
+    for (k = 1; k <= P.max_iter; ++k) {
+      T vn[VPT], z[VPT];
+      T zz = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        vn[j] = (y[j] + lam * (d[j] - b[j])) * ia[j];  // eq. 3.4(a)
+        z[j] = vn[j] + b[j];                                  // u^k = v^k + b^{k-1}
+        zz += z[j] * z[j];
+      }
+      T s2 = T(1);
+      if (P.h_kind == H_L2) {
+        const T nz = sqrt(Group<G, T>::sum(zz));
+        s2 = shrink2_scale(nz, tau);
+      }
+      T r1 = T(0), r2 = T(0), r3 = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const T dn = P.h_kind == H_L2 ? s2 * z[j] : shrink1(z[j], tau * wt(j));  // eq. 3.4(b)
+        if (P.stop_rule == STOP_PAPER) {
+          r1 += (vn[j] - v[j]) * (vn[j] - v[j]);
+          r2 += (dn - d[j]) * (dn - d[j]);
+          r3 += (dn - vn[j]) * (dn - vn[j]);
+        } else {
+          const T du = z[j] - (d[j] + b[j]);  // u^k - u^{k-1}, u^{k-1} = d^{k-1} + b^{k-1}
+          r1 += du * du;
+        }
+        b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
+        d[j] = dn;
+        v[j] = vn[j];
+      }
+      if (P.stop_rule == STOP_PAPER) {
+        Group<G, T>::sum3(r1, r2, r3);
+        if (r1 <= P.tol && r2 <= P.tol && r3 <= P.tol) {
+          *conv = true;
+          break;
+        }
+      } else {
+        Group<G, T>::sum3(r1, zz, r2);
+        if (k >= 2 && r1 <= P.tol * (zz > T(1) ? zz : T(1))) {
+          *conv = true;
+          break;
+        }
+      }
+    }
+    return k > P.max_iter ? P.max_iter : k;
+  }
+
+  // phi = <y, d> - 1/2 d^T A d - c0 - t H(d), FP64 accumulation; returns H(d).
+  __device__ double objective(const DiagPart<T>& P, double t, double* H) {
+    double s = 0.0, h = 0.0, z = 0.0;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const double dj = (double)d[j];
+      s += (double)y[j] * dj - 0.5 * (double)at(j) * dj * dj;
+      if (P.h_kind == H_L2) h += dj * dj;
+      else h += (double)wt(j) * fabs(dj);
+    }
+    Group<G, double>::sum3(s, h, z);
+    *H = P.h_kind == H_L2 ? sqrt(h) : h;
+    return s - P.c0 - t * (*H);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Plain evaluation.
+template <typename T>
+struct DiagEvalArgs {
+  DiagPart<T> P;
+  int n;
+  int64_t batch;
+  const T* x;
+  const T* t;
+  double* phi;
+  T* grad;
+  T* dphidt;
+  int32_t* iters;
+  uint8_t* qstatus;
+};
+
+template <int G>
+constexpr int block_of() { return G == 1 || G == 32 ? 128 : G; }
+
+template <typename T, int G, int VPT>
+__global__ void __launch_bounds__(block_of<G>()) k_diag_eval(DiagEvalArgs<T> A) {
+  const int64_t q = G == 1 ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                           : (G == 32 ? ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : (int64_t)blockIdx.x);
+  if (q >= A.batch) return;  // whole groups leave together
+  Query<T, G, VPT> Q;
+  Q.load(A.P, A.x + q * A.n, A.n);
+  Q.cold_start();
+  const T tq = A.t[q];
+  bool conv;
+  const int k = Q.solve(A.P, tq, &conv);
+  double H;
+  const double phi = Q.objective(A.P, (double)tq, &H);
+  const int l = group_lane<G>();
+  bool finite = isfinite(phi);
+#pragma unroll
+  for (int j = 0; j < VPT; ++j) {
+    const int i = l + G * j;
+    if (i < A.n) A.grad[q * A.n + i] = Q.d[j];
+  }
+  if (l == 0) {
+    A.phi[q] = phi;
+    if (A.dphidt) A.dphidt[q] = (T)(-H);
+    if (A.iters) A.iters[q] = k;
+    if (A.qstatus) A.qstatus[q] = !finite ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED);
+  }
+}
+
+template <typename T, int G, int VPT>
+static void launch_eval(const DiagEvalArgs<T>& a, cudaStream_t s) {
+  if constexpr (G == 1) {
+    k_diag_eval<T, 1, VPT><<<(unsigned)((a.batch + 127) / 128), 128, 0, s>>>(a);
+  } else if constexpr (G == 32) {
+    k_diag_eval<T, 32, VPT><<<(unsigned)((a.batch + 3) / 4), 128, 0, s>>>(a);
+  } else {
+    k_diag_eval<T, G, VPT><<<(unsigned)a.batch, G, 0, s>>>(a);
+  }
+}
+
+// Pick the group shape from n.
+template <typename T>
+static hopf_status dispatch_eval(const DiagEvalArgs<T>& a, cudaStream_t s) {
+  const int n = a.n;
+  if (n <= 16) launch_eval<T, 1, 16>(a, s);
+  else if (n <= 64) launch_eval<T, 32, 2>(a, s);
+  else if (n <= 256) launch_eval<T, 32, 8>(a, s);
+  else if (n <= 512) launch_eval<T, 32, 16>(a, s);
+  else if (n <= 4096) launch_eval<T, 256, 16>(a, s);
+  else launch_eval<T, 512, 16>(a, s);
+  HOPF_CUDA(cudaGetLastError());
+  return HOPF_OK;
+}
+
+size_t diag_workspace(const hopf_handle, int64_t) { return 0; }
+
+template <typename T>
+static DiagPart<T> part_of(hopf_handle h);
+
+template <>
+DiagPart<float> part_of<float>(hopf_handle h) {
+  return DiagPart<float>{h->d_af, h->d_c ? h->d_cf : nullptr, h->d_wf, h->c0, (float)h->lambda, (float)h->tol,
+                         h->max_iter, h->stop_rule, h->h_kind};
+}
+template <>
+DiagPart<double> part_of<double>(hopf_handle h) {
+  return DiagPart<double>{h->d_A, h->d_c, h->d_w, h->c0, h->lambda, h->tol, h->max_iter, h->stop_rule, h->h_kind};
+}
+
+hopf_status diag_eval_f32(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
+  DiagEvalArgs<float> a{part_of<float>(h), h->n, batch, x, t, phi, grad, dphidt, iters, qstatus};
+  if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
+  hopf_status s = dispatch_eval(a, stream);
+  if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
+  return s;
+}
+
+hopf_status diag_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
+                          double* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
+  DiagEvalArgs<double> a{part_of<double>(h), h->n, batch, x, t, phi, grad, dphidt, iters, qstatus};
+  if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
+  hopf_status s = dispatch_eval(a, stream);
+  if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Union of initial data (Section 2.2): phi = min_i phi_i.  Pass 1 evaluates
+// every (query, part) pair; pass 2 picks the minimising part (ties to the
+// smallest index) and re-runs it to write its gradient.
+constexpr int kMaxParts = 64;
+
+struct UnionArgs {
+  DiagPart<float> parts[kMaxParts];  // by value: the launch needs no host copy
+  int K, n;
+  int64_t batch;
+  const float* x;
+  const float* t;       // time per query (union eval) or null (closest point)
+  double* phi_parts;    // [batch][K]
+  float* s_parts;       // [batch][K] Newton root per part (closest point)
+  int32_t* it_parts;    // [batch][K]
+  uint8_t* st_parts;    // [batch][K]
+  float s_tol;
+  int max_newton;
+  // outputs
+  double* phi;
+  float* grad;
+  int32_t* argmin;
+  int32_t* iters;
+  uint8_t* qstatus;
+  float* dist;
+  float* closest;
+};
+
+template <int G>
+__device__ __forceinline__ int64_t group_index() {
+  if constexpr (G == 32) return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  else return (int64_t)blockIdx.x;
+}
+
+template <int G, int VPT>
+__global__ void __launch_bounds__(block_of<G>()) k_union_parts(UnionArgs U) {
+  const int64_t pair = group_index<G>();
+  if (pair >= U.batch * U.K) return;
+  const int64_t q = pair / U.K;
+  const int part = (int)(pair % U.K);
+  const DiagPart<float> P = U.parts[part];
+  Query<float, G, VPT> Q;
+  Q.load(P, U.x + q * U.n, U.n);
+  Q.cold_start();
+  bool conv;
+  const int k = Q.solve(P, U.t[q], &conv);
+  double H;
+  const double phi = Q.objective(P, (double)U.t[q], &H);
+  if (group_lane<G>() == 0) {
+    U.phi_parts[pair] = phi;
+    U.it_parts[pair] = k;
+    U.st_parts[pair] = !isfinite(phi) ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED);
+  }
+}
+
+template <int G, int VPT>
+__global__ void __launch_bounds__(block_of<G>()) k_union_pick(UnionArgs U) {
+  const int64_t q = group_index<G>();
+  if (q >= U.batch) return;
+  int best = 0;
+  double bv = U.phi_parts[q * U.K];
+  for (int i = 1; i < U.K; ++i) {
+    const double v = U.phi_parts[q * U.K + i];
+    if (v < bv || (isnan(bv) && !isnan(v))) {
+      bv = v;
+      best = i;
+    }
+  }
+  const DiagPart<float> P = U.parts[best];
+  Query<float, G, VPT> Q;
+  Q.load(P, U.x + q * U.n, U.n);
+  Q.cold_start();
+  bool conv;
+  Q.solve(P, U.t[q], &conv);
+  const int l = group_lane<G>();
+#pragma unroll
+  for (int j = 0; j < VPT; ++j) {
+    const int i = l + G * j;
+    if (i < U.n) U.grad[q * U.n + i] = Q.d[j];
+  }
+  if (l == 0) {
+    U.phi[q] = bv;
+    U.argmin[q] = best;
+    if (U.iters) U.iters[q] = U.it_parts[q * U.K + best];
+    if (U.qstatus) U.qstatus[q] = U.st_parts[q * U.K + best];
+  }
+}
+
+// Newton on s for psi_i(y, s) = 0 (Section 3.2), warm-started solves.
+template <int G, int VPT>
+__global__ void __launch_bounds__(block_of<G>()) k_closest_parts(UnionArgs U) {
+  const int64_t pair = group_index<G>();
+  if (pair >= U.batch * U.K) return;
+  const int64_t q = pair / U.K;
+  const int part = (int)(pair % U.K);
+  const DiagPart<float> P = U.parts[part];
+  Query<float, G, VPT> Q;
+  Q.load(P, U.x + q * U.n, U.n);
+  Q.cold_start();
+  double s = 0.0;
+  bool ok = false, finite = true;
+  int l;
+  for (l = 0; l < U.max_newton; ++l) {
+    bool conv;
+    Q.solve(P, (float)s, &conv);
+    double H;
+    const double psi = Q.objective(P, s, &H);
+    // |grad psi| = |d| (H = l2 here)
+    if (!(H > 0.0) || !isfinite(psi)) {
+      finite = isfinite(psi);
+      break;
+    }
+    const double ds = psi / H;
+    s += ds;
+    if (fabs(ds) <= (double)U.s_tol * (s > 1.0 ? s : 1.0)) {
+      ok = true;
+      ++l;
+      break;
+    }
+  }
+  if (group_lane<G>() == 0) {
+    U.s_parts[pair] = (float)s;
+    U.phi_parts[pair] = s;
+    U.it_parts[pair] = l;
+    U.st_parts[pair] = !finite ? Q_NONFINITE : (ok ? Q_OK : Q_NOT_CONVERGED);
+  }
+}
+
+template <int G, int VPT>
+__global__ void __launch_bounds__(block_of<G>()) k_closest_pick(UnionArgs U) {
+  const int64_t q = group_index<G>();
+  if (q >= U.batch) return;
+  int best = 0;
+  double bv = U.phi_parts[q * U.K];
+  for (int i = 1; i < U.K; ++i) {
+    const double v = U.phi_parts[q * U.K + i];
+    if (v < bv || (isnan(bv) && !isnan(v))) {
+      bv = v;
+      best = i;
+    }
+  }
+  const float s = U.s_parts[q * U.K + best];
+  const int l = group_lane<G>();
+  if (U.closest) {
+    const DiagPart<float> P = U.parts[best];
+    Query<float, G, VPT> Q;
+    Q.load(P, U.x + q * U.n, U.n);
+    Q.cold_start();
+    bool conv;
+    Q.solve(P, s, &conv);
+    float nn = 0.f;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) nn += Q.d[j] * Q.d[j];
+    nn = sqrtf(Group<G, float>::sum(nn));
+    const float inv = nn > 0.f ? 1.f / nn : 0.f;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const int i = l + G * j;
+      if (i < U.n) U.closest[q * U.n + i] = U.x[q * U.n + i] - s * Q.d[j] * inv;  // eq. projection_when_s_known
+    }
+  }
+  if (l == 0) {
+    U.dist[q] = s;
+    U.argmin[q] = best;
+    if (U.iters) U.iters[q] = U.it_parts[q * U.K + best];
+    if (U.qstatus) U.qstatus[q] = U.st_parts[q * U.K + best];
+  }
+}
+
+size_t union_workspace(int K, int n, int64_t batch) {
+  (void)n;
+  size_t b = (size_t)batch * K;
+  return round_up(b * 8, 256) + round_up(b * 4, 256) + round_up(b * 4, 256) + round_up(b, 256);
+}
+
+static hopf_status carve_union(const hopf_handle* parts, int K, int64_t batch, void* ws, UnionArgs* U) {
+  if (K > kMaxParts) return fail(HOPF_EUNSUPPORTED, "hopf_union: at most 64 parts");
+  char* p = (char*)ws;
+  size_t b = (size_t)batch * K;
+  U->phi_parts = (double*)p;
+  p += round_up(b * 8, 256);
+  U->s_parts = (float*)p;
+  p += round_up(b * 4, 256);
+  U->it_parts = (int32_t*)p;
+  p += round_up(b * 4, 256);
+  U->st_parts = (uint8_t*)p;
+  for (int i = 0; i < K; ++i) U->parts[i] = part_of<float>(parts[i]);
+  U->K = K;
+  U->n = parts[0]->n;
+  U->batch = batch;
+  return HOPF_OK;
+}
+
+template <int G, int VPT>
+static void launch_union(UnionArgs& U, bool closest, cudaStream_t s) {
+  const int64_t pairs = U.batch * U.K;
+  const unsigned bx = G == 32 ? 128 : G;
+  const int per = G == 32 ? 4 : 1;
+  if (!closest) {
+    k_union_parts<G, VPT><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
+    k_union_pick<G, VPT><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);
+  } else {
+    k_closest_parts<G, VPT><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
+    k_closest_pick<G, VPT><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);
+  }
+}
+
+static hopf_status dispatch_union(UnionArgs& U, bool closest, cudaStream_t s) {
+  const int n = U.n;
+  if (n <= 64) launch_union<32, 2>(U, closest, s);
+  else if (n <= 256) launch_union<32, 8>(U, closest, s);
+  else if (n <= 512) launch_union<32, 16>(U, closest, s);
+  else if (n <= 4096) launch_union<256, 16>(U, closest, s);
+  else launch_union<512, 16>(U, closest, s);
+  HOPF_CUDA(cudaGetLastError());
+  return HOPF_OK;
+}
+
+hopf_status union_eval(const hopf_handle* parts, int K, int64_t batch, const float* x, const float* t, double* phi,
+                       float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus, void* ws, size_t,
+                       cudaStream_t stream) {
+  UnionArgs U{};
+  hopf_status s = carve_union(parts, K, batch, ws, &U);
+  if (s != HOPF_OK) return s;
+  U.x = x;
+  U.t = t;
+  U.phi = phi;
+  U.grad = grad;
+  U.argmin = argmin;
+  U.iters = iters;
+  U.qstatus = qstatus;
+  return dispatch_union(U, false, stream);
+}
+
+hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
+                          int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                          uint8_t* qstatus, void* ws, size_t, cudaStream_t stream) {
+  UnionArgs U{};
+  hopf_status s = carve_union(parts, K, batch, ws, &U);
+  if (s != HOPF_OK) return s;
+  U.x = x;
+  U.t = nullptr;
+  U.s_tol = s_tol;
+  U.max_newton = max_newton;
+  U.dist = dist;
+  U.closest = closest;
+  U.argmin = argmin;
+  U.iters = newton;
+  U.qstatus = qstatus;
+  return dispatch_union(U, true, stream);
+}
+
+}  // namespace hopf

@@ -1,0 +1,285 @@
+// C ABI entry points: argument checks, handle lifetime, dispatch to kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "hopf_internal.h"
+
+namespace hopf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+hopf_status fail(hopf_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+hopf_status cuda_fail(cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? HOPF_ENOMEM : HOPF_ECUDA;
+}
+
+int sm_count(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v;
+}
+
+static void free_handle(hopf_handle h) {
+  if (!h) return;
+  void* ptrs[] = {h->d_A, h->d_c, h->d_w, h->d_cf, h->d_wf, h->d_af, h->d_M64, h->d_M32, h->d_A32,
+                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Abf};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+}  // namespace hopf
+
+using namespace hopf;
+
+extern "C" {
+
+const char* hopf_last_error(void) { return g_last_error.c_str(); }
+
+hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t stop) {
+  set_error("");
+  if (!h) return fail(HOPF_EINVAL, "hopf_profile_events: null handle");
+  if ((start == nullptr) != (stop == nullptr)) return fail(HOPF_EINVAL, "hopf_profile_events: give both events or none");
+  h->prof_start = start;
+  h->prof_stop = stop;
+  return HOPF_OK;
+}
+
+const char* hopf_version(void) { return "hopf-gb300 0.1 (sm_103a)"; }
+
+hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t stream) {
+  set_error("");
+  if (!desc || !out) return fail(HOPF_EINVAL, "hopf_create: null desc or out");
+  *out = nullptr;
+  const hopf_desc& d = *desc;
+  if (d.a_kind != HOPF_A_DIAG && d.a_kind != HOPF_A_DENSE) return fail(HOPF_EINVAL, "hopf_create: bad a_kind");
+  const int nmax = d.a_kind == HOPF_A_DIAG ? 8192 : 4096;
+  if (d.n < 1 || d.n > nmax) return fail(HOPF_EINVAL, "hopf_create: n out of range");
+  if (!d.A) return fail(HOPF_EINVAL, "hopf_create: null A");
+  if (d.h_kind != HOPF_H_L1 && d.h_kind != HOPF_H_WL1 && d.h_kind != HOPF_H_L2)
+    return fail(HOPF_EINVAL, "hopf_create: bad h_kind");
+  if (d.h_kind == HOPF_H_WL1 && !d.w) return fail(HOPF_EINVAL, "hopf_create: weighted l1 needs w");
+  if (!(d.lambda > 0) || !std::isfinite(d.lambda)) return fail(HOPF_EINVAL, "hopf_create: lambda must be > 0");
+  if (!(d.tol > 0) || !std::isfinite(d.tol)) return fail(HOPF_EINVAL, "hopf_create: tol must be > 0");
+  if (d.max_iter < 1) return fail(HOPF_EINVAL, "hopf_create: max_iter must be >= 1");
+  if (d.stop_rule != HOPF_STOP_PAPER && d.stop_rule != HOPF_STOP_UREL)
+    return fail(HOPF_EINVAL, "hopf_create: bad stop_rule");
+  if (d.precision != HOPF_P_FP64 && d.precision != HOPF_P_FP32 && d.precision != HOPF_P_BF16 &&
+      d.precision != HOPF_P_MIXED)
+    return fail(HOPF_EINVAL, "hopf_create: bad precision");
+  if (d.a_kind == HOPF_A_DENSE && d.precision == HOPF_P_FP64)
+    return fail(HOPF_EUNSUPPORTED, "hopf_create: FP64 is implemented for diagonal A only");
+  if (d.a_kind == HOPF_A_DENSE && d.stop_rule == HOPF_STOP_PAPER)
+    return fail(HOPF_EUNSUPPORTED, "hopf_create: dense A uses the relative u stop rule (HOPF_STOP_UREL)");
+  const int n = d.n;
+  for (int i = 0; i < n; ++i) {
+    if (d.h_kind == HOPF_H_WL1 && !(d.w[i] > 0)) return fail(HOPF_EINVAL, "hopf_create: weights must be > 0");
+    if (d.centre && !std::isfinite(d.centre[i])) return fail(HOPF_EINVAL, "hopf_create: non-finite centre");
+    if (d.a_kind == HOPF_A_DIAG && !(d.A[i] > 0 && std::isfinite(d.A[i])))
+      return fail(HOPF_ENOTSPD, "hopf_create: diagonal A must be positive");
+  }
+
+  hopf_handle h = new hopf_handle_s();
+  h->n = n;
+  h->n_pad = (int)round_up(n, 128);
+  h->a_kind = d.a_kind;
+  h->h_kind = d.h_kind;
+  h->precision = d.precision;
+  h->stop_rule = d.stop_rule;
+  h->max_iter = d.max_iter;
+  h->c0 = d.c0;
+  h->lambda = d.lambda;
+  h->tol = d.tol;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  h->num_sms = sm_count(h->device);
+
+#define H_ALLOC(ptr, bytes)                           \
+  do {                                                \
+    cudaError_t e2 = cudaMalloc((void**)&(ptr), (bytes)); \
+    if (e2 != cudaSuccess) {                          \
+      free_handle(h);                                 \
+      return cuda_fail(e2, "cudaMalloc");             \
+    }                                                 \
+  } while (0)
+#define H_CALL(call)                                  \
+  do {                                                \
+    cudaError_t e2 = (call);                          \
+    if (e2 != cudaSuccess) {                          \
+      free_handle(h);                                 \
+      return cuda_fail(e2, #call);                    \
+    }                                                 \
+  } while (0)
+
+  const int np = h->n_pad;
+  std::vector<double> wv(n, 1.0);
+  if (d.h_kind == HOPF_H_WL1)
+    for (int i = 0; i < n; ++i) wv[i] = d.w[i];
+  std::vector<float> wf(np, 1.0f), cf(np, 0.0f);
+  for (int i = 0; i < n; ++i) {
+    wf[i] = (float)wv[i];
+    cf[i] = d.centre ? (float)d.centre[i] : 0.0f;
+  }
+  H_ALLOC(h->d_w, sizeof(double) * n);
+  H_CALL(cudaMemcpyAsync(h->d_w, wv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, stream));
+  H_ALLOC(h->d_wf, sizeof(float) * np);
+  H_CALL(cudaMemcpyAsync(h->d_wf, wf.data(), sizeof(float) * np, cudaMemcpyHostToDevice, stream));
+  H_ALLOC(h->d_cf, sizeof(float) * np);
+  H_CALL(cudaMemcpyAsync(h->d_cf, cf.data(), sizeof(float) * np, cudaMemcpyHostToDevice, stream));
+  if (d.centre) {
+    H_ALLOC(h->d_c, sizeof(double) * n);
+    H_CALL(cudaMemcpyAsync(h->d_c, d.centre, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
+  }
+  if (d.a_kind == HOPF_A_DIAG) {
+    H_ALLOC(h->d_A, sizeof(double) * n);
+    H_CALL(cudaMemcpyAsync(h->d_A, d.A, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
+    std::vector<float> af(np, 1.0f);
+    for (int i = 0; i < n; ++i) af[i] = (float)d.A[i];
+    H_ALLOC(h->d_af, sizeof(float) * np);
+    H_CALL(cudaMemcpyAsync(h->d_af, af.data(), sizeof(float) * np, cudaMemcpyHostToDevice, stream));
+    H_CALL(cudaStreamSynchronize(stream));
+  } else {
+    hopf_status s = dense_setup(h, d.A, stream);
+    if (s != HOPF_OK) {
+      free_handle(h);
+      return s;
+    }
+  }
+#undef H_ALLOC
+#undef H_CALL
+  *out = h;
+  return HOPF_OK;
+}
+
+void hopf_destroy(hopf_handle h) { free_handle(h); }
+
+hopf_status hopf_workspace_size(hopf_handle h, int64_t batch, size_t* bytes) {
+  set_error("");
+  if (!h || !bytes || batch < 0) return fail(HOPF_EINVAL, "hopf_workspace_size: bad argument");
+  *bytes = h->a_kind == HOPF_A_DIAG ? diag_workspace(h, batch) : dense_workspace(h, batch);
+  return HOPF_OK;
+}
+
+static hopf_status check_eval(hopf_handle h, int64_t batch, const void* x, const void* t, const void* phi,
+                              const void* grad, void* ws, size_t ws_bytes) {
+  if (!h) return fail(HOPF_EINVAL, "hopf_eval: null handle");
+  if (batch < 0) return fail(HOPF_EINVAL, "hopf_eval: negative batch");
+  if (batch > (int64_t)1 << 31) return fail(HOPF_EINVAL, "hopf_eval: batch too large");
+  if (batch == 0) return HOPF_OK;
+  if (!x || !t || !phi || !grad) return fail(HOPF_EINVAL, "hopf_eval: null x, t, phi or grad");
+  size_t need = h->a_kind == HOPF_A_DIAG ? diag_workspace(h, batch) : dense_workspace(h, batch);
+  if (need > 0 && (!ws || ws_bytes < need)) return fail(HOPF_EINVAL, "hopf_eval: workspace too small");
+  if (need > 0 && ((uintptr_t)ws & 255u)) return fail(HOPF_EINVAL, "hopf_eval: workspace must be 256-byte aligned");
+  return HOPF_OK;
+}
+
+hopf_status hopf_eval(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                      float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
+                      cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_eval(h, batch, x, t, phi, grad, workspace, ws_bytes);
+  if (s != HOPF_OK || batch == 0) return s;
+  if (h->precision == HOPF_P_FP64) return fail(HOPF_EINVAL, "hopf_eval: FP64 handle needs hopf_eval_f64");
+  if (h->a_kind == HOPF_A_DIAG) return diag_eval_f32(h, batch, x, t, phi, grad, dphidt, iters, qstatus, stream);
+  DenseWs w;
+  s = dense_carve(h, batch, workspace, ws_bytes, &w);
+  if (s != HOPF_OK) return s;
+  if (h->precision == HOPF_P_FP32) return dense_eval_simt(h, w, x, t, phi, grad, dphidt, iters, qstatus, stream);
+  return dense_eval_tc(h, w, x, t, phi, grad, dphidt, iters, qstatus, stream);
+}
+
+hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
+                          double* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
+                          cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_eval(h, batch, x, t, phi, grad, workspace, ws_bytes);
+  if (s != HOPF_OK || batch == 0) return s;
+  if (h->precision != HOPF_P_FP64 || h->a_kind != HOPF_A_DIAG)
+    return fail(HOPF_EINVAL, "hopf_eval_f64: needs a diagonal FP64 handle");
+  return diag_eval_f64(h, batch, x, t, phi, grad, dphidt, iters, qstatus, stream);
+}
+
+static hopf_status check_parts(const hopf_handle* parts, int32_t K, bool need_l2) {
+  if (!parts || K < 1) return fail(HOPF_EINVAL, "hopf_union: need K >= 1 parts");
+  for (int i = 0; i < K; ++i) {
+    if (!parts[i]) return fail(HOPF_EINVAL, "hopf_union: null part");
+    if (parts[i]->a_kind != HOPF_A_DIAG || parts[i]->precision != HOPF_P_FP32)
+      return fail(HOPF_EUNSUPPORTED, "hopf_union: parts must be diagonal FP32 handles");
+    if (parts[i]->n != parts[0]->n || parts[i]->h_kind != parts[0]->h_kind)
+      return fail(HOPF_EINVAL, "hopf_union: parts must share n and h_kind");
+    if (need_l2 && parts[i]->h_kind != HOPF_H_L2)
+      return fail(HOPF_EINVAL, "hopf_union_closest: parts must use H = l2");
+  }
+  return HOPF_OK;
+}
+
+hopf_status hopf_union_workspace_size(const hopf_handle* parts, int32_t K, int64_t batch, size_t* bytes) {
+  set_error("");
+  hopf_status s = check_parts(parts, K, false);
+  if (s != HOPF_OK) return s;
+  if (!bytes || batch < 0) return fail(HOPF_EINVAL, "hopf_union_workspace_size: bad argument");
+  *bytes = union_workspace(K, parts[0]->n, batch);
+  return HOPF_OK;
+}
+
+hopf_status hopf_union_eval(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, const float* t,
+                            double* phi, float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus,
+                            void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_parts(parts, K, false);
+  if (s != HOPF_OK) return s;
+  if (batch < 0) return fail(HOPF_EINVAL, "hopf_union_eval: negative batch");
+  if (batch == 0) return HOPF_OK;
+  if (!x || !t || !phi || !grad || !argmin) return fail(HOPF_EINVAL, "hopf_union_eval: null output");
+  if (!workspace || ws_bytes < union_workspace(K, parts[0]->n, batch))
+    return fail(HOPF_EINVAL, "hopf_union_eval: workspace too small");
+  return union_eval(parts, K, batch, x, t, phi, grad, argmin, iters, qstatus, workspace, ws_bytes, stream);
+}
+
+hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, float s_tol,
+                               int32_t max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                               uint8_t* qstatus, void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_parts(parts, K, true);
+  if (s != HOPF_OK) return s;
+  if (batch < 0 || max_newton < 1 || !(s_tol > 0)) return fail(HOPF_EINVAL, "hopf_union_closest: bad argument");
+  if (batch == 0) return HOPF_OK;
+  if (!x || !dist || !argmin) return fail(HOPF_EINVAL, "hopf_union_closest: null x, dist or argmin");
+  if (!workspace || ws_bytes < union_workspace(K, parts[0]->n, batch))
+    return fail(HOPF_EINVAL, "hopf_union_closest: workspace too small");
+  return union_closest(parts, K, batch, x, s_tol, max_newton, dist, closest, argmin, newton, qstatus, workspace,
+                       ws_bytes, stream);
+}
+
+hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
+                          float* g_t, float* g_A, cudaStream_t stream) {
+  set_error("");
+  if (!h || batch < 0) return fail(HOPF_EINVAL, "hopf_backward: bad argument");
+  if (batch == 0) {
+    if (g_A) {
+      size_t m = h->a_kind == HOPF_A_DENSE ? (size_t)h->n * h->n : (size_t)h->n;
+      HOPF_CUDA(cudaMemsetAsync(g_A, 0, m * sizeof(float), stream));
+    }
+    return HOPF_OK;
+  }
+  if (!g_phi || !vstar) return fail(HOPF_EINVAL, "hopf_backward: null g_phi or vstar");
+  return backward(h, batch, g_phi, vstar, g_x, g_t, g_A, stream);
+}
+
+}  // extern "C"

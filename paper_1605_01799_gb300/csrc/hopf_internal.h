@@ -1,0 +1,98 @@
+// Internal declarations shared by the translation units of libhopf_gb300.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hopf.h"
+
+struct hopf_handle_s {
+  int n = 0;          // problem dimension
+  int n_pad = 0;      // leading dimension of padded device arrays (multiple of 128)
+  int a_kind = 0, h_kind = 0, precision = 0, stop_rule = 0, max_iter = 0;
+  double c0 = 0, lambda = 1, tol = 0;
+  int device = 0, num_sms = 0;
+  // device copies (FP64 inputs)
+  double* d_A = nullptr;       // diagonal: [n]; dense: [n][n]
+  double* d_c = nullptr;       // [n] or null
+  double* d_w = nullptr;       // [n] (ones when not weighted)
+  float* d_cf = nullptr;       // [n_pad] centre as float (zeros when none)
+  float* d_wf = nullptr;       // [n_pad] weights as float (padding 1)
+  float* d_af = nullptr;       // diagonal A as float [n_pad]
+  // dense derived operands, padded to n_pad x n_pad, row-major
+  double* d_M64 = nullptr;     // (A + lambda I)^{-1}, FP64
+  float* d_M32 = nullptr;      // FP32 copy of M
+  float* d_A32 = nullptr;      // FP32 copy of A
+  uint16_t* d_Mbf = nullptr;   // BF16(M)
+  uint16_t* d_Ah16 = nullptr;  // FP16(A)
+  uint16_t* d_Al16 = nullptr;  // FP16((A - FP16(A)) * 2^11)
+  uint16_t* d_Abf = nullptr;   // BF16(A) (for the BF16 form's final phi pass)
+  cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
+};
+
+namespace hopf {
+
+// thread-local last error
+void set_error(const std::string& msg);
+hopf_status fail(hopf_status s, const std::string& msg);
+hopf_status cuda_fail(cudaError_t e, const char* what);
+
+#define HOPF_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return hopf::cuda_fail(e_, #call); \
+  } while (0)
+
+// ---- setup (setup.cu) ----
+hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream);
+
+// ---- diagonal path (diag.cu) ----
+size_t diag_workspace(const hopf_handle h, int64_t batch);
+hopf_status diag_eval_f32(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+hopf_status diag_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
+                          double* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+size_t union_workspace(int K, int n, int64_t batch);
+hopf_status union_eval(const hopf_handle* parts, int K, int64_t batch, const float* x, const float* t, double* phi,
+                       float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus, void* ws, size_t ws_bytes,
+                       cudaStream_t stream);
+hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
+                          int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                          uint8_t* qstatus, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// ---- dense path ----
+// Workspace shared by the dense solvers.
+struct DenseWs {
+  int64_t B = 0, B_pad = 0;  // batch and its padding to the column tile
+  int rt = 0;                // number of 128-row tiles of n_pad
+  float* y = nullptr;        // [B_pad][n_pad] x - c
+  float* u = nullptr;        // [B_pad][n_pad] d-update argument
+  uint16_t* ph = nullptr;    // [B_pad][n_pad] tensor-core operand 1 (BF16 r, or FP16 split of p)
+  uint16_t* pl = nullptr;    // [B_pad][n_pad] tensor-core operand 2 (FP16 split of p, scaled)
+  uint16_t* g = nullptr;     // [B_pad][n_pad] BF16 residual g
+  float* part = nullptr;     // [2][2][rt][B_pad] residual / norm partials by parity
+  double* fpart = nullptr;   // [2][rt][B_pad] final phi partials
+  float* tau = nullptr;      // [B_pad] t / lambda
+  float* tq = nullptr;       // [B_pad] t
+  float* scale = nullptr;    // [B_pad] l2 prox scale of the current iterate
+  int* qiter = nullptr;      // [B_pad]
+  int* qdone = nullptr;      // [B_pad]
+  unsigned* bar = nullptr;   // [4] grid barrier + counters
+  int* err = nullptr;        // [1]
+};
+size_t dense_workspace(const hopf_handle h, int64_t batch);
+hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_bytes, DenseWs* d);
+hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                            float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+
+// ---- backward (backward.cu) ----
+hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,
+                     float* g_A, cudaStream_t stream);
+
+int sm_count(int device);
+
+}  // namespace hopf

@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every function include/hopf.h declares, and rejects bad arguments
+before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hg():
+    from paper_1605_01799_gb300 import build
+    build.build()
+    import paper_1605_01799_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(hopf_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(hg):
+    names = declared_functions()
+    assert len(names) >= 10
+    L = hg.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(hg.EXPORTS), set(names) ^ set(hg.EXPORTS)
+
+
+def test_version(hg):
+    assert "sm_103a" in hg.version()
+
+
+def _desc(hg, **kw):
+    A = kw.pop("A", np.ones(4))
+    d = dict(n=4, a_kind=0, A=A.ctypes.data, centre=None, c0=0.5, h_kind=0, w=None, lam=1.0, tol=1e-10,
+             max_iter=10, precision=1, stop_rule=0)
+    d.update(kw)
+    return hg.hopf_desc(**d), A
+
+
+@pytest.mark.parametrize("field,value", [("n", 0), ("n", 9000), ("a_kind", 7), ("h_kind", 9), ("lam", 0.0),
+                                         ("lam", -1.0), ("tol", 0.0), ("max_iter", 0), ("precision", 42),
+                                         ("stop_rule", 5)])
+def test_create_rejects_bad_arguments(hg, field, value):
+    d, keep = _desc(hg, **{field: value})
+    h = ctypes.c_void_p()
+    st = hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None)
+    assert st == hg.HOPF_EINVAL
+    assert not h.value
+    assert hg.lib().hopf_last_error().decode()
+
+
+def test_create_rejects_weighted_without_weights(hg):
+    d, keep = _desc(hg, h_kind=1)
+    h = ctypes.c_void_p()
+    assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+
+
+def test_create_rejects_nonpositive_diagonal(hg):
+    d, keep = _desc(hg, A=np.array([1.0, 0.0, 2.0, 3.0]))
+    h = ctypes.c_void_p()
+    assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_ENOTSPD
+
+
+def test_unsupported_combinations(hg):
+    A = np.eye(4)
+    d, keep = _desc(hg, A=A, a_kind=1, precision=0)
+    h = ctypes.c_void_p()
+    assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+    d, keep = _desc(hg, A=A, a_kind=1, precision=1, stop_rule=0)
+    assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+
+
+def test_null_arguments(hg):
+    L = hg.lib()
+    assert L.hopf_create(None, None, None) == hg.HOPF_EINVAL
+    assert L.hopf_eval(None, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
+    assert L.hopf_eval_f64(None, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
+    b = ctypes.c_size_t()
+    assert L.hopf_workspace_size(None, 4, ctypes.byref(b)) == hg.HOPF_EINVAL
+    assert L.hopf_union_eval(None, 0, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
+    assert L.hopf_backward(None, 4, None, None, None, None, None, None) == hg.HOPF_EINVAL
+    L.hopf_destroy(None)

@@ -1,0 +1,130 @@
+"""Dense-A solvers on the GPU against the FP64 oracle (same seeded inputs).
+
+Tolerances.  A = Q diag(s) Q^T with s in [0.1, 10] has condition 100, so an
+FP32 evaluation of A p or M r (relative rounding ~6e-8 per entry) moves the
+fixed point by up to ~cond * 6e-8 ~ 6e-6 relative in the gradient; measured
+errors sit near 1e-6.  phi is stationary in v at the minimiser, so its error
+is second order and FP64 accumulation keeps it near 1e-11 relative.  Bars:
+phi <= 1e-6 relative (floor 1) for every query; gradient <= 5e-6 relative
+(floor 1) for every query and <= 1.5e-6 at the median.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+PHI_TOL, GRAD_MAX, GRAD_MED = 1e-6, 5e-6, 1.5e-6
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1605_01799_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _cuda(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _errors(out, ref):
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    ephi = np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+    eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+    return ephi, eg
+
+
+_REF = {}
+
+
+def _case(orc, n, B, h_kind, seed):
+    key = (n, B, h_kind, seed)
+    if key not in _REF:
+        A, Q, s = wl.spd_matrix(seed, seed + 1, n)
+        w = wl.uniform(seed + 2, n, 0.5, 1.5) if h_kind == 1 else None
+        x = wl.normal(seed + 3, B * n, 2.0).reshape(B, n).astype(np.float32)
+        t = wl.uniform(seed + 4, B, 0.1, 3.0).astype(np.float32)
+        P = orc.Problem(A, h_kind, w=w, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL)
+        ref = P.eval(x.astype(np.float64), t.astype(np.float64))
+        _REF[key] = (A, w, x, t, ref)
+    return _REF[key]
+
+
+@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+@pytest.mark.parametrize("n,B,h_kind", [(128, 300, 1), (200, 129, 1), (384, 257, 0), (256, 64, 2), (129, 1, 1)])
+def test_dense_parity(hg, orc, precision, n, B, h_kind):
+    """Ragged n (not a multiple of the 128-row tile) and ragged batches (not a
+    multiple of the query tile) for each Hamiltonian."""
+    import torch
+    A, w, x, t, ref = _case(orc, n, B, h_kind, 11000 + n + h_kind)
+    prec = getattr(hg, "P_" + precision)
+    try:
+        h = hg.Hopf(A, h_kind, w=w, tol=1e-14, max_iter=3000, precision=prec)
+    except hg.HopfError as e:
+        if e.status == hg.HOPF_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    ephi, eg = _errors(out, ref)
+    assert (out["status"].cpu().numpy() == hg.Q_OK).all()
+    assert ephi.max() <= PHI_TOL, ephi.max()
+    assert eg.max() <= GRAD_MAX, eg.max()
+    assert np.median(eg) <= GRAD_MED, np.median(eg)
+    dphidt = out["dphidt"].cpu().numpy()
+    H = ref["dphidt"]
+    assert np.allclose(dphidt, H, rtol=1e-5, atol=1e-5)
+
+
+def test_dense_iteration_counts(hg, orc):
+    """Same stop rule and tolerance on both sides: the GPU's counts follow the
+    oracle's (FP32 rounding can move a query across the threshold by a step)."""
+    import torch
+    n, B = 128, 200
+    A, w, x, t, ref = _case(orc, n, B, 1, 11500)
+    tol = 1e-12
+    h = hg.Hopf(A, 1, w=w, tol=tol, max_iter=3000, precision=hg.P_FP32)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    same = orc.Problem(A, 1, w=w, tol=tol, max_iter=3000, stop_rule=orc.STOP_UREL).eval(
+        x.astype(np.float64), t.astype(np.float64))
+    it = out["iters"].cpu().numpy()
+    assert np.median(np.abs(it - same["iters"])) <= 1
+    assert np.abs(it - same["iters"]).max() <= 10
+
+
+def test_dense_t_zero_and_not_converged(hg, orc):
+    """t = 0 gives phi = J(x) (eq. 1.1b); a tiny max_iter reports
+    NOT_CONVERGED with iters = max_iter."""
+    import torch
+    n, B = 128, 40
+    A, Q, s = wl.spd_matrix(11601, 11602, n)
+    x = wl.normal(11603, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = np.zeros(B, np.float32)
+    h = hg.Hopf(A, 0, tol=1e-14, max_iter=3000, precision=hg.P_FP32)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    Ainv = (Q / s) @ Q.T
+    xd = x.astype(np.float64)
+    J = 0.5 * np.einsum("bi,ij,bj->b", xd, Ainv, xd) - 0.5
+    assert np.abs(out["phi"].cpu().numpy() - J).max() <= 1e-6 * max(1, np.abs(J).max())
+    h2 = hg.Hopf(A, 0, tol=1e-14, max_iter=3, precision=hg.P_FP32)
+    out = h2.eval(_cuda(x), _cuda(np.full(B, 1.0, np.float32)))
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == hg.Q_NOT_CONVERGED).all()
+    assert (out["iters"].cpu().numpy() == 3).all()
+
+
+def test_dense_not_spd(hg):
+    A = np.eye(64)
+    A[3, 3] = -5.0
+    with pytest.raises(hg.HopfError) as e:
+        hg.Hopf(A, 0, tol=1e-12, max_iter=10, precision=hg.P_FP32)
+    assert e.value.status == hg.HOPF_ENOTSPD

@@ -1,0 +1,126 @@
+"""Diagonal-A path on the GPU against the FP64 oracle (same seeded inputs)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1605_01799_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _cuda(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_workload1_fp64_paper_rule(hg, orc):
+    """n = 8, a_i ~ U[0.5, 2], H = l1, 1,000 queries, FP64, paper stop rule
+    (tol 1e-10, 500 iterations): same iterates as the oracle up to rounding,
+    so phi / grad agree to ~1e-12 and the iteration counts match."""
+    import torch
+    d = wl.diag_l1_fp64()
+    h = hg.Hopf(d["a"], hg.H_L1, tol=d["tol"], max_iter=d["max_iter"], precision=hg.P_FP64,
+                stop_rule=hg.STOP_PAPER)
+    out = h.eval(_cuda(d["x"]), _cuda(d["t"]))
+    torch.cuda.synchronize()
+    ref = orc.Problem(d["a"], orc.H_L1, tol=d["tol"], max_iter=d["max_iter"]).eval(d["x"], d["t"])
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy()
+    assert np.abs(phi - ref["phi"]).max() <= 1e-12 * max(1, np.abs(ref["phi"]).max())
+    assert np.abs(g - ref["grad"]).max() <= 1e-10
+    it = out["iters"].cpu().numpy()
+    assert np.abs(it - ref["iters"]).max() <= 1 and (it == ref["iters"]).mean() >= 0.99
+    assert (out["status"].cpu().numpy() == hg.Q_OK).all()
+    assert np.allclose(out["dphidt"].cpu().numpy(), ref["dphidt"], rtol=1e-12, atol=1e-12)
+    # the workload's own closed form: phi = sum shrink(x_i,t)^2/(2 a_i) - 1/2
+    s = np.sign(d["x"]) * np.maximum(np.abs(d["x"]) - d["t"][:, None], 0)
+    closed = (s * s / (2 * d["a"])).sum(1) - 0.5
+    assert np.abs(phi - closed).max() <= 1e-8 * max(1, np.abs(closed).max())
+
+
+@pytest.mark.parametrize("n", [1, 5, 16, 17, 33, 64, 100, 256, 257, 600, 4096, 5000])
+@pytest.mark.parametrize("h_kind", [0, 1, 2])
+def test_fp32_shapes_and_hamiltonians(hg, orc, n, h_kind):
+    """FP32 kernel at every group shape (thread / warp / CTA per query),
+    ragged n, each Hamiltonian; relative stop rule so iteration counts are
+    comparable.  Tolerance: FP32 state with a_i in [0.5, 2] (condition <= 4):
+    grad error ~ 1e-6 relative, phi (FP64-accumulated) ~ 1e-6 relative."""
+    import torch
+    B = 37 if n >= 4096 else 131
+    seed = 9000 + n * 10 + h_kind
+    a = wl.uniform(seed, n, 0.5, 2.0)
+    w = wl.uniform(seed + 1, n, 0.5, 1.5) if h_kind == 1 else None
+    c = wl.normal(seed + 2, n, 1.0)
+    x = wl.normal(seed + 3, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(seed + 4, B, 0.0, 3.0).astype(np.float32)
+    t[0] = 0.0  # phi(x, 0) = J(x)
+    tol = 1e-12
+    h = hg.Hopf(a, h_kind, w=w, centre=c, tol=tol, max_iter=3000, precision=hg.P_FP32, stop_rule=hg.STOP_UREL)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    P = orc.Problem(a, h_kind, w=w, centre=c, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL)
+    ref = P.eval(x.astype(np.float64), t.astype(np.float64))
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    ephi = np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+    eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+    assert ephi.max() <= 1e-6, ephi.max()
+    assert eg.max() <= 2e-5, eg.max()
+    assert (out["status"].cpu().numpy() == hg.Q_OK).all()
+    # iteration counts against the oracle run with the same rule and tolerance
+    same = orc.Problem(a, h_kind, w=w, centre=c, tol=tol, max_iter=3000, stop_rule=orc.STOP_UREL).eval(
+        x.astype(np.float64), t.astype(np.float64))
+    it = out["iters"].cpu().numpy()
+    assert np.median(np.abs(it - same["iters"])) <= 1
+
+
+def test_paper_rule_fp32_matches_oracle_counts(hg, orc):
+    import torch
+    n, B = 12, 500
+    a = 1.0 + np.arange(n) / (n - 1)  # D_ii = 1 + (i-1)/(n-1), Section 4.5
+    x = wl.uniform(9101, B * n, -10, 10).reshape(B, n).astype(np.float32)
+    t = wl.uniform(9102, B, 0.0, 10.0).astype(np.float32)
+    for hk in (0, 2):
+        h = hg.Hopf(a, hk, tol=1e-8, max_iter=1000, precision=hg.P_FP32, stop_rule=hg.STOP_PAPER)
+        out = h.eval(_cuda(x), _cuda(t))
+        torch.cuda.synchronize()
+        ref = orc.Problem(a, hk, tol=1e-8, max_iter=1000).eval(x.astype(np.float64), t.astype(np.float64))
+        it = out["iters"].cpu().numpy()
+        assert np.abs(it - ref["iters"]).max() <= 2
+        assert (it == ref["iters"]).mean() >= 0.9
+        assert np.allclose(out["phi"].cpu().numpy(), ref["phi"], rtol=1e-5, atol=1e-4)
+
+
+def test_empty_batch_and_single_query(hg, orc):
+    import torch
+    a = np.ones(8)
+    h = hg.Hopf(a, hg.H_L2, tol=1e-12, max_iter=100, precision=hg.P_FP32, stop_rule=hg.STOP_UREL)
+    x0 = torch.zeros(0, 8, dtype=torch.float32, device="cuda")
+    t0 = torch.zeros(0, dtype=torch.float32, device="cuda")
+    out = h.eval(x0, t0)
+    assert out["phi"].numel() == 0
+    x = np.array([[3.0, 0, 0, 4.0, 0, 0, 0, 0]], np.float32)
+    out = h.eval(_cuda(x), _cuda(np.array([1.0], np.float32)))
+    torch.cuda.synchronize()
+    # unit sphere moved by t = 1 (Section 1): phi = 1/2 (|x| - t)^2 - 1/2 = 7.5
+    assert abs(out["phi"].item() - 7.5) <= 1e-5
+
+
+def test_nonfinite_input_reports_status(hg):
+    import torch
+    a = np.ones(4)
+    h = hg.Hopf(a, hg.H_L1, tol=1e-12, max_iter=50, precision=hg.P_FP32, stop_rule=hg.STOP_UREL)
+    x = np.array([[1.0, np.nan, 0.5, 2.0], [1.0, 2.0, 3.0, 4.0]], np.float32)
+    out = h.eval(_cuda(x), _cuda(np.array([0.5, 0.5], np.float32)))
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    assert st[0] == hg.Q_NONFINITE and st[1] == hg.Q_OK
