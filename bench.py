@@ -2,7 +2,7 @@
 
 Workload (default): dense SPD A = Q diag(s) Q^T, n = 1024, s log-uniform in
 [0.1, 10], H = sum w_i |p_i| with w ~ U[0.5, 1.5], 65,536 queries per GPU with
-x ~ N(0, 4I), t ~ U[0.1, 3]; lambda = 1, relative stop 1e-14 on |u^k - u^{k-1}|^2.
+x ~ N(0, 4I), t ~ U[0.1, 3]; lambda = 1, relative stop 1e-13 on |u^k - u^{k-1}|^2.
 One step = one hopf_eval of the whole batch: every split Bregman iteration,
 the final phi pass and the reductions.  Metric: evaluations (phi, grad phi,
 d phi/dt) per second.
@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hopf evals/s (phi, grad phi at 1e-6 rel), n=1024, batch 64K, dense A, weighted l1"
-TOL = 1e-14
+TOL = 1e-13
 MAX_ITER = 1000
 
 
@@ -178,6 +178,10 @@ def main():
 
     # timed region: device-resident inputs (256 MiB per step, larger than L2)
     ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in ev_k:  # torch creates the CUDA event on first record
+        a_.record()
+        b_.record()
+    torch.cuda.synchronize()
     clk_path = tempfile.mktemp(suffix=".csv")
     clk = sample_clocks(clk_path)
     time.sleep(0.5)

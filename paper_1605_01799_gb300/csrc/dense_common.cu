@@ -31,8 +31,10 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 16 
   s[11] = B_pad * 4;                     // qdone
   s[12] = 64;                            // bar (16 unsigned)
   s[13] = 64;                            // err
+  s[14] = B_pad * 4;                     // qact
+  s[15] = (B_pad / 128) * 4;             // tile_act
   size_t total = 0;
-  for (int i = 0; i < 14; ++i) {
+  for (int i = 0; i < 16; ++i) {
     if (out) out[i] = total;
     total += round_up(s[i], 256);
   }
@@ -64,6 +66,8 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
   d->qdone = (int*)(p + off[11]);
   d->bar = (unsigned*)(p + off[12]);
   d->err = (int*)(p + off[13]);
+  d->qact = (int*)(p + off[14]);
+  d->tile_act = (int*)(p + off[15]);
   return HOPF_OK;
 }
 

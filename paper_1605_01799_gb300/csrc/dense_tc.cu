@@ -1,12 +1,736 @@
-// Dense A on the tensor cores (tcgen05): placeholder until the kernel lands.
+// Dense A on the 5th-generation tensor cores (tcgen05 + TMA + TMEM), sm_103a.
+//
+// Two forms of the split Bregman iteration (eq. 3.4(a)-(c)) in terms of the
+// d-update argument u (u^k = v^k + b^{k-1}; p = prox_{(t/lambda)H}(u) is d,
+// b = u - p):
+//
+//  MIXED (defect correction).  With M = (A + lambda I)^{-1} and the identity
+//  M (A + lambda I) = I, the v-update of eq. 3.4(a) becomes
+//     u^{k+1} = u^k + M g^k,   g^k = y - A p^k - lambda (u^k - p^k),
+//  so the fixed point is g = 0 whatever approximation of M the step uses:
+//    phase A:  A p on the tensor cores as a two-term FP16 split,
+//              A p ~ A_hi p_hi + 2^-11 (A_hi p_lo' + A_lo' p_hi)
+//              (A_lo' = fp16((A - A_hi) 2^11), p_lo' likewise), the correction
+//              terms in a second TMEM accumulator scaled exactly in the
+//              epilogue; the epilogue forms g and stores it in BF16;
+//    phase B:  M g with BF16 operands, the epilogue updates u, stores the FP16
+//              split of the next p and the residual partial sums.
+//  BF16 (the paper's form, v = M r with r = y + lambda (2p - u) in BF16): one
+//  phase per iteration.  Its fixed point carries the BF16 error of M r.
+//
+// The start v^0 = d^0 = y, b^0 = 0 (Section 3.1) is u^0 = p^0 = y.  After the
+// last iteration a final pass computes A p (FP16 split) for
+// phi = <y,p> - 1/2 <p, A p> - c0 - t H(p) (FP64 partial sums).
+//
+// One persistent cooperative launch, one CTA per SM, 320 threads:
+//   warp 0   TMA producer (one elected lane), 3-stage shared-memory ring
+//   warp 1   TMEM owner and MMA issuer (one elected lane)
+//   warps 2-9 epilogue: TMEM -> registers -> elementwise update -> global;
+//            two warps per TMEM lane quadrant, each taking half the columns
+// Work item = (128-row tile of n, 128-query column tile); items of a phase
+// are dealt round-robin over CTAs; grid barriers separate the phases.  Every
+// wait is bounded: on timeout the CTA records an error word, drains its own
+// copies and MMAs, frees TMEM and leaves.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "hopf_internal.h"
 
 namespace hopf {
 
-hopf_status dense_eval_tc(hopf_handle, DenseWs&, const float*, const float*, double*, float*, float*, int32_t*,
-                          uint8_t*, cudaStream_t) {
-  return fail(HOPF_EUNSUPPORTED, "tensor-core dense solver not built yet");
+hopf_status dense_init(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s);
+hopf_status dense_finalize(hopf_handle h, DenseWs& w, double* phi, float* dphidt, int32_t* iters, uint8_t* qstatus,
+                           cudaStream_t s);
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;        // 16 KB: 128 rows x 128 bytes
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // up to 2 A tiles + 2 B tiles
+constexpr int NT = 320;                        // 2 role warps + 8 epilogue warps
+constexpr int NEPI = 256;                      // epilogue threads
+constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 accumulators x 128 columns
+constexpr int FORM_MIXED = 0, FORM_BF16 = 1;
+constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3;
+constexpr float kLoScale = 2048.f;             // 2^11: FP16 split scale
+
+struct TcArgs {
+  CUtensorMap mAh, mAl, mM, mP1, mP2, mG;
+  float* y;
+  float* u;
+  uint16_t* p1;
+  uint16_t* p2;
+  uint16_t* g;
+  float* part;
+  double* fpart;
+  float* tau;
+  float* scale;
+  int* qiter;
+  int* qdone;
+  int* qact;
+  int* tile_act;
+  unsigned* bar;
+  int* err;
+  const float* w;
+  float* grad;
+  int64_t B, B_pad;
+  int n, np, rt, ct, h_kind, max_iter, form;
+  float lam, tol;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^32 cycles, or as soon as the CTA aborts.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 32)) {
+      atomicExch(err, ERR_MBAR_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// K-major operand tile in shared memory, 128-byte swizzle: rows of 128 bytes,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, K-major A and B, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt /* 0 = F16, 1 = BF16 */) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+__device__ __forceinline__ float prox1(float u, float w, float tau, float sc, int h_kind) {
+  return h_kind == H_L2 ? sc * u : shrink1(u, tau * w);
+}
+
+// -------------------------------------------------------------- shared state
+struct Smem {
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  uint32_t tmem_base;
+  int abort;
+  int epi_abort;  // snapshot of abort read by all epilogue warps after a barrier
+  int first;
+  float qtau[BN], qscale[BN];
+  int qact[BN];
+  float red[4][BN][2];
+  double redd[4][BN][2];
+};
+
+struct PhaseCfg {
+  int na, nb, nterm;
+  int ta[3], tb[3], td[3];
+  uint32_t idesc;
+};
+
+__device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
+  PhaseCfg c{};
+  if (ph == PH_A || ph == PH_F) {
+    c.na = 2; c.nb = 2; c.nterm = 3;
+    c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // A_hi p_hi     -> D1
+    c.ta[1] = 0; c.tb[1] = 1; c.td[1] = 1;   // A_hi p_lo'    -> D2
+    c.ta[2] = 1; c.tb[2] = 0; c.td[2] = 1;   // A_lo' p_hi    -> D2
+    c.idesc = idesc_f16(0);
+  } else {
+    c.na = 1; c.nb = 1; c.nterm = 1;
+    c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // M (g or r)    -> D1
+    c.idesc = idesc_f16(1);
+  }
+  return c;
+}
+
+__device__ __forceinline__ bool tile_on(const TcArgs& a, int ph, int c) {
+  return ph == PH_F ? ((int64_t)c * BN < a.B) : (a.tile_act[c] > 0);
+}
+
+// ------------------------------------------------------------ role: producer
+struct ProdState {
+  uint32_t kb = 0;                 // k-blocks issued so far (ring position)
+  uint32_t last_par[STAGES];       // parity of the last load issued into each stage
+  bool used[STAGES];
+};
+
+// BF16 form: r^{k-1} lives in buffer (k-1) & 1 (p1 = buffer 0, p2 = buffer 1)
+// and the epilogue of iteration k writes r^k into the other one, so no CTA
+// overwrites an operand another CTA may still be loading.
+__device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, int k, ProdState& st) {
+  const PhaseCfg cfg = phase_cfg(ph);
+  const CUtensorMap* A0 = (ph == PH_A || ph == PH_F) ? &a.mAh : &a.mM;
+  const CUtensorMap* A1 = &a.mAl;
+  const CUtensorMap* B0 = (ph == PH_A || ph == PH_F) ? &a.mP1 : (ph == PH_B ? &a.mG : (((k - 1) & 1) ? &a.mP2 : &a.mP1));
+  const CUtensorMap* B1 = &a.mP2;
+  const uint32_t bytes = (uint32_t)(cfg.na + cfg.nb) * TILE_BYTES;
+  const int nk = a.np / BK, items = a.rt * a.ct;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int r = it % a.rt, c = it / a.rt;
+    if (!tile_on(a, ph, c)) continue;
+    for (int kb = 0; kb < nk; ++kb, ++st.kb) {
+      const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
+      if (!mbar_wait(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort)) return;
+      const uint32_t full = sa(&S.full[s]);
+      mbar_expect_tx(full, bytes);
+      uint8_t* base = stages + (size_t)s * STAGE_BYTES;
+      const int kx = kb * BK;
+      tma_load(sa(base), A0, full, kx, r * BM);
+      if (cfg.na > 1) tma_load(sa(base + TILE_BYTES), A1, full, kx, r * BM);
+      tma_load(sa(base + 2 * TILE_BYTES), B0, full, kx, c * BN);
+      if (cfg.nb > 1) tma_load(sa(base + 3 * TILE_BYTES), B1, full, kx, c * BN);
+      st.last_par[s] = use & 1;
+      st.used[s] = true;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- role: MMA
+struct MmaState {
+  uint32_t kb = 0;    // k-blocks consumed
+  uint32_t item = 0;  // accumulator tiles produced
+  bool issued = false;
+};
+
+__device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, MmaState& st) {
+  const PhaseCfg cfg = phase_cfg(ph);
+  const int nk = a.np / BK, items = a.rt * a.ct;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int c = it / a.rt;
+    if (!tile_on(a, ph, c)) continue;
+    const uint32_t buf = st.item & 1, use = st.item >> 1;
+    if (!mbar_wait(sa(&S.tempty[buf]), (use & 1) ^ 1, a.err, &S.abort)) return;
+    tc_fence_after();
+    const uint32_t d0 = S.tmem_base + buf * 256;
+    for (int kb = 0; kb < nk; ++kb, ++st.kb) {
+      const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
+      if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
+      tc_fence_after();
+      const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int tm = 0; tm < cfg.nterm; ++tm) {
+          const uint64_t ad = smem_desc(base + cfg.ta[tm] * TILE_BYTES) + (uint64_t)(kk * 2);
+          const uint64_t bd = smem_desc(base + (2 + cfg.tb[tm]) * TILE_BYTES) + (uint64_t)(kk * 2);
+          // the first product into an accumulator overwrites it
+          const bool first_into = (kb == 0 && kk == 0) && (tm == 0 || cfg.td[tm] != cfg.td[tm - 1]);
+          mma_f16(d0 + cfg.td[tm] * BN, ad, bd, cfg.idesc, first_into ? 0u : 1u);
+        }
+      }
+      st.issued = true;
+      mma_commit(sa(&S.empty[s]));  // frees the stage once these MMAs have read it
+    }
+    mma_commit(sa(&S.tfull[buf]));  // accumulator ready for the epilogue
+    ++st.item;
+  }
+}
+
+// ------------------------------------------------------------ role: epilogue
+struct EpiState {
+  uint32_t item = 0;
+};
+
+// Load the per-query data of column tile c into shared memory.
+__device__ void epi_stage_queries(const TcArgs& a, Smem& S, int ph, int c, int k, int et) {
+  if (et >= BN) return;
+  const int64_t q = (int64_t)c * BN + et;
+  S.qtau[et] = a.tau[q];
+  S.qscale[et] = a.scale[q];
+  S.qact[et] = ph == PH_F ? (q < a.B) : a.qact[q];
+  if (et == 0) S.first = (ph != PH_F) && k == 1;
+}
+
+// Transpose-reduce: lane L holds v[0..31] (one value per column for its row);
+// on return v[0] of lane L is the sum over the 32 lanes of column L.  Each
+// halving step keeps one half of the columns and exchanges the other half
+// with the partner lane: 16 + 8 + 4 + 2 + 1 = 31 shuffles for 32 columns.
+__device__ __forceinline__ void transpose_reduce32(float v[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+__device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState& st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int et = threadIdx.x - 64;      // 0..255
+  const int qd = warp & 3;              // TMEM lane quadrant of this warp
+  const int jbase = ((warp - 2) >> 2) * (BN / 2);  // this warp's half of the columns
+  const int rloc = qd * 32 + lane;      // row within the tile
+  const int items = a.rt * a.ct;
+  const int np = a.np, hk = a.h_kind;
+  const float lam = a.lam;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int r = it % a.rt, c = it / a.rt;
+    if (!tile_on(a, ph, c)) continue;
+    const uint32_t buf = st.item & 1, use = st.item >> 1;
+    ++st.item;
+    epi_sync();  // previous item's readers of the shared query data are done
+    epi_stage_queries(a, S, ph, c, k, et);
+    if (et == 0) S.epi_abort = S.abort;
+    epi_sync();
+    if (S.epi_abort) return;  // the same decision in all eight warps
+    // a failed wait skips the work of this item but keeps the warp in step
+    // with the others at the named barriers below
+    const bool good = mbar_wait(sa(&S.tfull[buf]), use & 1, a.err, &S.abort);
+    if (good) tc_fence_after();
+    const int row = r * BM + rloc;
+    const float wr = a.w[row];
+    const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
+    const bool first = S.first;
+    for (int j0 = jbase; good && j0 < jbase + BN / 2; j0 += 32) {
+      float d1[32], d2[32];
+      tmem_ld32(tbase + j0, d1);
+      if (ph == PH_A || ph == PH_F) tmem_ld32(tbase + BN + j0, d2);
+      if (ph == PH_A) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int j = j0 + jj;
+          if (!S.qact[j]) continue;
+          const int64_t off = ((int64_t)c * BN + j) * np + row;
+          const float uu = a.u[off], yy = __ldg(a.y + off);
+          const float tau = S.qtau[j], sc = S.qscale[j];
+          const float p = first ? yy : prox1(uu, wr, tau, sc, hk);
+          float ap = d1[jj] + d2[jj] * (1.f / kLoScale);
+          if (hk == H_L2 && !first) ap *= sc;  // l2: the operand held u, p = sc u
+          const float g = yy - ap - lam * (uu - p);
+          a.g[off] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+        }
+      } else if (ph == PH_B || ph == PH_P) {
+        float v0[32], v1[32];
+        uint16_t* rbuf = (k & 1) ? a.p2 : a.p1;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int j = j0 + jj;
+          v0[jj] = 0.f;
+          v1[jj] = 0.f;
+          if (!S.qact[j]) continue;
+          const int64_t off = ((int64_t)c * BN + j) * np + row;
+          const float uu = a.u[off];
+          const float tau = S.qtau[j];
+          float un;
+          if (ph == PH_B) {
+            un = uu + d1[jj];
+            const float pn = hk == H_L2 ? un : shrink1(un, tau * wr);
+            const __half hi = __float2half_rn(pn);
+            a.p1[off] = __half_as_ushort(hi);
+            a.p2[off] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
+          } else {
+            const float yy = __ldg(a.y + off);
+            const float p = first ? yy : prox1(uu, wr, tau, S.qscale[j], hk);
+            un = d1[jj] + uu - p;
+            const float pn = prox1(un, wr, tau, 1.f, hk);
+            rbuf[off] = __bfloat16_as_ushort(__float2bfloat16_rn(yy + lam * (2.f * pn - un)));
+          }
+          a.u[off] = un;
+          v0[jj] = (un - uu) * (un - uu);
+          v1[jj] = un * un;
+        }
+        transpose_reduce32(v0, lane);
+        transpose_reduce32(v1, lane);
+        S.red[qd][j0 + lane][0] = v0[0];
+        S.red[qd][j0 + lane][1] = v1[0];
+      } else {  // PH_F: phi partials and the gradient
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int j = j0 + jj;
+          double f0 = 0.0, f1 = 0.0;
+          if (S.qact[j]) {
+            const int64_t q = (int64_t)c * BN + j;
+            const int64_t off = q * np + row;
+            const float uu = a.u[off], yy = a.y[off];
+            const float sc = S.qscale[j];
+            const float p = prox1(uu, wr, S.qtau[j], sc, hk);
+            float ap = d1[jj] + d2[jj] * (1.f / kLoScale);
+            if (hk == H_L2) ap *= sc;
+            const double pd = p;
+            f0 = (double)yy * pd - 0.5 * pd * (double)ap;
+            f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
+            if (row < a.n) a.grad[q * a.n + row] = p;
+          }
+          f0 = warp_sum(f0);
+          f1 = warp_sum(f1);
+          if (lane == 0) {
+            S.redd[qd][j][0] = f0;
+            S.redd[qd][j][1] = f1;
+          }
+        }
+      }
+    }
+    // release the accumulator buffer to the MMA warp
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
+    if (ph != PH_A) {
+      epi_sync();
+      if (et < BN) {
+        const int64_t q = (int64_t)c * BN + et;
+        if (ph == PH_F) {
+          const double s0 = S.redd[0][et][0] + S.redd[1][et][0] + S.redd[2][et][0] + S.redd[3][et][0];
+          const double s1 = S.redd[0][et][1] + S.redd[1][et][1] + S.redd[2][et][1] + S.redd[3][et][1];
+          a.fpart[(int64_t)r * a.B_pad + q] = s0;
+          a.fpart[(int64_t)(a.rt + r) * a.B_pad + q] = s1;
+        } else if (S.qact[et]) {
+          const float s0 = S.red[0][et][0] + S.red[1][et][0] + S.red[2][et][0] + S.red[3][et][0];
+          const float s1 = S.red[0][et][1] + S.red[1][et][1] + S.red[2][et][1] + S.red[3][et][1];
+          const int par = k & 1;
+          a.part[((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
+          a.part[((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
+        }
+      }
+    }
+  }
+}
+
+// Decision for iteration k (convergence of iteration k-1), one thread per
+// query of a column tile; the epilogue warps of every CTA share the tiles.
+__device__ void prepass(const TcArgs& a, Smem& S, int k) {
+  const int et = threadIdx.x - 64;
+  for (int c = blockIdx.x; c < a.ct; c += gridDim.x) {
+    if (et < BN) {
+      const int64_t q = (int64_t)c * BN + et;
+      int act = 0;
+      if (k == 1) {
+        act = q < a.B;
+        a.scale[q] = 1.f;
+      } else if (!a.qdone[q]) {
+        const int par = (k - 1) & 1;
+        float du2 = 0.f, nu2 = 0.f;
+        for (int rr = 0; rr < a.rt; ++rr) {
+          du2 += a.part[((int64_t)(par * 2 + 0) * a.rt + rr) * a.B_pad + q];
+          nu2 += a.part[((int64_t)(par * 2 + 1) * a.rt + rr) * a.B_pad + q];
+        }
+        const int kprev = k - 1;
+        a.scale[q] = shrink2_scale(sqrtf(nu2), a.tau[q]);
+        if (kprev >= 2 && du2 <= a.tol * fmaxf(1.f, nu2)) {
+          a.qdone[q] = 1;
+          a.qiter[q] = kprev;
+        } else if (kprev >= a.max_iter) {
+          a.qdone[q] = 2;
+          a.qiter[q] = a.max_iter;
+        } else {
+          act = 1;
+        }
+      }
+      a.qact[q] = act;
+      const int cnt = __reduce_add_sync(0xffffffffu, act);
+      if ((et & 31) == 0) S.red[et >> 5][0][0] = __int_as_float(cnt);
+    }
+    epi_sync();
+    if (et == 0) {
+      int tot = 0;
+      for (int i = 0; i < 4; ++i) tot += __float_as_int(S.red[i][0][0]);
+      a.tile_act[c] = tot;
+      if (tot) atomicAdd(a.bar + 2 + (k % 3), (unsigned)tot);
+    }
+    epi_sync();
+  }
+}
+
+// BF16 form, before the final pass: FP16 split of p = prox(u) for every query.
+__device__ void prep_final_operand(const TcArgs& a) {
+  const int64_t total = a.B_pad * a.np;
+  const int64_t stride = (int64_t)gridDim.x * NEPI;
+  for (int64_t i = (int64_t)blockIdx.x * NEPI + (threadIdx.x - 64); i < total; i += stride) {
+    const int64_t q = i / a.np;
+    const int row = (int)(i % a.np);
+    const float uu = a.u[i];
+    const float pn = a.h_kind == H_L2 ? uu : shrink1(uu, a.tau[q] * a.w[row]);
+    const __half hi = __float2half_rn(pn);
+    a.p1[i] = __half_as_ushort(hi);
+    a.p2[i] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Smem& S = *reinterpret_cast<Smem*>(stages + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(sa(&S.full[s]), 1);
+      mbar_init(sa(&S.empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(sa(&S.tfull[b]), 1);
+      mbar_init(sa(&S.tempty[b]), 8);
+    }
+    mbar_init(sa(&S.drain), 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.mAh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.mM)) : "memory");
+  }
+
+  ProdState ps;
+  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
+  MmaState ms;
+  EpiState es;
+  auto run = [&](int ph, int k) {
+    if (warp == 0) {
+      if (lane == 0) {
+        proxy_fence_global();  // generic-proxy writes of the last phase, then TMA reads
+        producer_phase(a, S, stages, ph, k, ps);
+      }
+    } else if (warp == 1) {
+      if (lane == 0) mma_phase(a, S, stages, ph, ms);
+    } else {
+      epilogue_phase(a, S, ph, k, es);
+      proxy_fence_global();
+    }
+  };
+
+  bool ok = true;
+  for (int k = 1; ok; ++k) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
+    if (warp >= 2) prepass(a, S, k);
+    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+    if (ld_acquire_u32(a.bar + 2 + (k % 3)) == 0) break;
+    if (a.form == FORM_MIXED) {
+      run(PH_A, k);
+      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+      run(PH_B, k);
+    } else {
+      run(PH_P, k);
+    }
+    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+  }
+  if (ok && a.form == FORM_BF16) {
+    if (warp >= 2) prep_final_operand(a);
+    proxy_fence_global();
+    ok = grid_barrier(a.bar, gridDim.x, a.err);
+  }
+  if (ok) run(PH_F, 0);
+
+  // drain: no copy or MMA of this CTA may be in flight when TMEM is freed
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s)
+      if (ps.used[s]) {
+        const long long t0 = clock64();
+        while (!mbar_test(sa(&S.full[s]), ps.last_par[s]) && clock64() - t0 < (1ll << 31)) {
+        }
+      }
+  }
+  if (warp == 1 && lane == 0 && ms.issued) {
+    mma_commit(sa(&S.drain));
+    const long long t0 = clock64();
+    while (!mbar_test(sa(&S.drain), 0) && clock64() - t0 < (1ll << 31)) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  }
+  return fn;
+}
+
+// 2-D tensor [rows][np] of 16-bit elements, box 128 rows x 64 elements.
+static bool encode(CUtensorMap* m, const void* ptr, int64_t rows, int np, bool bf16) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)np * 2};
+  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// FP16 split of y (MIXED: p^0 = y) or BF16 r^0 = y + lambda y (BF16 form).
+__global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restrict__ p1, uint16_t* __restrict__ p2,
+                                  int64_t total, int form, float lam) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = y[i];
+    if (form == FORM_MIXED) {
+      const __half hi = __float2half_rn(v);
+      p1[i] = __half_as_ushort(hi);
+      p2[i] = __half_as_ushort(__float2half_rn((v - __half2float(hi)) * kLoScale));
+    } else {
+      p1[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v + lam * v));
+    }
+  }
+}
+
+}  // namespace tc
+
+hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
+  using namespace tc;
+  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : FORM_BF16;
+  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
+    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
+  hopf_status s = dense_init(h, w, x, t, stream);
+  if (s != HOPF_OK) return s;
+  const int64_t total = w.B_pad * h->n_pad;
+  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda);
+  HOPF_CUDA(cudaGetLastError());
+
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  const int np = h->n_pad;
+  bool ok = encode(&a.mAh, h->d_Ah16, np, np, false) && encode(&a.mAl, h->d_Al16, np, np, false) &&
+            encode(&a.mM, h->d_Mbf, np, np, true) &&
+            encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
+            encode(&a.mG, w.g, w.B_pad, np, true);
+  if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
+  a.y = w.y;
+  a.u = w.u;
+  a.p1 = w.ph;
+  a.p2 = w.pl;
+  a.g = w.g;
+  a.part = w.part;
+  a.fpart = w.fpart;
+  a.tau = w.tau;
+  a.scale = w.scale;
+  a.qiter = w.qiter;
+  a.qdone = w.qdone;
+  a.qact = w.qact;
+  a.tile_act = w.tile_act;
+  a.bar = w.bar;
+  a.err = w.err;
+  a.w = h->d_wf;
+  a.grad = grad;
+  a.B = w.B;
+  a.B_pad = w.B_pad;
+  a.n = h->n;
+  a.np = np;
+  a.rt = np / BM;
+  a.ct = (int)(w.B_pad / BN);
+  a.h_kind = h->h_kind;
+  a.max_iter = h->max_iter;
+  a.form = form;
+  a.lam = (float)h->lambda;
+  a.tol = (float)h->tol;
+
+  const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + sizeof(Smem);
+  HOPF_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc, NT, smem));
+  if (per_sm < 1) return fail(HOPF_ECUDA, "dense tensor-core solver: kernel does not fit on an SM");
+  const int grid = h->num_sms;  // one CTA per SM: each holds all 512 TMEM columns
+  void* args[] = {&a};
+  if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
+  HOPF_CUDA(cudaLaunchCooperativeKernel((const void*)k_dense_tc, dim3(grid), dim3(NT), args, smem, stream));
+  if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
+  return dense_finalize(h, w, phi, dphidt, iters, qstatus, stream);
 }
 
 }  // namespace hopf

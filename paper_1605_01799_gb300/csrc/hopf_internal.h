@@ -79,6 +79,8 @@ struct DenseWs {
   float* scale = nullptr;    // [B_pad] l2 prox scale of the current iterate
   int* qiter = nullptr;      // [B_pad]
   int* qdone = nullptr;      // [B_pad]
+  int* qact = nullptr;       // [B_pad] updated in the current iteration
+  int* tile_act = nullptr;   // [B_pad / 128] active queries per column tile
   unsigned* bar = nullptr;   // [4] grid barrier + counters
   int* err = nullptr;        // [1]
 };

@@ -31,7 +31,7 @@ def test_backward_dense_matches_oracle(hg, orc, n, B):
     x = wl.normal(12003, B * n, 2.0).reshape(B, n).astype(np.float32)
     t = wl.uniform(12004, B, 0.1, 3.0).astype(np.float32)
     g = wl.normal(12005, B, 1.0).astype(np.float32)
-    h = hg.Hopf(A, hg.H_L1, tol=1e-14, max_iter=3000, precision=hg.P_FP32)
+    h = hg.Hopf(A, hg.H_L1, tol=1e-13, max_iter=3000, precision=hg.P_FP32)
     out = h.eval(_cuda(x), _cuda(t))
     gx, gt, gA = h.backward(_cuda(g), out["grad"])
     torch.cuda.synchronize()
@@ -70,7 +70,7 @@ def test_backward_fd_on_sampled_queries(hg, orc):
     A, Q, s = wl.spd_matrix(12201, 12202, n)
     x = wl.normal(12203, B * n, 2.0).reshape(B, n).astype(np.float32)
     t = wl.uniform(12204, B, 0.1, 3.0).astype(np.float32)
-    h = hg.Hopf(A, hg.H_L1, tol=1e-14, max_iter=3000, precision=hg.P_FP32)
+    h = hg.Hopf(A, hg.H_L1, tol=1e-13, max_iter=3000, precision=hg.P_FP32)
     out = h.eval(_cuda(x), _cuda(t))
     v_gpu = out["grad"].cpu().numpy().astype(np.float64)
     w = np.ones(n)

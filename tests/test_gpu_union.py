@@ -54,7 +54,9 @@ def test_union_phi(hg, orc, n, K, B):
     g = out["grad"].cpu().numpy().astype(np.float64)
     ok = ~diff
     eg = np.linalg.norm(g[ok] - ref["grad"][ok], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"][ok], axis=1))
-    assert eg.max() <= 2e-5, eg.max()
+    # semi-axes in [0.2, 5] give A = diag(semi^2) a condition up to 625, and the
+    # FP32 gradient moves by up to ~cond * 6e-8 relative
+    assert eg.max() <= 1e-4, eg.max()
     assert (out["status"].cpu().numpy() == hg.Q_OK).all()
 
 
@@ -77,7 +79,9 @@ def test_closest_point(hg, orc):
                 best, bk, bp = dk, k, p + d["centres"][k]
         assert abs(dist[q] - best) <= 1e-5 * max(1, best), (q, dist[q], best)
         if am[q] == bk:
-            assert np.abs(cl[q] - bp).max() <= 1e-4 * max(1, np.abs(bp).max())
+            # closest = x - s grad/|grad|: the FP32 direction error (~cond * 6e-8
+            # with cond <= 625, times a safety factor) is scaled by s (<= ~15)
+            assert np.abs(cl[q] - bp).max() <= 1e-3 * max(1, np.abs(bp).max())
     # and the oracle's own Newton-on-s route agrees
     ref = orc.union_closest(oparts, d["x"].astype(np.float64), s_tol=1e-12, max_newton=100)
     assert np.abs(dist - ref["dist"]).max() <= 1e-5 * max(1, np.abs(ref["dist"]).max())
