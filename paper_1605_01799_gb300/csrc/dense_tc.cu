@@ -335,7 +335,8 @@ __device__ __forceinline__ void transpose_reduce32(float v[32], int lane) {
   }
 }
 
-__device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState& st) {
+template <int ph>
+__device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;      // 0..255
   const int qd = warp & 3;              // TMEM lane quadrant of this warp
@@ -363,57 +364,91 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
     const bool first = S.first;
     for (int j0 = jbase; good && j0 < jbase + BN / 2; j0 += 32) {
-      float d1[32], d2[32];
+      float d1[32];
       tmem_ld32(tbase + j0, d1);
-      if (ph == PH_A || ph == PH_F) tmem_ld32(tbase + BN + j0, d2);
-      if (ph == PH_A) {
+      if constexpr (ph == PH_A || ph == PH_F) {
+        // A p = D1 + 2^-11 D2: fold the correction accumulator in right away
+        float d2[32];
+        tmem_ld32(tbase + BN + j0, d2);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) d1[jj] += d2[jj] * (1.f / kLoScale);
+      }
+      // active queries of this 32-column chunk as a bit mask
+      const uint32_t am = __ballot_sync(0xffffffffu, S.qact[j0 + lane] != 0);
+      const float* ucol = a.u + ((int64_t)c * BN + j0) * np + row;
+      const float* ycol = a.y + ((int64_t)c * BN + j0) * np + row;
+      if constexpr (ph == PH_A) {
+        // all loads first (independent, in flight together), then the stores
+        float uu[32], yy[32];
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
-          const int j = j0 + jj;
-          if (!S.qact[j]) continue;
-          const int64_t off = ((int64_t)c * BN + j) * np + row;
-          const float uu = a.u[off], yy = __ldg(a.y + off);
-          const float tau = S.qtau[j], sc = S.qscale[j];
-          const float p = first ? yy : prox1(uu, wr, tau, sc, hk);
-          float ap = d1[jj] + d2[jj] * (1.f / kLoScale);
-          if (hk == H_L2 && !first) ap *= sc;  // l2: the operand held u, p = sc u
-          const float g = yy - ap - lam * (uu - p);
-          a.g[off] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+          uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
+          yy[jj] = (am >> jj & 1u) ? __ldg(ycol + (int64_t)jj * np) : 0.f;
         }
-      } else if (ph == PH_B || ph == PH_P) {
-        float v0[32], v1[32];
-        uint16_t* rbuf = (k & 1) ? a.p2 : a.p1;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
+          if (!(am >> jj & 1u)) continue;
           const int j = j0 + jj;
-          v0[jj] = 0.f;
-          v1[jj] = 0.f;
-          if (!S.qact[j]) continue;
-          const int64_t off = ((int64_t)c * BN + j) * np + row;
-          const float uu = a.u[off];
-          const float tau = S.qtau[j];
-          float un;
-          if (ph == PH_B) {
-            un = uu + d1[jj];
-            const float pn = hk == H_L2 ? un : shrink1(un, tau * wr);
+          const float tau = S.qtau[j], sc = S.qscale[j];
+          const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, sc, hk);
+          float ap = d1[jj];
+          if (hk == H_L2 && !first) ap *= sc;  // l2: the operand held u, p = sc u
+          const float g = yy[jj] - ap - lam * (uu[jj] - p);
+          a.g[((int64_t)c * BN + j) * np + row] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+        }
+      } else if constexpr (ph == PH_B) {
+        // d1 becomes |u^k - u^{k-1}|^2 and uu becomes |u^k|^2 in place
+        float uu[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const float du = (am >> jj & 1u) ? d1[jj] : 0.f;
+          const float un = uu[jj] + du;
+          if (am >> jj & 1u) {
+            const int64_t off = ((int64_t)c * BN + j0 + jj) * np + row;
+            const float pn = hk == H_L2 ? un : shrink1(un, S.qtau[j0 + jj] * wr);
             const __half hi = __float2half_rn(pn);
             a.p1[off] = __half_as_ushort(hi);
             a.p2[off] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
-          } else {
-            const float yy = __ldg(a.y + off);
-            const float p = first ? yy : prox1(uu, wr, tau, S.qscale[j], hk);
-            un = d1[jj] + uu - p;
-            const float pn = prox1(un, wr, tau, 1.f, hk);
-            rbuf[off] = __bfloat16_as_ushort(__float2bfloat16_rn(yy + lam * (2.f * pn - un)));
+            a.u[off] = un;
           }
-          a.u[off] = un;
-          v0[jj] = (un - uu) * (un - uu);
-          v1[jj] = un * un;
+          d1[jj] = du * du;
+          uu[jj] = (am >> jj & 1u) ? un * un : 0.f;
         }
-        transpose_reduce32(v0, lane);
-        transpose_reduce32(v1, lane);
-        S.red[qd][j0 + lane][0] = v0[0];
-        S.red[qd][j0 + lane][1] = v1[0];
+        transpose_reduce32(d1, lane);
+        transpose_reduce32(uu, lane);
+        S.red[qd][j0 + lane][0] = d1[0];
+        S.red[qd][j0 + lane][1] = uu[0];
+      } else if constexpr (ph == PH_P) {
+        float uu[32], yy[32];
+        uint16_t* rbuf = (k & 1) ? a.p2 : a.p1;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
+          yy[jj] = (am >> jj & 1u) ? __ldg(ycol + (int64_t)jj * np) : 0.f;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          float du = 0.f, un = 0.f;
+          if (am >> jj & 1u) {
+            const int j = j0 + jj;
+            const int64_t off = ((int64_t)c * BN + j) * np + row;
+            const float tau = S.qtau[j];
+            const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, S.qscale[j], hk);
+            un = d1[jj] + uu[jj] - p;
+            du = un - uu[jj];
+            const float pn = prox1(un, wr, tau, 1.f, hk);
+            rbuf[off] = __bfloat16_as_ushort(__float2bfloat16_rn(yy[jj] + lam * (2.f * pn - un)));
+            a.u[off] = un;
+          }
+          d1[jj] = du * du;
+          uu[jj] = un * un;
+        }
+        transpose_reduce32(d1, lane);
+        transpose_reduce32(uu, lane);
+        S.red[qd][j0 + lane][0] = d1[0];
+        S.red[qd][j0 + lane][1] = uu[0];
       } else {  // PH_F: phi partials and the gradient
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
@@ -425,7 +460,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState
             const float uu = a.u[off], yy = a.y[off];
             const float sc = S.qscale[j];
             const float p = prox1(uu, wr, S.qtau[j], sc, hk);
-            float ap = d1[jj] + d2[jj] * (1.f / kLoScale);
+            float ap = d1[jj];
             if (hk == H_L2) ap *= sc;
             const double pd = p;
             f0 = (double)yy * pd - 0.5 * pd * (double)ap;
@@ -445,11 +480,11 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
-    if (ph != PH_A) {
+    if constexpr (ph != PH_A) {
       epi_sync();
       if (et < BN) {
         const int64_t q = (int64_t)c * BN + et;
-        if (ph == PH_F) {
+        if constexpr (ph == PH_F) {
           const double s0 = S.redd[0][et][0] + S.redd[1][et][0] + S.redd[2][et][0] + S.redd[3][et][0];
           const double s1 = S.redd[0][et][1] + S.redd[1][et][1] + S.redd[2][et][1] + S.redd[3][et][1];
           a.fpart[(int64_t)r * a.B_pad + q] = s0;
@@ -464,6 +499,12 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int ph, int k, EpiState
       }
     }
   }
+}
+
+// The final pass runs once per call: kept out of line so its FP64 registers do
+// not weigh on the per-iteration epilogues.
+__device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, EpiState& st) {
+  epilogue_phase<PH_F>(a, S, 0, st);
 }
 
 // Decision for iteration k (convergence of iteration k-1), one thread per
@@ -526,6 +567,7 @@ __device__ void prep_final_operand(const TcArgs& a) {
   }
 }
 
+// 10 warps: 3 share a sub-partition's 16,384 registers, hence 168 per thread.
 __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -572,7 +614,10 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     } else if (warp == 1) {
       if (lane == 0) mma_phase(a, S, stages, ph, ms);
     } else {
-      epilogue_phase(a, S, ph, k, es);
+      if (ph == PH_A) epilogue_phase<PH_A>(a, S, k, es);
+      else if (ph == PH_B) epilogue_phase<PH_B>(a, S, k, es);
+      else if (ph == PH_P) epilogue_phase<PH_P>(a, S, k, es);
+      else epilogue_final(a, S, es);
       proxy_fence_global();
     }
   };
