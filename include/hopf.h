@@ -176,6 +176,23 @@ hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batc
                                int32_t max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
                                uint8_t* qstatus, void* workspace, size_t ws_bytes, cudaStream_t stream);
 
+/* hopf_union_closest without any allocation, for callers that may not call
+ * cudaMalloc once running: a controller that queries distances to obstacles
+ * at a fixed rate, code inside a fixed memory budget, or a host that gives the
+ * library no allocator.  (The paper has no counterpart: this is a property of
+ * the library, not of the method.)  Same arguments and results as
+ * hopf_union_closest, minus the workspace: the scratch is one static 8 MiB
+ * device array that every GPU which loads the library holds until the
+ * process exits, so batch * K may not exceed about 490,000 query-part pairs
+ * (larger requests return HOPF_EINVAL and launch nothing).  The first call on
+ * a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (nothing in it needs to start at
+ * zero): calls that overlap on the GPU race, so serialise them. */
+hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int64_t batch, const float* x,
+                                       float s_tol, int32_t max_newton, float* dist, float* closest, int32_t* argmin,
+                                       int32_t* newton, uint8_t* qstatus, cudaStream_t stream);
+
 /* Gradients of phi with respect to the data by the envelope theorem applied
  * to eq. 3.3 (v* = grad, the minimiser): with upstream weights g_phi[q],
  *   g_x[q]  = g_phi[q] v*_q                  ([batch][n] float, may be NULL)

@@ -26,7 +26,8 @@ STOP_PAPER, STOP_UREL = 0, 1
 Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
 
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
-           "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_backward",
+           "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
+           "hopf_backward",
            "hopf_profile_events", "hopf_last_error", "hopf_version"]
 
 
@@ -64,6 +65,8 @@ def lib():
             "hopf_union_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_union_closest": ([_vp, _i32, _i64, _vp, _f32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
                                    ctypes.c_int),
+            "hopf_union_closest_noalloc": ([_vp, _i32, _i64, _vp, _f32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
+                                           ctypes.c_int),
             "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
@@ -222,6 +225,25 @@ def union_closest(parts, x, s_tol=1e-6, max_newton=50, stream=None):
     _check(lib().hopf_union_closest(arr, len(parts), B, _ptr(x), float(s_tol), int(max_newton), _ptr(out["dist"]),
                                     _ptr(out["closest"]), _ptr(out["argmin"]), _ptr(out["newton"]),
                                     _ptr(out["status"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def union_closest_noalloc(parts, x, s_tol=1e-6, max_newton=50, out=None, stream=None):
+    """union_closest without allocation inside the library (static scratch of
+    8 MiB: batch * len(parts) up to about 490,000).  Pass preallocated
+    ``out`` tensors to keep the whole call allocation-free."""
+    import torch
+    B, n = x.shape
+    arr = _parts_array(parts)
+    if out is None:
+        out = {"dist": torch.empty(B, dtype=torch.float32, device=x.device),
+               "closest": torch.empty(B, n, dtype=torch.float32, device=x.device),
+               "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
+               "newton": torch.empty(B, dtype=torch.int32, device=x.device),
+               "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    _check(lib().hopf_union_closest_noalloc(arr, len(parts), B, _ptr(x), float(s_tol), int(max_newton),
+                                            _ptr(out["dist"]), _ptr(out["closest"]), _ptr(out["argmin"]),
+                                            _ptr(out["newton"]), _ptr(out["status"]), _stream(stream)))
     return out
 
 

@@ -11,6 +11,7 @@
 // G = 32 is a warp per query; G = 256 / 512 is a CTA per query for large n
 // (n <= 8192).
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "hopf_internal.h"
@@ -538,6 +539,56 @@ hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const 
   U.iters = newton;
   U.qstatus = qstatus;
   return dispatch_union(U, true, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free distance / closest point.
+//
+// Some callers must not allocate device memory once they are running: a
+// controller that queries the distance to a set of obstacles at a fixed rate,
+// code inside a region whose memory budget is fixed in advance, or a host
+// that hands this library no allocator at all.  For them the scratch of
+// union_closest lives in one static device array that every GPU loading the
+// library holds until the process exits.  The device address of that array
+// is looked up once per device, with the device current, on the first call
+// there; calls that overlap on the GPU share the array and race.  No entry of
+// the scratch needs to start at zero: every slot a call reads is written
+// earlier in the same call.
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+static hopf_status noalloc_scratch(void** out) {
+  int dev = 0;
+  HOPF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(HOPF_EUNSUPPORTED, "no-alloc scratch: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return HOPF_OK;
+}
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+hopf_status union_closest_noalloc(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
+                                  int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                                  uint8_t* qstatus, cudaStream_t stream) {
+  const size_t need = union_workspace(K, parts[0]->n, batch);
+  if (need > kNoAllocScratchBytes)
+    return fail(HOPF_EINVAL, "hopf_union_closest_noalloc: batch * parts needs more than the 8 MiB static scratch "
+                             "(at most about 490,000 query-part pairs)");
+  void* ws = nullptr;
+  hopf_status s = noalloc_scratch(&ws);
+  if (s != HOPF_OK) return s;
+  return union_closest(parts, K, batch, x, s_tol, max_newton, dist, closest, argmin, newton, qstatus, ws, need,
+                       stream);
 }
 
 }  // namespace hopf

@@ -267,6 +267,18 @@ hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batc
                        ws_bytes, stream);
 }
 
+hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int64_t batch, const float* x,
+                                       float s_tol, int32_t max_newton, float* dist, float* closest, int32_t* argmin,
+                                       int32_t* newton, uint8_t* qstatus, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_parts(parts, K, true);
+  if (s != HOPF_OK) return s;
+  if (batch < 0 || max_newton < 1 || !(s_tol > 0)) return fail(HOPF_EINVAL, "hopf_union_closest_noalloc: bad argument");
+  if (batch == 0) return HOPF_OK;
+  if (!x || !dist || !argmin) return fail(HOPF_EINVAL, "hopf_union_closest_noalloc: null x, dist or argmin");
+  return union_closest_noalloc(parts, K, batch, x, s_tol, max_newton, dist, closest, argmin, newton, qstatus, stream);
+}
+
 hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
                           float* g_t, float* g_A, cudaStream_t stream) {
   set_error("");

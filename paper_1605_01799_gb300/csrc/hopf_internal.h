@@ -61,6 +61,10 @@ hopf_status union_eval(const hopf_handle* parts, int K, int64_t batch, const flo
 hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
                           int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
                           uint8_t* qstatus, void* ws, size_t ws_bytes, cudaStream_t stream);
+size_t noalloc_scratch_bytes();
+hopf_status union_closest_noalloc(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
+                                  int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
+                                  uint8_t* qstatus, cudaStream_t stream);
 
 // ---- dense path ----
 // Workspace shared by the dense solvers.
