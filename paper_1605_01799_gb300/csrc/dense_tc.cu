@@ -19,8 +19,13 @@
 //  phase per iteration.  Its fixed point carries the BF16 error of M r.
 //
 // The start v^0 = d^0 = y, b^0 = 0 (Section 3.1) is u^0 = p^0 = y.  After the
-// last iteration a final pass computes A p (FP16 split) for
-// phi = <y,p> - 1/2 <p, A p> - c0 - t H(p) (FP64 partial sums).
+// last iteration a final pass computes A p for
+// phi = <y,p> - 1/2 <p, A p> - c0 - t H(p) (FP64 partial sums) with a
+// three-term FP16 split of both A and p (about 33 bits: the two-term split's
+// 2^-22 would leave ~1e-6 in phi, where <y,p> and <p,Ap>/2 cancel):
+//   A p ~ D1 + 2^-11 D2 + 2^-22 D3,  D1 = A1 p1,  D2 = A1 p2 + A2 p1,
+//   D3 = A1 p3 + A2 p2 + A3 p1,
+// two ring stages per k-block and both TMEM buffers per tile.
 //
 // One persistent cooperative launch, one CTA per SM, 320 threads:
 //   warp 0   TMA producer (one elected lane), 3-stage shared-memory ring
@@ -55,9 +60,10 @@ constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 accumulators x 1
 constexpr int FORM_MIXED = 0, FORM_BF16 = 1;
 constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3;
 constexpr float kLoScale = 2048.f;             // 2^11: FP16 split scale
+constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 
 struct TcArgs {
-  CUtensorMap mAh, mAl, mM, mP1, mP2, mG;
+  CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mG, mP3;  // mP3: the g plane read as the third split of p
   float* y;
   float* u;
   uint16_t* p1;
@@ -189,6 +195,7 @@ __device__ __forceinline__ float prox1(float u, float w, float tau, float sc, in
 // -------------------------------------------------------------- shared state
 struct Smem {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  uint64_t cfull[2], cempty[2];  // final pass: hand-off of the D1 chunks
   uint32_t tmem_base;
   int abort;
   int epi_abort;  // snapshot of abort read by all epilogue warps after a barrier
@@ -243,30 +250,41 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
   const CUtensorMap* B1 = &a.mP2;
   const uint32_t bytes = (uint32_t)(cfg.na + cfg.nb) * TILE_BYTES;
   const int nk = a.np / BK, items = a.rt * a.ct;
+  const int nsub = ph == PH_F ? 2 : 1;  // PH_F: {A1, A2 | p1, p2} then {A1, A3 | p3, p1}
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, ph, c)) continue;
-    for (int kb = 0; kb < nk; ++kb, ++st.kb) {
-      const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
-      if (!mbar_wait(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort)) return;
-      const uint32_t full = sa(&S.full[s]);
-      mbar_expect_tx(full, bytes);
-      uint8_t* base = stages + (size_t)s * STAGE_BYTES;
-      const int kx = kb * BK;
-      tma_load(sa(base), A0, full, kx, r * BM);
-      if (cfg.na > 1) tma_load(sa(base + TILE_BYTES), A1, full, kx, r * BM);
-      tma_load(sa(base + 2 * TILE_BYTES), B0, full, kx, c * BN);
-      if (cfg.nb > 1) tma_load(sa(base + 3 * TILE_BYTES), B1, full, kx, c * BN);
-      st.last_par[s] = use & 1;
-      st.used[s] = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
+        const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
+        if (!mbar_wait(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort)) return;
+        const uint32_t full = sa(&S.full[s]);
+        mbar_expect_tx(full, bytes);
+        uint8_t* base = stages + (size_t)s * STAGE_BYTES;
+        const int kx = kb * BK;
+        const CUtensorMap* a1 = sub ? &a.mAl2 : A1;
+        const CUtensorMap* b0 = sub ? &a.mP3 : B0;
+        const CUtensorMap* b1 = sub ? &a.mP1 : B1;
+        tma_load(sa(base), A0, full, kx, r * BM);
+        if (cfg.na > 1) tma_load(sa(base + TILE_BYTES), a1, full, kx, r * BM);
+        tma_load(sa(base + 2 * TILE_BYTES), b0, full, kx, c * BN);
+        if (cfg.nb > 1) tma_load(sa(base + 3 * TILE_BYTES), b1, full, kx, c * BN);
+        st.last_par[s] = use & 1;
+        st.used[s] = true;
+      }
     }
   }
 }
 
 // ----------------------------------------------------------------- role: MMA
+// TMEM: two buffers of 256 columns; each tile normally takes one buffer
+// (alternating), the final pass takes both.  Per-buffer counts of empty waits
+// and full commits give the mbarrier parities.
 struct MmaState {
-  uint32_t kb = 0;    // k-blocks consumed
-  uint32_t item = 0;  // accumulator tiles produced
+  uint32_t kb = 0;       // ring stages consumed
+  uint32_t nb = 0;       // buffer of the next ordinary tile
+  uint32_t ue[2] = {0, 0}, uf[2] = {0, 0};
+  uint32_t ce[2] = {0, 0}, cf[2] = {0, 0};  // final-pass chunk slots
   bool issued = false;
 };
 
@@ -276,12 +294,65 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, Mma
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int c = it / a.rt;
     if (!tile_on(a, ph, c)) continue;
-    const uint32_t buf = st.item & 1, use = st.item >> 1;
-    if (!mbar_wait(sa(&S.tempty[buf]), (use & 1) ^ 1, a.err, &S.abort)) return;
+    const uint32_t buf = ph == PH_F ? 0 : st.nb;
+    if (ph != PH_F) st.nb ^= 1;
+    for (uint32_t b = 0; b < 2; ++b) {
+      if (ph != PH_F && b != buf) continue;
+      if (!mbar_wait(sa(&S.tempty[b]), (st.ue[b] & 1) ^ 1, a.err, &S.abort)) return;
+      ++st.ue[b];
+    }
     tc_fence_after();
     const uint32_t d0 = S.tmem_base + buf * 256;
-    for (int kb = 0; kb < nk; ++kb, ++st.kb) {
+    for (int kb = 0; kb < nk; ++kb) {
+      if (ph == PH_F) {
+        // The main term D1 = A1 p1 goes into one of two 128-column slots per
+        // 128-wide K chunk (two k-blocks); the epilogue adds the chunks up in
+        // registers, so no TMEM accumulator sums more than 8 products of
+        // K = 16.  D2 and D3 (scaled by 2^-11, 2^-22) accumulate over all of K
+        // in the second buffer.  TMEM: D1 slots at 0 and 128, D2 at 256, D3 at 384.
+        const uint32_t chunk = kb >> 1, slot = chunk & 1;
+        if ((kb & 1) == 0) {
+          if (!mbar_wait(sa(&S.cempty[slot]), (st.ce[slot] & 1) ^ 1, a.err, &S.abort)) return;
+          ++st.ce[slot];
+          tc_fence_after();
+        }
+        const uint32_t d1 = S.tmem_base + slot * BN, d2 = S.tmem_base + 256, d3 = S.tmem_base + 384;
+        // sub-stage X: {A1, A2 | p1, p2};  sub-stage Y: {A1, A3 | p3, p1}
+        for (int sub = 0; sub < 2; ++sub, ++st.kb) {
+          const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
+          if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
+          tc_fence_after();
+          const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
+          const uint32_t idesc = idesc_f16(0);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t a0 = smem_desc(base) + (uint64_t)(kk * 2);
+            const uint64_t a1 = smem_desc(base + TILE_BYTES) + (uint64_t)(kk * 2);
+            const uint64_t b0 = smem_desc(base + 2 * TILE_BYTES) + (uint64_t)(kk * 2);
+            const uint64_t b1 = smem_desc(base + 3 * TILE_BYTES) + (uint64_t)(kk * 2);
+            const uint32_t fc = ((kb & 1) == 0 && kk == 0) ? 0u : 1u;  // chunk start overwrites D1
+            const uint32_t fi = (kb == 0 && kk == 0) ? 0u : 1u;        // item start overwrites D2, D3
+            if (sub == 0) {
+              mma_f16(d1, a0, b0, idesc, fc);    // D1 += A1 p1
+              mma_f16(d2, a0, b1, idesc, fi);    // D2 += A1 p2
+              mma_f16(d2, a1, b0, idesc, 1u);    // D2 += A2 p1
+              mma_f16(d3, a1, b1, idesc, fi);    // D3 += A2 p2
+            } else {
+              mma_f16(d3, a0, b0, idesc, 1u);    // D3 += A1 p3
+              mma_f16(d3, a1, b1, idesc, 1u);    // D3 += A3 p1
+            }
+          }
+          st.issued = true;
+          mma_commit(sa(&S.empty[s]));
+        }
+        if (kb & 1) {
+          mma_commit(sa(&S.cfull[slot]));  // this chunk of D1 is ready
+          ++st.cf[slot];
+        }
+        continue;
+      }
       const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
+      ++st.kb;
       if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
       tc_fence_after();
       const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
@@ -299,13 +370,15 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, Mma
       mma_commit(sa(&S.empty[s]));  // frees the stage once these MMAs have read it
     }
     mma_commit(sa(&S.tfull[buf]));  // accumulator ready for the epilogue
-    ++st.item;
+    ++st.uf[buf];
   }
 }
 
 // ------------------------------------------------------------ role: epilogue
 struct EpiState {
-  uint32_t item = 0;
+  uint32_t nb = 0;  // buffer of the next ordinary tile
+  uint32_t ue[2] = {0, 0}, uf[2] = {0, 0};
+  uint32_t ce[2] = {0, 0}, cf[2] = {0, 0};  // final-pass chunk slots
 };
 
 // Load the per-query data of column tile c into shared memory.
@@ -348,8 +421,9 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, ph, c)) continue;
-    const uint32_t buf = st.item & 1, use = st.item >> 1;
-    ++st.item;
+    const uint32_t buf = ph == PH_F ? 0 : st.nb;
+    if (ph != PH_F) st.nb ^= 1;
+    const uint32_t use = st.uf[buf]++;
     epi_sync();  // previous item's readers of the shared query data are done
     epi_stage_queries(a, S, ph, c, k, et);
     if (et == 0) S.epi_abort = S.abort;
@@ -367,7 +441,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
       float d1[32];
       tmem_ld32(tbase + j0, d1);
       if constexpr (ph == PH_A || ph == PH_F) {
-        // A p = D1 + 2^-11 D2: fold the correction accumulator in right away
+        // A p = D1 + 2^-11 D2 (+ 2^-22 D3 in the final pass): fold the
+        // correction accumulators in right away
         float d2[32];
         tmem_ld32(tbase + BN + j0, d2);
 #pragma unroll
@@ -460,8 +535,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
             const float uu = a.u[off], yy = a.y[off];
             const float sc = S.qscale[j];
             const float p = prox1(uu, wr, S.qtau[j], sc, hk);
-            float ap = d1[jj];
-            if (hk == H_L2) ap *= sc;
+            const float ap = d1[jj];  // the final operand is p itself (l2 too)
             const double pd = p;
             f0 = (double)yy * pd - 0.5 * pd * (double)ap;
             f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
@@ -480,6 +554,9 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
+    if (ph == PH_F && lane == 0) mbar_arrive(sa(&S.tempty[1]));
+    ++st.ue[buf];
+    if (ph == PH_F) ++st.ue[1];
     if constexpr (ph != PH_A) {
       epi_sync();
       if (et < BN) {
@@ -504,7 +581,97 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
 // The final pass runs once per call: kept out of line so its FP64 registers do
 // not weigh on the per-iteration epilogues.
 __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, EpiState& st) {
-  epilogue_phase<PH_F>(a, S, 0, st);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int et = threadIdx.x - 64;
+  const int qd = warp & 3;
+  const int jbase = ((warp - 2) >> 2) * (BN / 2);
+  const int rloc = qd * 32 + lane;
+  const int items = a.rt * a.ct, nk = a.np / BK;
+  const int np = a.np, hk = a.h_kind;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int r = it % a.rt, c = it / a.rt;
+    if (!tile_on(a, PH_F, c)) continue;
+    epi_sync();
+    epi_stage_queries(a, S, PH_F, c, 0, et);
+    if (et == 0) S.epi_abort = S.abort;
+    epi_sync();
+    if (S.epi_abort) return;
+    const uint32_t lanebase = S.tmem_base + ((uint32_t)(qd * 32) << 16);
+    // promote each 128-wide K chunk of D1 into FP32 registers (round to nearest)
+    float acc[BN / 2];
+#pragma unroll
+    for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
+    bool good = true;
+    for (int chunk = 0; chunk < nk / 2; ++chunk) {
+      const uint32_t slot = chunk & 1;
+      good = good && mbar_wait(sa(&S.cfull[slot]), st.cf[slot] & 1, a.err, &S.abort);
+      ++st.cf[slot];
+      if (good) {
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(lanebase + slot * BN + jbase, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += v[j];
+        tmem_ld32(lanebase + slot * BN + jbase + 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[32 + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sa(&S.cempty[slot]));
+      ++st.ce[slot];
+    }
+    const uint32_t use = st.uf[0]++;
+    good = good && mbar_wait(sa(&S.tfull[0]), use & 1, a.err, &S.abort);
+    if (good) tc_fence_after();
+    const int row = r * BM + rloc;
+    const float wr = a.w[row];
+    for (int g = 0; good && g < 2; ++g) {
+      const int j0 = jbase + 32 * g;
+      float d2[32], d3[32];
+      tmem_ld32(lanebase + 256 + j0, d2);
+      tmem_ld32(lanebase + 384 + j0, d3);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        // A p = D1 + 2^-11 D2 + 2^-22 D3
+        const float ap = acc[32 * g + jj] + (d2[jj] + d3[jj] * (1.f / kLoScale)) * (1.f / kLoScale);
+        double f0 = 0.0, f1 = 0.0;
+        if (S.qact[j]) {
+          const int64_t q = (int64_t)c * BN + j;
+          const int64_t off = q * np + row;
+          const float uu = a.u[off], yy = a.y[off];
+          const float p = prox1(uu, wr, S.qtau[j], S.qscale[j], hk);
+          const double pd = p;
+          f0 = (double)yy * pd - 0.5 * pd * (double)ap;
+          f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
+          if (row < a.n) a.grad[q * a.n + row] = p;
+        }
+        f0 = warp_sum(f0);
+        f1 = warp_sum(f1);
+        if (lane == 0) {
+          S.redd[qd][j][0] = f0;
+          S.redd[qd][j][1] = f1;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(sa(&S.tempty[0]));
+      mbar_arrive(sa(&S.tempty[1]));
+    }
+    ++st.ue[0];
+    ++st.ue[1];
+    epi_sync();
+    if (et < BN) {
+      const int64_t q = (int64_t)c * BN + et;
+      const double s0 = S.redd[0][et][0] + S.redd[1][et][0] + S.redd[2][et][0] + S.redd[3][et][0];
+      const double s1 = S.redd[0][et][1] + S.redd[1][et][1] + S.redd[2][et][1] + S.redd[3][et][1];
+      a.fpart[(int64_t)r * a.B_pad + q] = s0;
+      a.fpart[(int64_t)(a.rt + r) * a.B_pad + q] = s1;
+    }
+  }
 }
 
 // Decision for iteration k (convergence of iteration k-1), one thread per
@@ -552,7 +719,8 @@ __device__ void prepass(const TcArgs& a, Smem& S, int k) {
   }
 }
 
-// BF16 form, before the final pass: FP16 split of p = prox(u) for every query.
+// Before the final pass: the three-term FP16 split of p = prox(u) for every
+// query (p1 and p2 planes, the third term in the g plane).
 __device__ void prep_final_operand(const TcArgs& a) {
   const int64_t total = a.B_pad * a.np;
   const int64_t stride = (int64_t)gridDim.x * NEPI;
@@ -560,10 +728,14 @@ __device__ void prep_final_operand(const TcArgs& a) {
     const int64_t q = i / a.np;
     const int row = (int)(i % a.np);
     const float uu = a.u[i];
-    const float pn = a.h_kind == H_L2 ? uu : shrink1(uu, a.tau[q] * a.w[row]);
-    const __half hi = __float2half_rn(pn);
-    a.p1[i] = __half_as_ushort(hi);
-    a.p2[i] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
+    const float pn = a.h_kind == H_L2 ? a.scale[q] * uu : shrink1(uu, a.tau[q] * a.w[row]);
+    const __half h1 = __float2half_rn(pn);
+    const float r1 = pn - __half2float(h1);  // exact
+    const __half h2 = __float2half_rn(r1 * kLoScale);
+    const float r2 = r1 - __half2float(h2) * (1.f / kLoScale);  // exact
+    a.p1[i] = __half_as_ushort(h1);
+    a.p2[i] = __half_as_ushort(h2);
+    a.g[i] = __half_as_ushort(__float2half_rn(r2 * kLo2Scale));
   }
 }
 
@@ -584,6 +756,10 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
       mbar_init(sa(&S.tempty[b]), 8);
     }
     mbar_init(sa(&S.drain), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(sa(&S.cfull[b]), 1);
+      mbar_init(sa(&S.cempty[b]), 8);
+    }
     S.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -637,7 +813,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     }
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
   }
-  if (ok && a.form == FORM_BF16) {
+  if (ok) {
     if (warp >= 2) prep_final_operand(a);
     proxy_fence_global();
     ok = grid_barrier(a.bar, gridDim.x, a.err);
@@ -732,6 +908,7 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   memset(&a, 0, sizeof(a));
   const int np = h->n_pad;
   bool ok = encode(&a.mAh, h->d_Ah16, np, np, false) && encode(&a.mAl, h->d_Al16, np, np, false) &&
+            encode(&a.mAl2, h->d_Al2, np, np, false) && encode(&a.mP3, w.g, w.B_pad, np, false) &&
             encode(&a.mM, h->d_Mbf, np, np, true) &&
             encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
             encode(&a.mG, w.g, w.B_pad, np, true);

@@ -35,7 +35,7 @@ int sm_count(int device) {
 static void free_handle(hopf_handle h) {
   if (!h) return;
   void* ptrs[] = {h->d_A, h->d_c, h->d_w, h->d_cf, h->d_wf, h->d_af, h->d_M64, h->d_M32, h->d_A32,
-                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Abf};
+                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;

@@ -28,6 +28,7 @@ struct hopf_handle_s {
   uint16_t* d_Mbf = nullptr;   // BF16(M)
   uint16_t* d_Ah16 = nullptr;  // FP16(A)
   uint16_t* d_Al16 = nullptr;  // FP16((A - FP16(A)) * 2^11)
+  uint16_t* d_Al2 = nullptr;   // FP16((A - hi - lo * 2^-11) * 2^22): third term of the split
   uint16_t* d_Abf = nullptr;   // BF16(A) (for the BF16 form's final phi pass)
   cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
 };

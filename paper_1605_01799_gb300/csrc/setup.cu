@@ -61,10 +61,12 @@ __global__ void k_finish_inverse(const double* __restrict__ S, double* __restric
   if (Mbf) Mbf[idx] = __bfloat16_as_ushort(__double2bfloat16(m));
 }
 
-// Copies of A: FP32, BF16, and the two-term FP16 split A = hi + lo * 2^-11 with
-// hi = fp16(A) and lo = fp16((A - hi) * 2^11), padded with zeros.
+// Copies of A: FP32, BF16, and the three-term FP16 split
+// A = hi + lo * 2^-11 + lo2 * 2^-22 with hi = fp16(A), lo = fp16((A - hi) 2^11),
+// lo2 = fp16((A - hi - lo 2^-11) 2^22), padded with zeros.
 __global__ void k_cast_A(const double* __restrict__ A, float* __restrict__ A32, uint16_t* __restrict__ Abf,
-                         uint16_t* __restrict__ Ah, uint16_t* __restrict__ Al, int n, int np) {
+                         uint16_t* __restrict__ Ah, uint16_t* __restrict__ Al, uint16_t* __restrict__ Al2, int n,
+                         int np) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)np * np) return;
   int i = (int)(idx / np), j = (int)(idx % np);
@@ -73,10 +75,13 @@ __global__ void k_cast_A(const double* __restrict__ A, float* __restrict__ A32, 
   if (A32) A32[idx] = (float)a;
   if (Abf) Abf[idx] = __bfloat16_as_ushort(__double2bfloat16(a));
   if (Ah) {
-    __half hi = __double2half(a);
-    double rest = (a - (double)__half2float(hi)) * 2048.0;
+    const __half hi = __double2half(a);
+    const double r1 = a - (double)__half2float(hi);
+    const __half lo = __double2half(r1 * 2048.0);
+    const double r2 = r1 - (double)__half2float(lo) / 2048.0;
     Ah[idx] = __half_as_ushort(hi);
-    Al[idx] = __half_as_ushort(__double2half(rest));
+    Al[idx] = __half_as_ushort(lo);
+    Al2[idx] = __half_as_ushort(__double2half(r2 * 4194304.0));
   }
 }
 
@@ -129,11 +134,12 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
     S_CALL(cudaMalloc(&h->d_Mbf, pp * sizeof(uint16_t)));
     S_CALL(cudaMalloc(&h->d_Ah16, pp * sizeof(uint16_t)));
     S_CALL(cudaMalloc(&h->d_Al16, pp * sizeof(uint16_t)));
+    S_CALL(cudaMalloc(&h->d_Al2, pp * sizeof(uint16_t)));
     S_CALL(cudaMalloc(&h->d_Abf, pp * sizeof(uint16_t)));
   }
   k_finish_inverse<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf, n, np);
-  k_cast_A<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(h->d_A, h->d_A32, h->d_Abf, h->d_Ah16, h->d_Al16, n,
-                                                               np);
+  k_cast_A<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(h->d_A, h->d_A32, h->d_Abf, h->d_Ah16, h->d_Al16,
+                                                               h->d_Al2, n, np);
   S_CALL(cudaGetLastError());
   S_CALL(cudaStreamSynchronize(stream));
   cleanup();
