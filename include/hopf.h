@@ -210,6 +210,13 @@ hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, cons
  * Not thread-safe with concurrent hopf_eval calls on the same handle. */
 hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t stop);
 
+/* Query compaction of the dense tensor-core (MIXED) solver: as queries
+ * converge, the still-active ones are packed into fewer column tiles so the
+ * tensor cores work only on unconverged queries.  On by default; off gives the
+ * same results (each query's arithmetic does not depend on its column), only
+ * slower.  Other paths ignore it. */
+hopf_status hopf_set_compaction(hopf_handle h, int32_t on);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* hopf_last_error(void);
 

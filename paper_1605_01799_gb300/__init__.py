@@ -28,7 +28,7 @@ Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
            "hopf_backward",
-           "hopf_profile_events", "hopf_last_error", "hopf_version"]
+           "hopf_profile_events", "hopf_set_compaction", "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -69,6 +69,7 @@ def lib():
                                            ctypes.c_int),
             "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
+            "hopf_set_compaction": ([_vp, _i32], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
             "hopf_version": ([], ctypes.c_char_p),
         }
@@ -170,6 +171,9 @@ class Hopf:
         sp = None if start is None else ctypes.c_void_p(start.cuda_event)
         ep = None if stop is None else ctypes.c_void_p(stop.cuda_event)
         _check(lib().hopf_profile_events(self.handle, sp, ep))
+
+    def set_compaction(self, on):
+        _check(lib().hopf_set_compaction(self.handle, 1 if on else 0))
 
     def backward(self, g_phi, vstar, want_x=True, want_t=True, want_A=True, stream=None):
         import torch

@@ -11,12 +11,12 @@
 
 namespace hopf {
 
-static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 16 */) {
+static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 */) {
   const int64_t B_pad = round_up(batch > 0 ? batch : 1, 256);
   const int64_t np = h->n_pad;
   const int rt = (int)(np / 128);
   const bool tc = h->precision != HOPF_P_FP32;
-  size_t s[16] = {0};
+  size_t s[32] = {0};
   s[0] = B_pad * np * 4;                 // y
   s[1] = B_pad * np * 4;                 // u
   s[2] = tc ? B_pad * np * 2 : 0;        // ph
@@ -33,8 +33,18 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 16 
   s[13] = 64;                            // err
   s[14] = B_pad * 4;                     // qact
   s[15] = (B_pad / 128) * 4;             // tile_act
+  s[16] = tc ? B_pad * np * 4 : 0;       // y_b
+  s[17] = tc ? B_pad * np * 4 : 0;       // u_b
+  s[18] = tc ? B_pad * np * 2 : 0;       // ph_b
+  s[19] = tc ? B_pad * np * 2 : 0;       // pl_b
+  s[20] = B_pad * 4;                     // scale_b
+  s[21] = B_pad * 4;                     // qact_b
+  s[22] = 2 * B_pad * 4;                 // sq
+  s[23] = tc ? B_pad * np * 4 : 0;       // ufin
+  s[24] = B_pad * 4;                     // sfin
+  s[25] = 2 * B_pad * 4;                 // taus
   size_t total = 0;
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 26; ++i) {
     if (out) out[i] = total;
     total += round_up(s[i], 256);
   }
@@ -44,7 +54,7 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 16 
 size_t dense_workspace(const hopf_handle h, int64_t batch) { return carve_sizes(h, batch, nullptr); }
 
 hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_bytes, DenseWs* d) {
-  size_t off[16];
+  size_t off[32];
   size_t total = carve_sizes(h, batch, off);
   if (ws_bytes < total) return fail(HOPF_EINVAL, "hopf_eval: workspace too small");
   char* p = (char*)ws;
@@ -68,6 +78,16 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
   d->err = (int*)(p + off[13]);
   d->qact = (int*)(p + off[14]);
   d->tile_act = (int*)(p + off[15]);
+  d->y_b = tc ? (float*)(p + off[16]) : nullptr;
+  d->u_b = tc ? (float*)(p + off[17]) : nullptr;
+  d->ph_b = tc ? (uint16_t*)(p + off[18]) : nullptr;
+  d->pl_b = tc ? (uint16_t*)(p + off[19]) : nullptr;
+  d->scale_b = (float*)(p + off[20]);
+  d->qact_b = (int*)(p + off[21]);
+  d->sq = (int*)(p + off[22]);
+  d->ufin = tc ? (float*)(p + off[23]) : nullptr;
+  d->sfin = (float*)(p + off[24]);
+  d->taus = (float*)(p + off[25]);
   return HOPF_OK;
 }
 
@@ -76,7 +96,8 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
 __global__ void k_dense_init(const float* __restrict__ x, const float* __restrict__ t, const float* __restrict__ c,
                              int n, int np, int64_t B, int64_t B_pad, float lam, float* __restrict__ y,
                              float* __restrict__ u, float* __restrict__ tau, float* __restrict__ tq,
-                             int* __restrict__ qiter, int* __restrict__ qdone) {
+                             int* __restrict__ qiter, int* __restrict__ qdone, int* __restrict__ sq,
+                             float* __restrict__ taus) {
   const int64_t q = blockIdx.x;  // one CTA per query (1-D grid: no 65,535 limit)
   if (q >= B_pad) return;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
@@ -89,8 +110,10 @@ __global__ void k_dense_init(const float* __restrict__ x, const float* __restric
     const float tt = q < B ? t[q] : 0.f;
     tq[q] = tt;
     tau[q] = tt / lam;
+    taus[q] = tt / lam;
     qiter[q] = 0;
     qdone[q] = q < B ? 0 : 1;
+    sq[q] = (int)q;  // slot q starts with query q
   }
 }
 
@@ -98,7 +121,7 @@ hopf_status dense_init(hopf_handle h, DenseWs& w, const float* x, const float* t
   HOPF_CUDA(cudaMemsetAsync(w.bar, 0, 64, s));
   HOPF_CUDA(cudaMemsetAsync(w.err, 0, 64, s));
   k_dense_init<<<(unsigned)w.B_pad, 256, 0, s>>>(x, t, h->d_cf, h->n, h->n_pad, w.B, w.B_pad, (float)h->lambda, w.y,
-                                                 w.u, w.tau, w.tq, w.qiter, w.qdone);
+                                                 w.u, w.tau, w.tq, w.qiter, w.qdone, w.sq, w.taus);
   HOPF_CUDA(cudaGetLastError());
   return HOPF_OK;
 }

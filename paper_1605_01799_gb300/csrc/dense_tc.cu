@@ -62,28 +62,44 @@ constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3;
 constexpr float kLoScale = 2048.f;             // 2^11: FP16 split scale
 constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 
+// Slot-indexed state comes in two buffer sets ([0], [1]); compaction packs the
+// active slots of one set into the other.  Query-indexed: tau, qiter, qdone,
+// ufin, sfin, fpart, the final-pass operand planes.
 struct TcArgs {
-  CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mG, mP3;  // mP3: the g plane read as the third split of p
-  float* y;
-  float* u;
-  uint16_t* p1;
-  uint16_t* p2;
+  CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mP1b, mP2b, mG, mP3;  // mP3: the g plane read as the third split of p
+  float* y[2];
+  float* u[2];
+  uint16_t* p1[2];
+  uint16_t* p2[2];
+  float* scale[2];
+  float* taus[2];     // t / lambda by slot
+  int* qact[2];       // 1 active, 2 retiring in this decision, 0 otherwise
+  int* sq[2];         // slot -> query
   uint16_t* g;
   float* part;
   double* fpart;
   float* tau;
-  float* scale;
   int* qiter;
   int* qdone;
-  int* qact;
   int* tile_act;
+  float* ufin;
+  float* sfin;
+  const float* x;     // the caller's queries [B][n] (final pass: y = x - c)
+  const float* cf;    // centre, padded
   unsigned* bar;
   int* err;
   const float* w;
   float* grad;
   int64_t B, B_pad;
-  int n, np, rt, ct, h_kind, max_iter, form;
+  int n, np, rt, ct, h_kind, max_iter, form, compact;
   float lam, tol;
+};
+
+// Per-CTA view of the slot layout; every CTA updates it identically.
+struct Ctx {
+  int cb;     // current buffer set
+  int ct_on;  // column tiles in use (the active prefix)
+  int fresh;  // compacted in this iteration: every tile below ct_on holds active slots
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -186,6 +202,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// the first 128 epilogue threads only (one per slot of a tile)
+__device__ __forceinline__ void epi_sync_half() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 __device__ __forceinline__ float prox1(float u, float w, float tau, float sc, int h_kind) {
@@ -202,6 +220,8 @@ struct Smem {
   int first;
   float qtau[BN], qscale[BN];
   int qact[BN];
+  int qid[BN];
+  int base[1024];  // compaction: first new slot of each column tile
   float red[4][BN][2];
   double redd[4][BN][2];
 };
@@ -228,8 +248,12 @@ __device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
   return c;
 }
 
-__device__ __forceinline__ bool tile_on(const TcArgs& a, int ph, int c) {
-  return ph == PH_F ? ((int64_t)c * BN < a.B) : (a.tile_act[c] > 0);
+__device__ __forceinline__ bool tile_on(const TcArgs& a, const Ctx& x, int ph, int c) {
+  if (ph == PH_F) return (int64_t)c * BN < a.B;
+  return c < x.ct_on && (x.fresh || a.tile_act[c] > 0);
+}
+__device__ __forceinline__ int phase_items(const TcArgs& a, const Ctx& x, int ph) {
+  return a.rt * (ph == PH_F ? a.ct : x.ct_on);
 }
 
 // ------------------------------------------------------------ role: producer
@@ -242,18 +266,22 @@ struct ProdState {
 // BF16 form: r^{k-1} lives in buffer (k-1) & 1 (p1 = buffer 0, p2 = buffer 1)
 // and the epilogue of iteration k writes r^k into the other one, so no CTA
 // overwrites an operand another CTA may still be loading.
-__device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, int k, ProdState& st) {
+__device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, int k, const Ctx& x,
+                               ProdState& st) {
   const PhaseCfg cfg = phase_cfg(ph);
   const CUtensorMap* A0 = (ph == PH_A || ph == PH_F) ? &a.mAh : &a.mM;
   const CUtensorMap* A1 = &a.mAl;
-  const CUtensorMap* B0 = (ph == PH_A || ph == PH_F) ? &a.mP1 : (ph == PH_B ? &a.mG : (((k - 1) & 1) ? &a.mP2 : &a.mP1));
-  const CUtensorMap* B1 = &a.mP2;
+  const CUtensorMap* B0 = ph == PH_A ? (x.cb ? &a.mP1b : &a.mP1)
+                          : ph == PH_F ? &a.mP1
+                          : ph == PH_B ? &a.mG
+                                       : (((k - 1) & 1) ? &a.mP2 : &a.mP1);
+  const CUtensorMap* B1 = (ph == PH_A && x.cb) ? &a.mP2b : &a.mP2;
   const uint32_t bytes = (uint32_t)(cfg.na + cfg.nb) * TILE_BYTES;
-  const int nk = a.np / BK, items = a.rt * a.ct;
+  const int nk = a.np / BK, items = phase_items(a, x, ph);
   const int nsub = ph == PH_F ? 2 : 1;  // PH_F: {A1, A2 | p1, p2} then {A1, A3 | p3, p1}
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
-    if (!tile_on(a, ph, c)) continue;
+    if (!tile_on(a, x, ph, c)) continue;
     for (int kb = 0; kb < nk; ++kb) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
         const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
@@ -288,12 +316,12 @@ struct MmaState {
   bool issued = false;
 };
 
-__device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, MmaState& st) {
+__device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, const Ctx& x, MmaState& st) {
   const PhaseCfg cfg = phase_cfg(ph);
-  const int nk = a.np / BK, items = a.rt * a.ct;
+  const int nk = a.np / BK, items = phase_items(a, x, ph);
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int c = it / a.rt;
-    if (!tile_on(a, ph, c)) continue;
+    if (!tile_on(a, x, ph, c)) continue;
     const uint32_t buf = ph == PH_F ? 0 : st.nb;
     if (ph != PH_F) st.nb ^= 1;
     for (uint32_t b = 0; b < 2; ++b) {
@@ -382,22 +410,29 @@ struct EpiState {
 };
 
 // Load the per-query data of column tile c into shared memory.
-__device__ void epi_stage_queries(const TcArgs& a, Smem& S, int ph, int c, int k, int et) {
+__device__ void epi_stage_queries(const TcArgs& a, Smem& S, int ph, int c, int k, const Ctx& x, int et) {
   if (et >= BN) return;
-  const int64_t q = (int64_t)c * BN + et;
-  S.qtau[et] = a.tau[q];
-  S.qscale[et] = a.scale[q];
-  S.qact[et] = ph == PH_F ? (q < a.B) : a.qact[q];
+  const int64_t sl = (int64_t)c * BN + et;  // slot (the query itself in the final pass)
+  if (ph == PH_F) {
+    S.qtau[et] = a.tau[sl];
+    S.qscale[et] = a.sfin[sl];
+    S.qact[et] = sl < a.B;
+  } else {
+    S.qtau[et] = a.taus[x.cb][sl];
+    S.qscale[et] = a.scale[x.cb][sl];
+    S.qact[et] = a.qact[x.cb][sl] == 1;
+  }
   if (et == 0) S.first = (ph != PH_F) && k == 1;
 }
 
-// Transpose-reduce: lane L holds v[0..31] (one value per column for its row);
-// on return v[0] of lane L is the sum over the 32 lanes of column L.  Each
-// halving step keeps one half of the columns and exchanges the other half
-// with the partner lane: 16 + 8 + 4 + 2 + 1 = 31 shuffles for 32 columns.
-__device__ __forceinline__ void transpose_reduce32(float v[32], int lane) {
+// Transpose-reduce over 16 columns: lane L holds v[0..15] (one value per
+// column for its row).  Four halving steps (8 + 4 + 2 + 1 shuffles) leave lane
+// L with column (L & 15) summed over the 16 lanes that share bit 4 of L; one
+// more exchange across bit 4 completes the sum over all 32 rows.  On return
+// v[0] of lanes L and L ^ 16 holds the total of column L & 15.
+__device__ __forceinline__ void transpose_reduce16(float v[16], int lane) {
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
+  for (int o = 8; o >= 1; o >>= 1) {
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < o; ++i) {
@@ -406,27 +441,55 @@ __device__ __forceinline__ void transpose_reduce32(float v[32], int lane) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 template <int ph>
-__device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
+__device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;      // 0..255
   const int qd = warp & 3;              // TMEM lane quadrant of this warp
   const int jbase = ((warp - 2) >> 2) * (BN / 2);  // this warp's half of the columns
   const int rloc = qd * 32 + lane;      // row within the tile
-  const int items = a.rt * a.ct;
+  const int items = phase_items(a, x, ph);
   const int np = a.np, hk = a.h_kind;
   const float lam = a.lam;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  const int cb = x.cb;
+  // the query data (tau, scale, active) of the next item is loaded into
+  // registers while the current item is processed
+  int it = blockIdx.x;
+  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+  float pf_tau = 0.f, pf_sc = 1.f;
+  int pf_act = 0;
+  if (it < items && et < BN) {
+    const int64_t sl = (int64_t)(it / a.rt) * BN + et;
+    pf_tau = a.taus[cb][sl];
+    pf_sc = a.scale[cb][sl];
+    pf_act = a.qact[cb][sl] == 1;
+  }
+  while (it < items) {
     const int r = it % a.rt, c = it / a.rt;
-    if (!tile_on(a, ph, c)) continue;
-    const uint32_t buf = ph == PH_F ? 0 : st.nb;
-    if (ph != PH_F) st.nb ^= 1;
+    int it_next = it + gridDim.x;
+    while (it_next < items && !tile_on(a, x, ph, it_next / a.rt)) it_next += gridDim.x;
+    const uint32_t buf = st.nb;
+    st.nb ^= 1;
     const uint32_t use = st.uf[buf]++;
     epi_sync();  // previous item's readers of the shared query data are done
-    epi_stage_queries(a, S, ph, c, k, et);
-    if (et == 0) S.epi_abort = S.abort;
+    if (et < BN) {
+      S.qtau[et] = pf_tau;
+      S.qscale[et] = pf_sc;
+      S.qact[et] = pf_act;
+      if (it_next < items) {
+        const int64_t sl = (int64_t)(it_next / a.rt) * BN + et;
+        pf_tau = a.taus[cb][sl];
+        pf_sc = a.scale[cb][sl];
+        pf_act = a.qact[cb][sl] == 1;
+      }
+    }
+    if (et == 0) {
+      S.first = k == 1;
+      S.epi_abort = S.abort;
+    }
     epi_sync();
     if (S.epi_abort) return;  // the same decision in all eight warps
     // a failed wait skips the work of this item but keeps the warp in step
@@ -437,31 +500,32 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
     const float wr = a.w[row];
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
     const bool first = S.first;
-    for (int j0 = jbase; good && j0 < jbase + BN / 2; j0 += 32) {
-      float d1[32];
-      tmem_ld32(tbase + j0, d1);
-      if constexpr (ph == PH_A || ph == PH_F) {
-        // A p = D1 + 2^-11 D2 (+ 2^-22 D3 in the final pass): fold the
-        // correction accumulators in right away
-        float d2[32];
-        tmem_ld32(tbase + BN + j0, d2);
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) d1[jj] += d2[jj] * (1.f / kLoScale);
-      }
-      // active queries of this 32-column chunk as a bit mask
-      const uint32_t am = __ballot_sync(0xffffffffu, S.qact[j0 + lane] != 0);
-      const float* ucol = a.u + ((int64_t)c * BN + j0) * np + row;
-      const float* ycol = a.y + ((int64_t)c * BN + j0) * np + row;
+    for (int j0 = jbase; good && j0 < jbase + BN / 2; j0 += 16) {
+      float d1[16];
+      tmem_ld16(tbase + j0, d1);
       if constexpr (ph == PH_A) {
-        // all loads first (independent, in flight together), then the stores
-        float uu[32], yy[32];
+        // A p = D1 + 2^-11 D2
+        float d2[16];
+        tmem_ld16(tbase + BN + j0, d2);
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
-          yy[jj] = (am >> jj & 1u) ? __ldg(ycol + (int64_t)jj * np) : 0.f;
+        for (int jj = 0; jj < 16; ++jj) d1[jj] += d2[jj] * (1.f / kLoScale);
+      }
+      // active queries of this 16-column chunk as a bit mask (lanes 0-15 vote)
+      const uint32_t am = __ballot_sync(0xffffffffu, lane < 16 && S.qact[j0 + (lane & 15)] != 0);
+      const int64_t col0 = ((int64_t)c * BN + j0) * np + row;
+      if constexpr (ph == PH_A) {
+        const float* ucol = a.u[cb] + col0;
+        const float* ycol = a.y[cb] + col0;
+        // all loads first (independent, in flight together), then the stores
+        float uu[16], yy[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const bool on = am >> jj & 1u;
+          uu[jj] = on ? ucol[(int64_t)jj * np] : 0.f;
+          yy[jj] = on ? __ldg(ycol + (int64_t)jj * np) : 0.f;
         }
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
+        for (int jj = 0; jj < 16; ++jj) {
           if (!(am >> jj & 1u)) continue;
           const int j = j0 + jj;
           const float tau = S.qtau[j], sc = S.qscale[j];
@@ -469,84 +533,69 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
           float ap = d1[jj];
           if (hk == H_L2 && !first) ap *= sc;  // l2: the operand held u, p = sc u
           const float g = yy[jj] - ap - lam * (uu[jj] - p);
-          a.g[((int64_t)c * BN + j) * np + row] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+          a.g[col0 + (int64_t)jj * np] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
         }
       } else if constexpr (ph == PH_B) {
         // d1 becomes |u^k - u^{k-1}|^2 and uu becomes |u^k|^2 in place
-        float uu[32];
+        float* U = a.u[cb] + col0;
+        uint16_t* P1 = a.p1[cb] + col0;
+        uint16_t* P2 = a.p2[cb] + col0;
+        float uu[16];
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
+        for (int jj = 0; jj < 16; ++jj) uu[jj] = (am >> jj & 1u) ? U[(int64_t)jj * np] : 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const float du = (am >> jj & 1u) ? d1[jj] : 0.f;
+        for (int jj = 0; jj < 16; ++jj) {
+          const bool on = am >> jj & 1u;
+          const float du = on ? d1[jj] : 0.f;
           const float un = uu[jj] + du;
-          if (am >> jj & 1u) {
-            const int64_t off = ((int64_t)c * BN + j0 + jj) * np + row;
+          if (on) {
             const float pn = hk == H_L2 ? un : shrink1(un, S.qtau[j0 + jj] * wr);
             const __half hi = __float2half_rn(pn);
-            a.p1[off] = __half_as_ushort(hi);
-            a.p2[off] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
-            a.u[off] = un;
+            P1[(int64_t)jj * np] = __half_as_ushort(hi);
+            P2[(int64_t)jj * np] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
+            U[(int64_t)jj * np] = un;
           }
           d1[jj] = du * du;
-          uu[jj] = (am >> jj & 1u) ? un * un : 0.f;
+          uu[jj] = on ? un * un : 0.f;
         }
-        transpose_reduce32(d1, lane);
-        transpose_reduce32(uu, lane);
-        S.red[qd][j0 + lane][0] = d1[0];
-        S.red[qd][j0 + lane][1] = uu[0];
+        transpose_reduce16(d1, lane);
+        transpose_reduce16(uu, lane);
+        if (lane < 16) {
+          S.red[qd][j0 + lane][0] = d1[0];
+          S.red[qd][j0 + lane][1] = uu[0];
+        }
       } else if constexpr (ph == PH_P) {
-        float uu[32], yy[32];
-        uint16_t* rbuf = (k & 1) ? a.p2 : a.p1;
+        float* U = a.u[cb] + col0;
+        const float* ycol = a.y[cb] + col0;
+        uint16_t* rbuf = ((k & 1) ? a.p2[cb] : a.p1[cb]) + col0;  // BF16 form: no compaction, set 0
+        float uu[16], yy[16];
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          uu[jj] = (am >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
-          yy[jj] = (am >> jj & 1u) ? __ldg(ycol + (int64_t)jj * np) : 0.f;
+        for (int jj = 0; jj < 16; ++jj) {
+          const bool on = am >> jj & 1u;
+          uu[jj] = on ? U[(int64_t)jj * np] : 0.f;
+          yy[jj] = on ? __ldg(ycol + (int64_t)jj * np) : 0.f;
         }
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
+        for (int jj = 0; jj < 16; ++jj) {
           float du = 0.f, un = 0.f;
           if (am >> jj & 1u) {
             const int j = j0 + jj;
-            const int64_t off = ((int64_t)c * BN + j) * np + row;
             const float tau = S.qtau[j];
             const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, S.qscale[j], hk);
             un = d1[jj] + uu[jj] - p;
             du = un - uu[jj];
             const float pn = prox1(un, wr, tau, 1.f, hk);
-            rbuf[off] = __bfloat16_as_ushort(__float2bfloat16_rn(yy[jj] + lam * (2.f * pn - un)));
-            a.u[off] = un;
+            rbuf[(int64_t)jj * np] = __bfloat16_as_ushort(__float2bfloat16_rn(yy[jj] + lam * (2.f * pn - un)));
+            U[(int64_t)jj * np] = un;
           }
           d1[jj] = du * du;
           uu[jj] = un * un;
         }
-        transpose_reduce32(d1, lane);
-        transpose_reduce32(uu, lane);
-        S.red[qd][j0 + lane][0] = d1[0];
-        S.red[qd][j0 + lane][1] = uu[0];
-      } else {  // PH_F: phi partials and the gradient
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int j = j0 + jj;
-          double f0 = 0.0, f1 = 0.0;
-          if (S.qact[j]) {
-            const int64_t q = (int64_t)c * BN + j;
-            const int64_t off = q * np + row;
-            const float uu = a.u[off], yy = a.y[off];
-            const float sc = S.qscale[j];
-            const float p = prox1(uu, wr, S.qtau[j], sc, hk);
-            const float ap = d1[jj];  // the final operand is p itself (l2 too)
-            const double pd = p;
-            f0 = (double)yy * pd - 0.5 * pd * (double)ap;
-            f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
-            if (row < a.n) a.grad[q * a.n + row] = p;
-          }
-          f0 = warp_sum(f0);
-          f1 = warp_sum(f1);
-          if (lane == 0) {
-            S.redd[qd][j][0] = f0;
-            S.redd[qd][j][1] = f1;
-          }
+        transpose_reduce16(d1, lane);
+        transpose_reduce16(uu, lane);
+        if (lane < 16) {
+          S.red[qd][j0 + lane][0] = d1[0];
+          S.red[qd][j0 + lane][1] = uu[0];
         }
       }
     }
@@ -554,45 +603,37 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, EpiState& st) {
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
-    if (ph == PH_F && lane == 0) mbar_arrive(sa(&S.tempty[1]));
     ++st.ue[buf];
-    if (ph == PH_F) ++st.ue[1];
     if constexpr (ph != PH_A) {
       epi_sync();
-      if (et < BN) {
+      if (et < BN && S.qact[et]) {
         const int64_t q = (int64_t)c * BN + et;
-        if constexpr (ph == PH_F) {
-          const double s0 = S.redd[0][et][0] + S.redd[1][et][0] + S.redd[2][et][0] + S.redd[3][et][0];
-          const double s1 = S.redd[0][et][1] + S.redd[1][et][1] + S.redd[2][et][1] + S.redd[3][et][1];
-          a.fpart[(int64_t)r * a.B_pad + q] = s0;
-          a.fpart[(int64_t)(a.rt + r) * a.B_pad + q] = s1;
-        } else if (S.qact[et]) {
-          const float s0 = S.red[0][et][0] + S.red[1][et][0] + S.red[2][et][0] + S.red[3][et][0];
-          const float s1 = S.red[0][et][1] + S.red[1][et][1] + S.red[2][et][1] + S.red[3][et][1];
-          const int par = k & 1;
-          a.part[((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
-          a.part[((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
-        }
+        const float s0 = S.red[0][et][0] + S.red[1][et][0] + S.red[2][et][0] + S.red[3][et][0];
+        const float s1 = S.red[0][et][1] + S.red[1][et][1] + S.red[2][et][1] + S.red[3][et][1];
+        const int par = k & 1;
+        a.part[((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
+        a.part[((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
       }
     }
+    it = it_next;
   }
 }
 
 // The final pass runs once per call: kept out of line so its FP64 registers do
 // not weigh on the per-iteration epilogues.
-__device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, EpiState& st) {
+__device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx& x, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;
   const int qd = warp & 3;
   const int jbase = ((warp - 2) >> 2) * (BN / 2);
   const int rloc = qd * 32 + lane;
-  const int items = a.rt * a.ct, nk = a.np / BK;
+  const int items = phase_items(a, x, PH_F), nk = a.np / BK;
   const int np = a.np, hk = a.h_kind;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
-    if (!tile_on(a, PH_F, c)) continue;
+    if (!tile_on(a, x, PH_F, c)) continue;
     epi_sync();
-    epi_stage_queries(a, S, PH_F, c, 0, et);
+    epi_stage_queries(a, S, PH_F, c, 0, x, et);
     if (et == 0) S.epi_abort = S.abort;
     epi_sync();
     if (S.epi_abort) return;
@@ -640,7 +681,8 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, EpiState& 
         if (S.qact[j]) {
           const int64_t q = (int64_t)c * BN + j;
           const int64_t off = q * np + row;
-          const float uu = a.u[off], yy = a.y[off];
+          const float uu = a.ufin[off];
+          const float yy = row < a.n ? a.x[q * a.n + row] - a.cf[row] : 0.f;  // y = x - c, as at the start
           const float p = prox1(uu, wr, S.qtau[j], S.qscale[j], hk);
           const double pd = p;
           f0 = (double)yy * pd - 0.5 * pd * (double)ap;
@@ -675,37 +717,51 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, EpiState& 
 }
 
 // Decision for iteration k (convergence of iteration k-1), one thread per
-// query of a column tile; the epilogue warps of every CTA share the tiles.
-__device__ void prepass(const TcArgs& a, Smem& S, int k) {
+// slot of a column tile.  A slot that stops (converged, or at max_iter) is
+// retired at once: its u and l2 scale go to the query-indexed final arrays,
+// the 256 epilogue threads copying the row together.
+__device__ __noinline__ void prepass(const TcArgs& a, Smem& S, int k, const Ctx& x) {
   const int et = threadIdx.x - 64;
-  for (int c = blockIdx.x; c < a.ct; c += gridDim.x) {
+  int* const QA = a.qact[x.cb];
+  float* const SC = a.scale[x.cb];
+  const int* const SQ = a.sq[x.cb];
+  const float* const U = a.u[x.cb];
+  for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
     if (et < BN) {
-      const int64_t q = (int64_t)c * BN + et;
+      const int64_t sl = (int64_t)c * BN + et;
+      const int qid = SQ[sl];
       int act = 0;
       if (k == 1) {
-        act = q < a.B;
-        a.scale[q] = 1.f;
-      } else if (!a.qdone[q]) {
+        act = qid < a.B;
+        SC[sl] = 1.f;
+      } else if (QA[sl] == 1) {
         const int par = (k - 1) & 1;
         float du2 = 0.f, nu2 = 0.f;
         for (int rr = 0; rr < a.rt; ++rr) {
-          du2 += a.part[((int64_t)(par * 2 + 0) * a.rt + rr) * a.B_pad + q];
-          nu2 += a.part[((int64_t)(par * 2 + 1) * a.rt + rr) * a.B_pad + q];
+          du2 += a.part[((int64_t)(par * 2 + 0) * a.rt + rr) * a.B_pad + sl];
+          nu2 += a.part[((int64_t)(par * 2 + 1) * a.rt + rr) * a.B_pad + sl];
         }
         const int kprev = k - 1;
-        a.scale[q] = shrink2_scale(sqrtf(nu2), a.tau[q]);
+        const float sc = shrink2_scale(sqrtf(nu2), a.taus[x.cb][sl]);
+        SC[sl] = sc;
         if (kprev >= 2 && du2 <= a.tol * fmaxf(1.f, nu2)) {
-          a.qdone[q] = 1;
-          a.qiter[q] = kprev;
+          a.qdone[qid] = 1;
+          a.qiter[qid] = kprev;
+          a.sfin[qid] = sc;
+          act = 2;
         } else if (kprev >= a.max_iter) {
-          a.qdone[q] = 2;
-          a.qiter[q] = a.max_iter;
+          a.qdone[qid] = 2;
+          a.qiter[qid] = a.max_iter;
+          a.sfin[qid] = sc;
+          act = 2;
         } else {
           act = 1;
         }
       }
-      a.qact[q] = act;
-      const int cnt = __reduce_add_sync(0xffffffffu, act);
+      QA[sl] = act;
+      S.qact[et] = act;
+      S.qid[et] = qid;
+      const int cnt = __reduce_add_sync(0xffffffffu, act == 1 ? 1 : 0);
       if ((et & 31) == 0) S.red[et >> 5][0][0] = __int_as_float(cnt);
     }
     epi_sync();
@@ -715,26 +771,117 @@ __device__ void prepass(const TcArgs& a, Smem& S, int k) {
       a.tile_act[c] = tot;
       if (tot) atomicAdd(a.bar + 2 + (k % 3), (unsigned)tot);
     }
+    // retire the slots that stopped in this decision (rows streamed together)
+    const int per_row = a.np / 4;
+    for (int e = et; e < BN * per_row; e += NEPI) {
+      const int j = e / per_row, i = (e - j * per_row) * 4;
+      if (S.qact[j] != 2) continue;
+      *reinterpret_cast<float4*>(a.ufin + (int64_t)S.qid[j] * a.np + i) =
+          *reinterpret_cast<const float4*>(U + ((int64_t)c * BN + j) * a.np + i);
+    }
     epi_sync();
   }
 }
 
+// Compaction: the active slots (qact == 1) of buffer set x.cb move, in order,
+// to the front of the other set: y, u and the FP16 split of p by rows, the
+// slot's query and scale with them.  Every CTA scans the per-tile active counts
+// itself; tile c's active slots start at base[c].  Slots past the active count
+// in the last new tile are marked inactive.
+__device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int n_active) {
+  const int et = threadIdx.x - 64;
+  const int cb = x.cb, nb = cb ^ 1;
+  if (et == 0) {
+    int acc = 0;
+    for (int c = 0; c < x.ct_on; ++c) {
+      S.base[c] = acc;
+      acc += a.tile_act[c];
+    }
+  }
+  epi_sync();
+  const int np = a.np;
+  for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
+    if (et < BN) {
+      const int64_t sl = (int64_t)c * BN + et;
+      const bool act = a.qact[cb][sl] == 1;
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      if ((et & 31) == 0) S.red[et >> 5][1][0] = __int_as_float(__popc(m));
+      epi_sync_half();
+      int rank = __popc(m & ((1u << (et & 31)) - 1u));
+      for (int wv = 0; wv < (et >> 5); ++wv) rank += __float_as_int(S.red[wv][1][0]);
+      S.qact[et] = act ? S.base[c] + rank : -1;  // destination slot
+      if (act) {
+        const int d = S.base[c] + rank;
+        a.sq[nb][d] = a.sq[cb][sl];
+        a.scale[nb][d] = a.scale[cb][sl];
+        a.taus[nb][d] = a.taus[cb][sl];
+        a.qact[nb][d] = 1;
+      }
+    }
+    epi_sync();
+    // all active rows of the tile at once: 256 threads stream (slot, 4-element)
+    // pieces, so many loads are in flight
+    const int per_row = np / 4, total = BN * per_row;
+    for (int e0 = et; e0 < total; e0 += 4 * NEPI) {
+      float4 yv[4], uv[4];
+      uint2 p1v[4], p2v[4];
+      int64_t dst[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {  // loads of four pieces first
+        const int e = e0 + b * NEPI;
+        dst[b] = -1;
+        if (e >= total) continue;
+        const int j = e / per_row, i = (e - j * per_row) * 4;
+        const int d = S.qact[j];
+        if (d < 0) continue;
+        const int64_t so = ((int64_t)c * BN + j) * np + i;
+        dst[b] = (int64_t)d * np + i;
+        yv[b] = *reinterpret_cast<const float4*>(a.y[cb] + so);
+        uv[b] = *reinterpret_cast<const float4*>(a.u[cb] + so);
+        p1v[b] = *reinterpret_cast<const uint2*>(a.p1[cb] + so);
+        p2v[b] = *reinterpret_cast<const uint2*>(a.p2[cb] + so);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (dst[b] < 0) continue;
+        *reinterpret_cast<float4*>(a.y[nb] + dst[b]) = yv[b];
+        *reinterpret_cast<float4*>(a.u[nb] + dst[b]) = uv[b];
+        *reinterpret_cast<uint2*>(a.p1[nb] + dst[b]) = p1v[b];
+        *reinterpret_cast<uint2*>(a.p2[nb] + dst[b]) = p2v[b];
+      }
+    }
+    epi_sync();
+  }
+  // the tail of the last new tile
+  const int need = (n_active + BN - 1) / BN;
+  for (int64_t sl = (int64_t)n_active + blockIdx.x * NEPI + et; sl < (int64_t)need * BN; sl += (int64_t)gridDim.x * NEPI) {
+    a.qact[nb][sl] = 0;
+    a.sq[nb][sl] = 0;
+    a.scale[nb][sl] = 1.f;
+    a.taus[nb][sl] = 0.f;
+  }
+}
+
 // Before the final pass: the three-term FP16 split of p = prox(u) for every
-// query (p1 and p2 planes, the third term in the g plane).
-__device__ void prep_final_operand(const TcArgs& a) {
+// query (query-indexed p1 and p2 planes of buffer set 0, the third term in the
+// g plane), from the retired u.
+__device__ __noinline__ void prep_final_operand(const TcArgs& a) {
   const int64_t total = a.B_pad * a.np;
   const int64_t stride = (int64_t)gridDim.x * NEPI;
   for (int64_t i = (int64_t)blockIdx.x * NEPI + (threadIdx.x - 64); i < total; i += stride) {
     const int64_t q = i / a.np;
     const int row = (int)(i % a.np);
-    const float uu = a.u[i];
-    const float pn = a.h_kind == H_L2 ? a.scale[q] * uu : shrink1(uu, a.tau[q] * a.w[row]);
+    float pn = 0.f;
+    if (q < a.B) {
+      const float uu = a.ufin[i];
+      pn = a.h_kind == H_L2 ? a.sfin[q] * uu : shrink1(uu, a.tau[q] * a.w[row]);
+    }
     const __half h1 = __float2half_rn(pn);
     const float r1 = pn - __half2float(h1);  // exact
     const __half h2 = __float2half_rn(r1 * kLoScale);
     const float r2 = r1 - __half2float(h2) * (1.f / kLoScale);  // exact
-    a.p1[i] = __half_as_ushort(h1);
-    a.p2[i] = __half_as_ushort(h2);
+    a.p1[0][i] = __half_as_ushort(h1);
+    a.p2[0][i] = __half_as_ushort(h2);
     a.g[i] = __half_as_ushort(__float2half_rn(r2 * kLo2Scale));
   }
 }
@@ -781,19 +928,23 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
   for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
   MmaState ms;
   EpiState es;
+  Ctx cx;
+  cx.cb = 0;
+  cx.ct_on = a.ct;
+  cx.fresh = 0;
   auto run = [&](int ph, int k) {
     if (warp == 0) {
       if (lane == 0) {
         proxy_fence_global();  // generic-proxy writes of the last phase, then TMA reads
-        producer_phase(a, S, stages, ph, k, ps);
+        producer_phase(a, S, stages, ph, k, cx, ps);
       }
     } else if (warp == 1) {
-      if (lane == 0) mma_phase(a, S, stages, ph, ms);
+      if (lane == 0) mma_phase(a, S, stages, ph, cx, ms);
     } else {
-      if (ph == PH_A) epilogue_phase<PH_A>(a, S, k, es);
-      else if (ph == PH_B) epilogue_phase<PH_B>(a, S, k, es);
-      else if (ph == PH_P) epilogue_phase<PH_P>(a, S, k, es);
-      else epilogue_final(a, S, es);
+      if (ph == PH_A) epilogue_phase<PH_A>(a, S, k, cx, es);
+      else if (ph == PH_B) epilogue_phase<PH_B>(a, S, k, cx, es);
+      else if (ph == PH_P) epilogue_phase<PH_P>(a, S, k, cx, es);
+      else epilogue_final(a, S, cx, es);
       proxy_fence_global();
     }
   };
@@ -801,9 +952,22 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
   bool ok = true;
   for (int k = 1; ok; ++k) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
-    if (warp >= 2) prepass(a, S, k);
+    if (warp >= 2) prepass(a, S, k, cx);
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
-    if (ld_acquire_u32(a.bar + 2 + (k % 3)) == 0) break;
+    const int n_active = (int)ld_acquire_u32(a.bar + 2 + (k % 3));
+    if (n_active == 0) break;
+    // pack the active slots when at least an eighth of the tiles in use would
+    // be freed (every CTA takes the same decision from the same count)
+    const int need = (n_active + BN - 1) / BN;
+    cx.fresh = 0;
+    if (a.compact && need + (cx.ct_on + 7) / 8 <= cx.ct_on) {
+      if (warp >= 2) compact(a, S, cx, n_active);
+      proxy_fence_global();
+      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+      cx.cb ^= 1;
+      cx.ct_on = need;
+      cx.fresh = 1;
+    }
     if (a.form == FORM_MIXED) {
       run(PH_A, k);
       if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
@@ -911,21 +1075,36 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
             encode(&a.mAl2, h->d_Al2, np, np, false) && encode(&a.mP3, w.g, w.B_pad, np, false) &&
             encode(&a.mM, h->d_Mbf, np, np, true) &&
             encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
+            encode(&a.mP1b, w.ph_b, w.B_pad, np, false) && encode(&a.mP2b, w.pl_b, w.B_pad, np, false) &&
             encode(&a.mG, w.g, w.B_pad, np, true);
   if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
-  a.y = w.y;
-  a.u = w.u;
-  a.p1 = w.ph;
-  a.p2 = w.pl;
+  a.y[0] = w.y;
+  a.y[1] = w.y_b;
+  a.u[0] = w.u;
+  a.u[1] = w.u_b;
+  a.p1[0] = w.ph;
+  a.p1[1] = w.ph_b;
+  a.p2[0] = w.pl;
+  a.p2[1] = w.pl_b;
+  a.scale[0] = w.scale;
+  a.scale[1] = w.scale_b;
+  a.taus[0] = w.taus;
+  a.taus[1] = w.taus + w.B_pad;
+  a.qact[0] = w.qact;
+  a.qact[1] = w.qact_b;
+  a.sq[0] = w.sq;
+  a.sq[1] = w.sq + w.B_pad;
   a.g = w.g;
   a.part = w.part;
   a.fpart = w.fpart;
   a.tau = w.tau;
-  a.scale = w.scale;
   a.qiter = w.qiter;
   a.qdone = w.qdone;
-  a.qact = w.qact;
   a.tile_act = w.tile_act;
+  a.ufin = w.ufin;
+  a.sfin = w.sfin;
+  a.x = x;
+  a.cf = h->d_cf;
   a.bar = w.bar;
   a.err = w.err;
   a.w = h->d_wf;
@@ -939,6 +1118,8 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.h_kind = h->h_kind;
   a.max_iter = h->max_iter;
   a.form = form;
+  // the BF16 form keeps its r double buffer in set 0 and runs without compaction
+  a.compact = form == FORM_MIXED && h->compact && a.ct <= 1024;  // the scan table holds 1,024 tiles
   a.lam = (float)h->lambda;
   a.tol = (float)h->tol;
 

@@ -49,6 +49,13 @@ extern "C" {
 
 const char* hopf_last_error(void) { return g_last_error.c_str(); }
 
+hopf_status hopf_set_compaction(hopf_handle h, int32_t on) {
+  set_error("");
+  if (!h) return fail(HOPF_EINVAL, "hopf_set_compaction: null handle");
+  h->compact = on ? 1 : 0;
+  return HOPF_OK;
+}
+
 hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t stop) {
   set_error("");
   if (!h) return fail(HOPF_EINVAL, "hopf_profile_events: null handle");

@@ -31,6 +31,7 @@ struct hopf_handle_s {
   uint16_t* d_Al2 = nullptr;   // FP16((A - hi - lo * 2^-11) * 2^22): third term of the split
   uint16_t* d_Abf = nullptr;   // BF16(A) (for the BF16 form's final phi pass)
   cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
+  int compact = 1;  // tensor-core path: pack active queries as others converge
 };
 
 namespace hopf {
@@ -86,6 +87,19 @@ struct DenseWs {
   int* qdone = nullptr;      // [B_pad]
   int* qact = nullptr;       // [B_pad] updated in the current iteration
   int* tile_act = nullptr;   // [B_pad / 128] active queries per column tile
+  // tensor-core path: slots (columns of the operand planes) are compacted as
+  // queries converge; a second buffer set receives the packed slots, and a
+  // converged query's u and l2 scale are retired to query-indexed arrays
+  float* y_b = nullptr;      // [B_pad][n_pad]
+  float* u_b = nullptr;      // [B_pad][n_pad]
+  uint16_t* ph_b = nullptr;  // [B_pad][n_pad]
+  uint16_t* pl_b = nullptr;  // [B_pad][n_pad]
+  float* scale_b = nullptr;  // [B_pad]
+  float* taus = nullptr;     // [2][B_pad] t / lambda by slot (moves with its query)
+  int* qact_b = nullptr;     // [B_pad]
+  int* sq = nullptr;         // [2][B_pad] slot -> query
+  float* ufin = nullptr;     // [B_pad][n_pad] u of converged queries, by query
+  float* sfin = nullptr;     // [B_pad] l2 scale of converged queries, by query
   unsigned* bar = nullptr;   // [4] grid barrier + counters
   int* err = nullptr;        // [1]
 };

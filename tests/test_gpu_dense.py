@@ -133,3 +133,32 @@ def test_dense_not_spd(hg):
     with pytest.raises(hg.HopfError) as e:
         hg.Hopf(A, 0, tol=1e-12, max_iter=10, precision=hg.P_FP32)
     assert e.value.status == hg.HOPF_ENOTSPD
+
+
+def test_compaction_does_not_change_results(hg, orc):
+    """Packing the active queries into fewer column tiles as others converge
+    moves a query's columns but not its arithmetic: with and without it the
+    outputs agree bit for bit.  (2,000 queries: 16 column tiles, so several
+    packings happen.)"""
+    import torch
+    n, B = 256, 2000
+    A, Q, s = wl.spd_matrix(11801, 11802, n)
+    w = wl.uniform(11803, n, 0.5, 1.5)
+    x = wl.normal(11804, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(11805, B, 0.1, 3.0).astype(np.float32)
+    t[::7] = 0.0  # queries that converge almost at once
+    outs = []
+    for on in (True, False):
+        try:
+            h = hg.Hopf(A, 1, w=w, tol=TOL, max_iter=3000, precision=hg.P_MIXED)
+        except hg.HopfError as e:
+            pytest.skip(str(e))
+        h.set_compaction(on)
+        outs.append(h.eval(_cuda(x), _cuda(t)))
+    torch.cuda.synchronize()
+    for key in ("phi", "grad", "iters", "status", "dphidt"):
+        assert torch.equal(outs[0][key], outs[1][key]), key
+    ref = orc.Problem(A, 1, w=w, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
+        x[:64].astype(np.float64), t[:64].astype(np.float64))
+    phi = outs[0]["phi"][:64].cpu().numpy()
+    assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= PHI_TOL
