@@ -255,19 +255,24 @@ def _autograd():
     import torch
 
     class HopfFn(torch.autograd.Function):
-        """phi(x, t; A) with the hand-written envelope-theorem backward.
-        ``A_param`` is the tensor the caller differentiates with respect to;
-        ``hopf`` must be a handle built from its current value."""
+        """phi(x, t; A) with the hand-written envelope-theorem backward
+        (hopf_backward): dphi/dx = v*, dphi/dt = -H(v*), dphi/dA = -1/2 v* v*^T.
+        ``A_param`` is the tensor the caller differentiates with respect to
+        (n x n, or n for a diagonal A); ``hopf`` must be a handle built from
+        its current value.  Returns phi (float64, one per query); the gradient
+        v* is available as ``hopf.last_grad``.  Second derivatives are not
+        provided."""
 
         @staticmethod
         def forward(ctx, x, t, A_param, hopf):
             out = hopf.eval(x, t)
+            hopf.last_grad = out["grad"]
             ctx.hopf = hopf
             ctx.save_for_backward(out["grad"])
-            return out["phi"].to(torch.float32), out["grad"]
+            return out["phi"]
 
         @staticmethod
-        def backward(ctx, g_phi, g_grad):
+        def backward(ctx, g_phi):
             (vstar,) = ctx.saved_tensors
             need_x, need_t, need_A = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
             gx, gt, gA = ctx.hopf.backward(g_phi.contiguous().to(torch.float32), vstar, need_x, need_t, need_A)
@@ -280,6 +285,7 @@ _HopfFn = None
 
 
 def HopfFn():
+    """The torch.autograd.Function class (created on first use)."""
     global _HopfFn
     if _HopfFn is None:
         _HopfFn = _autograd()
