@@ -9,6 +9,7 @@ d phi/dt) per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant mixed|fp32|bf16]
     python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+    python bench.py --workload ragged      # 512-instance ragged batch (one graph replay per step)
 
 For N > 1 launch under torch.distributed.run: every rank evaluates its own
 65,536 queries (weak scaling, no collective on the data path); the time is the
@@ -50,6 +51,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=192)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="dense", choices=["dense", "ragged"])
     return p.parse_args()
 
 
@@ -110,15 +112,21 @@ def peaks():
 
 
 def oracle_sample(A, w, x, t, count, tol):
-    """The FP64 oracle as it stands on `count` queries; returns (evals/s, threads, result)."""
+    """The FP64 oracle as it stands on `count` queries; returns (evals/s,
+    threads, result, seconds).  The oracle factors A + lambda I inside every
+    call; that factorisation (the counterpart of hopf_create, untimed on the
+    GPU) is timed by a call with no queries and taken out."""
     import oracle
     oracle.build()
     P = oracle.Problem(A, oracle.H_WL1, w=w, tol=tol, max_iter=MAX_ITER, stop_rule=oracle.STOP_UREL)
     xs = x[:count].astype(np.float64)
     ts = t[:count].astype(np.float64)
     t0 = time.perf_counter()
+    P.eval(np.zeros((0, A.shape[0])), np.zeros(0))
+    t_fact = time.perf_counter() - t0
+    t0 = time.perf_counter()
     r = P.eval(xs, ts)
-    dt = time.perf_counter() - t0
+    dt = max(time.perf_counter() - t0 - t_fact, 1e-9)
     return count / dt, oracle.num_threads(), r, dt
 
 
@@ -140,17 +148,197 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "dense_wl1_n%d" % args.n, "n": args.n, "batch_per_step": per_step,
-                       "note": "FP64 C oracle (plain loops, OpenMP over queries) on a bounded sample per step"},
+                       "note": "FP64 C oracle (plain loops, OpenMP over queries) on a bounded sample per step; "
+                        "the factorisation of A + lambda I is timed apart and excluded"},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": threads, "kind": "oracle",
                              "sample": "%d queries of the n=%d workload per step" % (per_step, args.n)},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+RAGGED_METRIC = ("Hopf evals/s, ragged batch of 512 instances (n log-uniform 16-4096, 64-8192 queries each, "
+                 "half diagonal FP32, half dense MIXED, H cycling l1 / weighted l1 / l2)")
+
+
+def ragged_workload():
+    """The 512 instances as HopfBatch descriptions, their inputs, and the
+    flat x / t of one step."""
+    import workloads as wl
+    inst = wl.ragged_instances(wl.ragged())
+    descs = [{"A": d["A"] if "A" in d else d["a"], "h_kind": d["h_kind"], "w": d["w"], "c0": d["c0"],
+              "lam": d["lam"], "tol": 1e-13 if "A" in d else 1e-12, "max_iter": 3000,
+              "dense": "A" in d} for d in inst]
+    counts = np.array([d["x"].shape[0] for d in inst], dtype=np.int64)
+    x = np.concatenate([d["x"].reshape(-1) for d in inst])
+    t = np.concatenate([d["t"] for d in inst])
+    return inst, descs, counts, x, t
+
+
+def ragged_cpu_sample(inst, descs, counts, count, seed=4901):
+    """The FP64 oracle on `count` queries drawn uniformly over all queries of
+    the batch, at the GPU's stop rule and tolerances.  The per-instance
+    Cholesky factor (the counterpart of hopf_create, which is not timed on the
+    GPU either) is timed on its own and taken out."""
+    import oracle
+    import workloads as wl
+    oracle.build()
+    qoff = np.concatenate([[0], np.cumsum(counts)])
+    picks = np.unique((wl.uniform(seed, count) * qoff[-1]).astype(np.int64))
+    by_inst = {}
+    for q in picks:
+        i = int(np.searchsorted(qoff, q, side="right") - 1)
+        by_inst.setdefault(i, []).append(int(q - qoff[i]))
+    total, done = 0.0, 0
+    for i, qs in by_inst.items():
+        d, e = inst[i], descs[i]
+        P = oracle.Problem(e["A"], e["h_kind"], w=e["w"], c0=e["c0"], lam=e["lam"], tol=e["tol"],
+                           max_iter=e["max_iter"], stop_rule=oracle.STOP_UREL)
+        t0 = time.perf_counter()
+        P.eval(np.zeros((0, d["n"])), np.zeros(0))
+        t_fact = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        P.eval(d["x"][qs].astype(np.float64), d["t"][qs].astype(np.float64))
+        total += max(time.perf_counter() - t0 - t_fact, 1e-9)
+        done += len(qs)
+    return done / total, oracle.num_threads(), done, total, len(by_inst)
+
+
+def run_ragged(args):
+    import torch
+    import paper_1605_01799_gb300 as hg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    inst, descs, counts, x, t = ragged_workload()
+    bd = [dict(e, precision=hg.P_MIXED if e["dense"] else hg.P_FP32, stop_rule=hg.STOP_UREL) for e in descs]
+    for e in bd:
+        e.pop("dense")
+    b = hg.HopfBatch(bd)
+    xd = torch.from_numpy(x).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    Q = int(counts.sum())
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    out = b.eval(counts, xd, td)  # the first call tunes the lane count and captures the graph
+    for _ in range(args.warmup):
+        out = b.eval(counts, xd, td, out=out)
+    torch.cuda.synchronize()
+    info = b.info()
+    iters = out["iters"].cpu().numpy().astype(np.float64)
+    status = out["status"].cpu().numpy()
+    clk_path = tempfile.mktemp(suffix=".csv")
+    clk = sample_clocks(clk_path)
+    time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = b.eval(counts, xd, td, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    if clk:
+        clk.terminate()
+        clk.wait()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = tt.item()
+    clocks = read_clocks(clk_path, local)
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        th = torch.from_numpy(t).pin_memory()
+        phih = torch.empty(Q, dtype=torch.float64).pin_memory()
+        gradh = torch.empty(x.size, dtype=torch.float32).pin_memory()
+        dth = torch.empty(Q, dtype=torch.float32).pin_memory()
+        steps_e2e = max(2, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(steps_e2e):
+            xd.copy_(xh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            out = b.eval(counts, xd, td, out=out)
+            phih.copy_(out["phi"], non_blocking=True)
+            gradh.copy_(out["grad"], non_blocking=True)
+            dth.copy_(out["dphidt"], non_blocking=True)
+        f1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = f0.elapsed_time(f1) / steps_e2e
+        e2e = {"value": ws * Q / (ems * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+               "d2h_bytes_per_step": int(Q * 8 + x.size * 4 + Q * 4), "ms_per_step": ems}
+
+    # work-weighted roofline: dense instances on the tensor pipe (4 n x n MMA
+    # passes per iteration plus 3 for setup and the final pass, MIXED form),
+    # diagonal ones on the FP32 pipe (about 10 flop per coordinate-iteration)
+    pk = peaks()
+    tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
+    alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    qoff = np.concatenate([[0], np.cumsum(counts)])
+    tc_flops, alu_flops, launches = 0.0, 0.0, 0
+    for i, e in enumerate(descs):
+        K = iters[qoff[i]:qoff[i + 1]]
+        n = inst[i]["n"]
+        if counts[i] == 0:
+            continue
+        if e["dense"]:
+            tc_flops += float(np.sum(2.0 * n * n * (4.0 * K + 3.0)))
+            launches += 4
+        else:
+            alu_flops += float(np.sum(10.0 * n * K))
+            launches += 1
+    t_roof = tc_flops / (tc_peak * 1e12) + alu_flops / (alu_peak * 1e12)
+    frac = t_roof / (ms * 1e-3)
+    roof = {"bound": "tensor+alu (work-weighted)", "achieved": frac, "peak": 1.0,
+            "unit": "fraction of the work-weighted roofline time", "frac": frac, "traffic": None,
+            "roofline_ms": 1e3 * t_roof, "tensor_flops": tc_flops, "alu_flops": alu_flops,
+            "peak_source": "tensor: MEASURED_PEAKS.json bf16_tflops_sustained (measured) %.1f TFLOP/s; "
+                           "alu: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived) %.1f TFLOP/s" % (tc_peak, alu_peak)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, threads, done, secs, ninst = ragged_cpu_sample(inst, descs, counts, max(8, args.cpu_sample // 2))
+        cpu = {"value": rate, "unit": "evals/s", "cores": threads, "kind": "oracle",
+               "sample": "%d queries drawn uniformly over the batch (%d instances), FP64 oracle, same stop rule; "
+                         "%.1f s of solves, per-instance factorisation excluded" % (done, ninst, secs)}
+    if rank == 0:
+        line = {"metric": RAGGED_METRIC, "value": ws * Q / (ms * 1e-3), "unit": "evals/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (diagonal) / bf16+f16 (dense)",
+                "data": "synthetic",
+                "config": {"workload": "ragged_512", "instances": len(inst), "queries": Q,
+                           "x_floats": int(x.size), "lanes": info["nstreams"], "tuned_ms": info["tuned_ms"],
+                           "parallelism": "replicas" if ws == 1 else "dp%d (each rank its own batch)" % ws,
+                           "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
+                "iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+                "status_ok_frac": float((status == 0).mean()), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": launches * args.steps}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ragged":
+        return run_ragged(args)
     import torch
     import paper_1605_01799_gb300 as hg
 
@@ -277,7 +465,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, threads, r, dt = oracle_sample(A, w, x, t, args.cpu_sample, TOL)
         cpu = {"value": rate, "unit": "evals/s", "cores": threads, "kind": "oracle",
-               "sample": "first %d queries of the same workload, FP64 oracle, same stop rule (%.1f s)"
+               "sample": "first %d queries of the same workload, FP64 oracle, same stop rule (%.1f s of solves; "
+                         "the factorisation of A + lambda I excluded)"
                          % (args.cpu_sample, dt)}
         # accuracy of the timed outputs on a few queries against a tight oracle run
         import oracle
@@ -307,7 +496,7 @@ def main():
                 "iters": {"mean": float(K.mean()), "max": int(K.max()), "min": int(K.min())},
                 "status_ok_frac": float((status == 0).mean()),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * args.steps, "accuracy": accuracy}
+                "gpu_launches": (3 if prec == hg.P_FP32 else 4) * args.steps, "accuracy": accuracy}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -203,6 +203,42 @@ hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int6
 hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
                           float* g_t, float* g_A, cudaStream_t stream);
 
+/* ---- ragged batches -----------------------------------------------------
+ * Many independent instances (each with its own A, H, n and number of
+ * queries) evaluated together.  Queries share no state (Section 1; Section
+ * 4.5 runs them one per core), so the batch is a set of single
+ * evaluations recorded into one CUDA graph and replayed by later calls that
+ * pass the same buffers and counts.  In the graph, dense instances with at
+ * least one 128 x 128 tile per SM run one after another on the whole GPU;
+ * the smaller dense instances then run side by side on worker streams
+ * ("lanes"), each capped at an equal share of the SMs so that the
+ * cooperative grids in flight fit together; diagonal instances are spread
+ * over the lanes and overlap both phases.  Instances go longest-first to the
+ * least loaded lane.
+ *
+ * Layout: instance i has counts[i] queries.  Per-query arrays (t, phi, dphidt,
+ * iters, qstatus) hold the instances one after another: instance i starts at
+ * row sum_{j<i} counts[j].  x and grad hold instance i's rows of length n_i
+ * starting at element sum_{j<i} counts[j] * n_j.  counts is a HOST array;
+ * everything else is device memory, as for hopf_eval.
+ *
+ * The first hopf_batch_eval call tunes the schedule: it captures and times
+ * the batch with 1, 2, 4, 8 and 16 lanes and keeps the fastest (so it
+ * synchronises `stream`; its results are those of the kept graph);
+ * hopf_batch_info reports the choice.  Instances
+ * with FP64 precision are not accepted. */
+typedef struct hopf_batch_s* hopf_batch;
+hopf_status hopf_batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out, cudaStream_t stream);
+void hopf_batch_destroy(hopf_batch b);
+hopf_status hopf_batch_workspace_size(hopf_batch b, const int64_t* counts, size_t* bytes);
+hopf_status hopf_batch_eval(hopf_batch b, const int64_t* counts, const float* x, const float* t, double* phi,
+                            float* grad, float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace,
+                            size_t ws_bytes, cudaStream_t stream);
+/* nstreams: worker streams chosen (0 before the first eval); used_graph: 1
+ * once the batch runs as a graph replay; tuned_ms[5]: the timed candidates
+ * (may be NULL). */
+hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms);
+
 /* Instrumentation: when `start` and `stop` are non-NULL CUDA events, every
  * later hopf_eval on this handle records `start` on its stream immediately
  * before the main solver kernel and `stop` immediately after it, so a caller

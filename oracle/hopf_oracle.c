@@ -256,9 +256,9 @@ void orc_solve(const orc_problem *p, const double *L, const double *x, double t,
 }
 
 /* Batch of queries: x is [batch][n] row-major, t is [batch]; grad is
- * [batch][n]; results are per query.  Queries are independent (the paper's
- * "totally parallelizable" remark, Section 4.5); with OpenMP they run one per
- * thread.  Returns 0, or -1 if A + lambda I is not SPD. */
+ * [batch][n]; results are per query.  Queries are independent: each one is
+ * its own small problem with no shared state (Section 1; Section 4.5 runs
+ * them one per core); with OpenMP they run one per thread.  Returns 0, or -1 if A + lambda I is not SPD. */
 int orc_eval_batch(const orc_problem *p, int64_t batch, const double *x, const double *t,
                    double *grad, orc_result *res)
 {

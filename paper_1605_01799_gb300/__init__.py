@@ -28,7 +28,8 @@ Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
            "hopf_backward",
-           "hopf_profile_events", "hopf_set_compaction", "hopf_last_error", "hopf_version"]
+           "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
+           "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -70,6 +71,11 @@ def lib():
             "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_set_compaction": ([_vp, _i32], ctypes.c_int),
+            "hopf_batch_create": ([ctypes.POINTER(hopf_desc), _i32, ctypes.POINTER(_vp), _vp], ctypes.c_int),
+            "hopf_batch_destroy": ([_vp], None),
+            "hopf_batch_workspace_size": ([_vp, _vp, ctypes.POINTER(_sz)], ctypes.c_int),
+            "hopf_batch_eval": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
             "hopf_version": ([], ctypes.c_char_p),
         }
@@ -187,6 +193,72 @@ class Hopf:
         _check(lib().hopf_backward(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
                                    _stream(stream)))
         return gx, gt, gA
+
+
+class HopfBatch:
+    """A ragged batch of instances evaluated as one CUDA graph replay.
+    ``instances``: list of dicts with keys A (1-D diagonal or 2-D dense),
+    h_kind and optionally w, centre, c0, lam, tol, max_iter, precision,
+    stop_rule (as for Hopf)."""
+
+    def __init__(self, instances, stream=None):
+        self._keep = []
+        descs = (hopf_desc * len(instances))()
+        self.ns = []
+        for i, d in enumerate(instances):
+            A = np.ascontiguousarray(d["A"], dtype=np.float64)
+            w = d.get("w")
+            w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+            c = d.get("centre")
+            c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+            self._keep += [A, w, c]
+            descs[i] = hopf_desc(A.shape[0], A_DIAG if A.ndim == 1 else A_DENSE, A.ctypes.data,
+                                 None if c is None else c.ctypes.data, float(d.get("c0", 0.5)), int(d["h_kind"]),
+                                 None if w is None else w.ctypes.data, float(d.get("lam", 1.0)),
+                                 float(d.get("tol", 1e-13)), int(d.get("max_iter", 1000)),
+                                 int(d.get("precision", P_MIXED if A.ndim == 2 else P_FP32)),
+                                 int(d.get("stop_rule", STOP_UREL)))
+            self.ns.append(A.shape[0])
+        h = ctypes.c_void_p()
+        _check(lib().hopf_batch_create(descs, len(instances), ctypes.byref(h), _stream(stream)))
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hopf_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def eval(self, counts, x, t, out=None, stream=None):
+        """counts: per-instance query counts; x: flat float32 cuda tensor of
+        sum(counts[i] * n_i) values; t: float32 [sum(counts)]."""
+        import torch
+        cnt = np.ascontiguousarray(counts, dtype=np.int64)
+        Q = int(cnt.sum())
+        X = int((cnt * np.array(self.ns, dtype=np.int64)).sum())
+        assert x.numel() == X and t.numel() == Q
+        if out is None:
+            out = {"phi": torch.empty(Q, dtype=torch.float64, device=x.device),
+                   "grad": torch.empty(X, dtype=torch.float32, device=x.device),
+                   "dphidt": torch.empty(Q, dtype=torch.float32, device=x.device),
+                   "iters": torch.empty(Q, dtype=torch.int32, device=x.device),
+                   "status": torch.empty(Q, dtype=torch.uint8, device=x.device)}
+        b = ctypes.c_size_t()
+        _check(lib().hopf_batch_workspace_size(self.handle, cnt.ctypes.data, ctypes.byref(b)))
+        if self._ws is None or self._ws.numel() < max(b.value, 1):
+            self._ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
+        _check(lib().hopf_batch_eval(self.handle, cnt.ctypes.data, _ptr(x), _ptr(t), _ptr(out["phi"]),
+                                     _ptr(out["grad"]), _ptr(out["dphidt"]), _ptr(out["iters"]),
+                                     _ptr(out["status"]), _ptr(self._ws), self._ws.numel(), _stream(stream)))
+        return out
+
+    def info(self):
+        ns, ug = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 5)()
+        _check(lib().hopf_batch_info(self.handle, ctypes.byref(ns), ctypes.byref(ug), ms))
+        return {"nstreams": ns.value, "used_graph": bool(ug.value), "tuned_ms": list(ms)}
 
 
 def _parts_array(parts):

@@ -379,6 +379,9 @@ hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const flo
   HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_simt, NT, 0));
   if (per_sm < 1) return fail(HOPF_ECUDA, "dense FP32 solver: kernel does not fit on an SM");
   int grid = per_sm * h->num_sms;
+  // under a cap (ragged batches) at most one CTA per SM of the share, so that
+  // any unplaced CTA always finds an SM free of other cooperative CTAs
+  if (h->grid_cap > 0 && grid > h->grid_cap) grid = h->grid_cap;
   const int items = a.rt * a.ct;
   if (grid > items) grid = items;
   void* args[] = {&a};

@@ -1056,6 +1056,21 @@ __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restr
 
 }  // namespace tc
 
+size_t tc_smem_bytes() { return 1024 + (size_t)tc::STAGES * tc::STAGE_BYTES + sizeof(tc::Smem); }
+
+// Raise the kernel's dynamic shared memory limit once (at handle creation, so
+// that later evaluations stay capturable in a CUDA graph).
+hopf_status dense_tc_prepare() {
+  static bool done[256] = {};
+  int dev = 0;
+  HOPF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 256 && !done[dev]) {
+    HOPF_CUDA(cudaFuncSetAttribute(tc::k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+    done[dev] = true;
+  }
+  return HOPF_OK;
+}
+
 hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
                           float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
   using namespace tc;
@@ -1123,12 +1138,15 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.lam = (float)h->lambda;
   a.tol = (float)h->tol;
 
-  const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + sizeof(Smem);
-  HOPF_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = tc_smem_bytes();
   int per_sm = 0;
   HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc, NT, smem));
   if (per_sm < 1) return fail(HOPF_ECUDA, "dense tensor-core solver: kernel does not fit on an SM");
-  const int grid = h->num_sms;  // one CTA per SM: each holds all 512 TMEM columns
+  // one CTA per SM (each holds all 512 TMEM columns), and no more CTAs than
+  // tiles: small problems leave the other SMs to concurrent work
+  const int tiles = a.rt * a.ct;
+  const int sms = h->grid_cap > 0 && h->grid_cap < h->num_sms ? h->grid_cap : h->num_sms;
+  const int grid = tiles < sms ? (tiles > 0 ? tiles : 1) : sms;
   void* args[] = {&a};
   if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
   HOPF_CUDA(cudaLaunchCooperativeKernel((const void*)k_dense_tc, dim3(grid), dim3(NT), args, smem, stream));

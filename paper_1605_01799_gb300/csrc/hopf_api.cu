@@ -49,6 +49,50 @@ extern "C" {
 
 const char* hopf_last_error(void) { return g_last_error.c_str(); }
 
+hopf_status hopf_batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out, cudaStream_t stream) {
+  set_error("");
+  if (!descs || !out || count < 1) return fail(HOPF_EINVAL, "hopf_batch_create: need descs, out and count >= 1");
+  *out = nullptr;
+  return batch_create(descs, count, out, stream);
+}
+
+void hopf_batch_destroy(hopf_batch b) { batch_destroy(b); }
+
+static hopf_status check_counts(hopf_batch b, const int64_t* counts) {
+  if (!b || !counts) return fail(HOPF_EINVAL, "hopf_batch: null batch or counts");
+  for (size_t i = 0; i < batch_count(b); ++i)
+    if (counts[i] < 0 || counts[i] > ((int64_t)1 << 31)) return fail(HOPF_EINVAL, "hopf_batch: bad query count");
+  return HOPF_OK;
+}
+
+hopf_status hopf_batch_workspace_size(hopf_batch b, const int64_t* counts, size_t* bytes) {
+  set_error("");
+  hopf_status s = check_counts(b, counts);
+  if (s != HOPF_OK) return s;
+  if (!bytes) return fail(HOPF_EINVAL, "hopf_batch_workspace_size: null bytes");
+  *bytes = batch_workspace(b, counts);
+  return HOPF_OK;
+}
+
+hopf_status hopf_batch_eval(hopf_batch b, const int64_t* counts, const float* x, const float* t, double* phi,
+                            float* grad, float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace,
+                            size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_counts(b, counts);
+  if (s != HOPF_OK) return s;
+  if (!x || !t || !phi || !grad) return fail(HOPF_EINVAL, "hopf_batch_eval: null x, t, phi or grad");
+  const size_t need = batch_workspace(b, counts);
+  if (need > 0 && (!workspace || ws_bytes < need)) return fail(HOPF_EINVAL, "hopf_batch_eval: workspace too small");
+  if (need > 0 && ((uintptr_t)workspace & 255u)) return fail(HOPF_EINVAL, "hopf_batch_eval: workspace must be 256-byte aligned");
+  return batch_eval(b, counts, x, t, phi, grad, dphidt, iters, qstatus, workspace, ws_bytes, stream);
+}
+
+hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms) {
+  set_error("");
+  if (!b) return fail(HOPF_EINVAL, "hopf_batch_info: null batch");
+  return batch_info(b, nstreams, used_graph, tuned_ms);
+}
+
 hopf_status hopf_set_compaction(hopf_handle h, int32_t on) {
   set_error("");
   if (!h) return fail(HOPF_EINVAL, "hopf_set_compaction: null handle");
@@ -163,6 +207,7 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
     H_CALL(cudaStreamSynchronize(stream));
   } else {
     hopf_status s = dense_setup(h, d.A, stream);
+    if (s == HOPF_OK && d.precision != HOPF_P_FP32) s = dense_tc_prepare();
     if (s != HOPF_OK) {
       free_handle(h);
       return s;

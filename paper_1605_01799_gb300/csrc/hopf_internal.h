@@ -14,6 +14,10 @@ struct hopf_handle_s {
   int a_kind = 0, h_kind = 0, precision = 0, stop_rule = 0, max_iter = 0;
   double c0 = 0, lambda = 1, tol = 0;
   int device = 0, num_sms = 0;
+  // SMs one cooperative dense launch may occupy (0: all).  A ragged batch sets
+  // it to its per-stream share so that the dense solvers running side by side
+  // on different streams fit on the GPU together.
+  int grid_cap = 0;
   // device copies (FP64 inputs)
   double* d_A = nullptr;       // diagonal: [n]; dense: [n][n]
   double* d_c = nullptr;       // [n] or null
@@ -107,6 +111,8 @@ size_t dense_workspace(const hopf_handle h, int64_t batch);
 hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_bytes, DenseWs* d);
 hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
                             float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+size_t tc_smem_bytes();
+hopf_status dense_tc_prepare();
 hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
                           float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
 
@@ -115,5 +121,15 @@ hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const flo
                      float* g_A, cudaStream_t stream);
 
 int sm_count(int device);
+
+// ---- ragged batches (batch.cu) ----
+hopf_status batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out, cudaStream_t stream);
+void batch_destroy(hopf_batch b);
+size_t batch_workspace(hopf_batch b, const int64_t* counts);
+size_t batch_count(hopf_batch b);
+hopf_status batch_eval(hopf_batch b, const int64_t* counts, const float* x, const float* t, double* phi, float* grad,
+                       float* dphidt, int32_t* iters, uint8_t* qstatus, void* ws, size_t ws_bytes,
+                       cudaStream_t stream);
+hopf_status batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms);
 
 }  // namespace hopf

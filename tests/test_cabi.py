@@ -94,3 +94,27 @@ def test_null_arguments(hg):
     assert L.hopf_union_eval(None, 0, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
     assert L.hopf_backward(None, 4, None, None, None, None, None, None) == hg.HOPF_EINVAL
     L.hopf_destroy(None)
+
+
+def test_batch_rejects_bad_arguments(hg):
+    L = hg.lib()
+    out = ctypes.c_void_p()
+    assert L.hopf_batch_create(None, 1, ctypes.byref(out), None) == hg.HOPF_EINVAL
+    d, keep = _desc(hg)
+    descs = (hg.hopf_desc * 2)(d, d)
+    assert L.hopf_batch_create(descs, 0, ctypes.byref(out), None) == hg.HOPF_EINVAL
+    # an FP64 instance is refused, and a bad instance is named in the message
+    descs[1].precision = hg.P_FP64
+    assert L.hopf_batch_create(descs, 2, ctypes.byref(out), None) == hg.HOPF_EUNSUPPORTED
+    assert not out.value
+    descs[1].precision = hg.P_FP32
+    descs[0].n = 0
+    assert L.hopf_batch_create(descs, 2, ctypes.byref(out), None) == hg.HOPF_EINVAL
+    assert "instance 0" in L.hopf_last_error().decode()
+    b = ctypes.c_size_t()
+    cnt = np.zeros(2, np.int64)
+    assert L.hopf_batch_workspace_size(None, cnt.ctypes.data, ctypes.byref(b)) == hg.HOPF_EINVAL
+    assert L.hopf_batch_eval(None, cnt.ctypes.data, None, None, None, None, None, None, None, None, 0,
+                             None) == hg.HOPF_EINVAL
+    assert L.hopf_batch_info(None, None, None, None) == hg.HOPF_EINVAL
+    L.hopf_batch_destroy(None)

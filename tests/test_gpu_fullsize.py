@@ -160,3 +160,65 @@ def test_dense_n2048_b32768_forward_backward(hg, orc):
             assert abs(fd - exact) <= 1e-5 * max(1, abs(fd)), (q, i1, i2, fd, exact)
             bound = 0.5 * f * (abs(vq[i1]) * dv + abs(vq[i2]) * dv + dv * dv)
             assert abs(gAq[i1, i2] * f - exact) <= bound + 1e-6 * abs(exact), (q, i1, i2, gAq[i1, i2] * f, exact)
+
+
+def _h_of(g, h_kind, w):
+    g = np.abs(g.astype(np.float64))
+    if h_kind == 0:
+        return g.sum(1)
+    if h_kind == 1:
+        return (g * w).sum(1)
+    return np.sqrt((g * g).sum(1))
+
+
+def test_ragged_512_instances(hg, orc):
+    """Ragged batch: 512 instances, n log-uniform in [16, 4096], 64 to 8,192
+    queries each; instances 0-255 diagonal (FP32), 256-511 dense (MIXED); H
+    cycles l1, weighted l1, l2; one graph replay.  Every query: converged,
+    finite, d phi/dt = -H(grad).  Sampled queries (first and last query of
+    16 seeded instances, plus the largest dense instance) against the oracle
+    with the bars of the single-instance tests."""
+    import torch
+    descs = wl.ragged()
+    inst = wl.ragged_instances(descs)
+    bd = [{"A": d["A"] if "A" in d else d["a"], "h_kind": d["h_kind"], "w": d["w"], "c0": d["c0"],
+           "lam": d["lam"], "tol": 1e-13 if "A" in d else 1e-12, "max_iter": 3000,
+           "precision": hg.P_MIXED if "A" in d else hg.P_FP32, "stop_rule": hg.STOP_UREL} for d in inst]
+    b = hg.HopfBatch(bd)
+    counts = np.array([d["x"].shape[0] for d in inst], dtype=np.int64)
+    ns = np.array([d["n"] for d in inst], dtype=np.int64)
+    x = torch.tensor(np.concatenate([d["x"].reshape(-1) for d in inst]), device="cuda")
+    t = torch.tensor(np.concatenate([d["t"] for d in inst]), device="cuda")
+    out = b.eval(counts, x, t)
+    torch.cuda.synchronize()
+    info = b.info()
+    assert info["used_graph"] and info["nstreams"] >= 1
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy()
+    st = out["status"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    dt = out["dphidt"].cpu().numpy()
+    del x, out
+    assert (st == hg.Q_OK).all(), np.bincount(st)
+    assert (it < 3000).all() and np.isfinite(phi).all() and np.isfinite(g).all()
+    qoff = np.concatenate([[0], np.cumsum(counts)])
+    xoff = np.concatenate([[0], np.cumsum(counts * ns)])
+    for i, d in enumerate(inst):
+        gi = g[xoff[i]:xoff[i + 1]].reshape(counts[i], ns[i])
+        Hi = _h_of(gi, d["h_kind"], d["w"])
+        assert np.allclose(dt[qoff[i]:qoff[i + 1]], -Hi, rtol=1e-5, atol=1e-5), i
+    pick = sorted(set(_sample(77005, 16, len(inst)).tolist()) |
+                  {int(np.argmax(np.where([("A" in d) for d in inst], ns, 0)))})
+    for i in pick:
+        d = inst[i]
+        A = d["A"] if "A" in d else d["a"]
+        q = np.unique([0, counts[i] - 1])
+        P = orc.Problem(A, d["h_kind"], w=d["w"], c0=d["c0"], lam=d["lam"], tol=1e-28, max_iter=50000,
+                        stop_rule=orc.STOP_UREL)
+        ref = P.eval(d["x"][q].astype(np.float64), d["t"][q].astype(np.float64))
+        gi = g[xoff[i]:xoff[i + 1]].reshape(counts[i], ns[i])[q]
+        ep = np.abs(phi[qoff[i] + q] - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+        eg = np.linalg.norm(gi - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+        assert ep.max() <= 1e-6, (i, ep.max())
+        assert eg.max() <= (6e-6 if "A" in d else 2e-5), (i, eg.max())
+    b.close()

@@ -145,6 +145,39 @@ def ragged_instance(desc, w=4):
     return out
 
 
+def ragged_instances(descs, w=4, workers=None):
+    """``ragged_instance`` for every description, drawn in a pool of
+    ``spawn``-started processes (safe after CUDA is initialised).  x, t, the
+    diagonals and weights equal those of the serial loop bit for bit; a dense
+    A agrees to rounding (the QR factorisation behind the Haar Q runs with
+    one BLAS thread per worker, which may round differently)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1 or len(descs) < 2:
+        return [ragged_instance(d, w) for d in descs]
+    # largest first so that the pool stays busy to the end
+    order = sorted(range(len(descs)), key=lambda i: -descs[i]["n"] * (descs[i]["n"] if descs[i]["dense"] else 1))
+    out = [None] * len(descs)
+    # one BLAS thread per worker: the pool is the parallelism
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            futs = {ex.submit(ragged_instance, descs[i], w): i for i in order}
+            for f in cf.as_completed(futs):
+                out[futs[f]] = f.result()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out
+
+
 # --- workload 5: differentiation, n = 2048, H = l1 ---------------------------
 def dense_l1_grad(n=2048, batch=32768, w=5):
     A, Q, s = spd_matrix(1000 * w + 1, 1000 * w + 2, n)
