@@ -54,8 +54,13 @@ namespace tc {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 2;        // 16 KB: 128 rows x 128 bytes
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // up to 2 A tiles + 2 B tiles
-constexpr int NT = 320;                        // 2 role warps + 8 epilogue warps
-constexpr int NEPI = 256;                      // epilogue threads
+#ifndef HOPF_TC_EPI_WARPS
+#define HOPF_TC_EPI_WARPS 16
+#endif
+constexpr int EPI_WARPS = HOPF_TC_EPI_WARPS;   // a multiple of 4: the same number per TMEM lane quadrant
+constexpr int NEPI = EPI_WARPS * 32;           // epilogue threads
+constexpr int NT = 64 + NEPI;                  // 2 role warps + the epilogue warps
+constexpr int CPW = BN / (EPI_WARPS / 4);      // tile columns per epilogue warp
 constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 accumulators x 128 columns
 constexpr int FORM_MIXED = 0, FORM_BF16 = 1;
 constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3;
@@ -67,6 +72,7 @@ constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 // ufin, sfin, fpart, the final-pass operand planes.
 struct TcArgs {
   CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mP1b, mP2b, mG, mP3;  // mP3: the g plane read as the third split of p
+  CUtensorMap mU[2], mY[2];  // FP32 state planes, for L2 prefetch of the epilogue's tiles
   float* y[2];
   float* u[2];
   uint16_t* p1[2];
@@ -137,6 +143,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   return true;
 }
 
+// Bring a 128 x 128 tile of an FP32 state plane into L2 ahead of the
+// epilogue that reads it (a hint: no shared memory, no completion to wait on).
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -201,7 +215,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NEPI) : "memory"); }
 // the first 128 epilogue threads only (one per slot of a tile)
 __device__ __forceinline__ void epi_sync_half() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -282,6 +296,12 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, x, ph, c)) continue;
+    // the epilogue of this item reads u (and y) of its tile one to two items
+    // from now: start the DRAM reads now
+    if (ph != PH_F) {
+      tma_prefetch_l2(&a.mU[x.cb], r * BM, c * BN);
+      if (ph != PH_B) tma_prefetch_l2(&a.mY[x.cb], r * BM, c * BN);
+    }
     for (int kb = 0; kb < nk; ++kb) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
         const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
@@ -449,7 +469,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;      // 0..255
   const int qd = warp & 3;              // TMEM lane quadrant of this warp
-  const int jbase = ((warp - 2) >> 2) * (BN / 2);  // this warp's half of the columns
+  const int jbase = ((warp - 2) >> 2) * CPW;  // this warp's share of the columns
   const int rloc = qd * 32 + lane;      // row within the tile
   const int items = phase_items(a, x, ph);
   const int np = a.np, hk = a.h_kind;
@@ -500,7 +520,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     const float wr = a.w[row];
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
     const bool first = S.first;
-    for (int j0 = jbase; good && j0 < jbase + BN / 2; j0 += 16) {
+    for (int j0 = jbase; good && j0 < jbase + CPW; j0 += 16) {
       float d1[16];
       tmem_ld16(tbase + j0, d1);
       if constexpr (ph == PH_A) {
@@ -625,7 +645,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;
   const int qd = warp & 3;
-  const int jbase = ((warp - 2) >> 2) * (BN / 2);
+  const int jbase = ((warp - 2) >> 2) * CPW;
   const int rloc = qd * 32 + lane;
   const int items = phase_items(a, x, PH_F), nk = a.np / BK;
   const int np = a.np, hk = a.h_kind;
@@ -639,9 +659,9 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     if (S.epi_abort) return;
     const uint32_t lanebase = S.tmem_base + ((uint32_t)(qd * 32) << 16);
     // promote each 128-wide K chunk of D1 into FP32 registers (round to nearest)
-    float acc[BN / 2];
+    float acc[CPW];
 #pragma unroll
-    for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
+    for (int j = 0; j < CPW; ++j) acc[j] = 0.f;
     bool good = true;
     for (int chunk = 0; chunk < nk / 2; ++chunk) {
       const uint32_t slot = chunk & 1;
@@ -649,13 +669,13 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
       ++st.cf[slot];
       if (good) {
         tc_fence_after();
-        float v[32];
-        tmem_ld32(lanebase + slot * BN + jbase, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += v[j];
-        tmem_ld32(lanebase + slot * BN + jbase + 32, v);
+        for (int j0 = 0; j0 < CPW; j0 += 16) {
+          float v[16];
+          tmem_ld16(lanebase + slot * BN + jbase + j0, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[32 + j] += v[j];
+          for (int j = 0; j < 16; ++j) acc[j0 + j] += v[j];
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -667,16 +687,18 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     if (good) tc_fence_after();
     const int row = r * BM + rloc;
     const float wr = a.w[row];
-    for (int g = 0; good && g < 2; ++g) {
-      const int j0 = jbase + 32 * g;
-      float d2[32], d3[32];
-      tmem_ld32(lanebase + 256 + j0, d2);
-      tmem_ld32(lanebase + 384 + j0, d3);
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
+    for (int g = 0; g < CPW / 16; ++g) {
+      if (!good) break;
+      const int j0 = jbase + 16 * g;
+      float d2[16], d3[16];
+      tmem_ld16(lanebase + 256 + j0, d2);
+      tmem_ld16(lanebase + 384 + j0, d3);
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
         const int j = j0 + jj;
         // A p = D1 + 2^-11 D2 + 2^-22 D3
-        const float ap = acc[32 * g + jj] + (d2[jj] + d3[jj] * (1.f / kLoScale)) * (1.f / kLoScale);
+        const float ap = acc[16 * g + jj] + (d2[jj] + d3[jj] * (1.f / kLoScale)) * (1.f / kLoScale);
         double f0 = 0.0, f1 = 0.0;
         if (S.qact[j]) {
           const int64_t q = (int64_t)c * BN + j;
@@ -719,7 +741,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
 // Decision for iteration k (convergence of iteration k-1), one thread per
 // slot of a column tile.  A slot that stops (converged, or at max_iter) is
 // retired at once: its u and l2 scale go to the query-indexed final arrays,
-// the 256 epilogue threads copying the row together.
+// the epilogue threads copying the row together.
 __device__ __noinline__ void prepass(const TcArgs& a, Smem& S, int k, const Ctx& x) {
   const int et = threadIdx.x - 64;
   int* const QA = a.qact[x.cb];
@@ -819,7 +841,7 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
       }
     }
     epi_sync();
-    // all active rows of the tile at once: 256 threads stream (slot, 4-element)
+    // all active rows of the tile at once: the epilogue threads stream (slot, 4-element)
     // pieces, so many loads are in flight
     const int per_row = np / 4, total = BN * per_row;
     for (int e0 = et; e0 < total; e0 += 4 * NEPI) {
@@ -886,7 +908,9 @@ __device__ __noinline__ void prep_final_operand(const TcArgs& a) {
   }
 }
 
-// 10 warps: 3 share a sub-partition's 16,384 registers, hence 168 per thread.
+// Registers: each of the 4 sub-partitions holds 16,384, shared by the warps
+// placed on it (warp w on sub-partition w % 4): 18 warps put 5 on two of them,
+// hence at most 96 per thread; 10 warps allow 168.
 __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -900,12 +924,12 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(sa(&S.tfull[b]), 1);
-      mbar_init(sa(&S.tempty[b]), 8);
+      mbar_init(sa(&S.tempty[b]), EPI_WARPS);
     }
     mbar_init(sa(&S.drain), 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(sa(&S.cfull[b]), 1);
-      mbar_init(sa(&S.cempty[b]), 8);
+      mbar_init(sa(&S.cempty[b]), EPI_WARPS);
     }
     S.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1039,6 +1063,21 @@ static bool encode(CUtensorMap* m, const void* ptr, int64_t rows, int np, bool b
   return r == CUDA_SUCCESS;
 }
 
+// 2-D tensor [rows][np] of FP32, box 128 rows x 128 elements, no swizzle
+// (used for L2 prefetch only).
+static bool encode_f32(CUtensorMap* m, const void* ptr, int64_t rows, int np) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)np * 4};
+  cuuint32_t box[2] = {128, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // FP16 split of y (MIXED: p^0 = y) or BF16 r^0 = y + lambda y (BF16 form).
 __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restrict__ p1, uint16_t* __restrict__ p2,
                                   int64_t total, int form, float lam) {
@@ -1091,7 +1130,10 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
             encode(&a.mM, h->d_Mbf, np, np, true) &&
             encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
             encode(&a.mP1b, w.ph_b, w.B_pad, np, false) && encode(&a.mP2b, w.pl_b, w.B_pad, np, false) &&
-            encode(&a.mG, w.g, w.B_pad, np, true);
+            encode(&a.mG, w.g, w.B_pad, np, true) && encode_f32(&a.mU[0], w.u, w.B_pad, np) &&
+            encode_f32(&a.mY[0], w.y, w.B_pad, np) &&
+            encode_f32(&a.mU[1], form == FORM_MIXED ? w.u_b : w.u, w.B_pad, np) &&
+            encode_f32(&a.mY[1], form == FORM_MIXED ? w.y_b : w.y, w.B_pad, np);
   if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
   a.y[0] = w.y;
   a.y[1] = w.y_b;
