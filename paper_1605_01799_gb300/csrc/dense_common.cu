@@ -22,7 +22,7 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 
   s[2] = tc ? B_pad * np * 2 : 0;        // ph
   s[3] = tc ? B_pad * np * 2 : 0;        // pl
   s[4] = tc ? B_pad * np * 2 : 0;        // g
-  s[5] = (size_t)2 * 2 * rt * B_pad * 4; // part
+  s[5] = (size_t)2 * 2 * 2 * rt * B_pad * 4; // part (two buffer sets; the FP32 solver uses the first)
   s[6] = (size_t)2 * rt * B_pad * 8;     // fpart
   s[7] = B_pad * 4;                      // tau
   s[8] = B_pad * 4;                      // tq
@@ -31,14 +31,14 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 
   s[11] = B_pad * 4;                     // qdone
   s[12] = 64;                            // bar (16 unsigned)
   s[13] = 64;                            // err
-  s[14] = B_pad * 4;                     // qact
-  s[15] = (B_pad / 128) * 4;             // tile_act
+  s[14] = 2 * B_pad * 4;                 // qact (by decision parity)
+  s[15] = 2 * (B_pad / 128) * 4;         // tile_act (tensor-core solver: last decision with active slots, and its count)
   s[16] = tc ? B_pad * np * 4 : 0;       // y_b
   s[17] = tc ? B_pad * np * 4 : 0;       // u_b
   s[18] = tc ? B_pad * np * 2 : 0;       // ph_b
   s[19] = tc ? B_pad * np * 2 : 0;       // pl_b
   s[20] = B_pad * 4;                     // scale_b
-  s[21] = B_pad * 4;                     // qact_b
+  s[21] = 2 * B_pad * 4;                 // qact_b (by decision parity)
   s[22] = 2 * B_pad * 4;                 // sq
   s[23] = tc ? B_pad * np * 4 : 0;       // ufin
   s[24] = B_pad * 4;                     // sfin
@@ -120,6 +120,7 @@ __global__ void k_dense_init(const float* __restrict__ x, const float* __restric
 hopf_status dense_init(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s) {
   HOPF_CUDA(cudaMemsetAsync(w.bar, 0, 64, s));
   HOPF_CUDA(cudaMemsetAsync(w.err, 0, 64, s));
+  HOPF_CUDA(cudaMemsetAsync(w.tile_act, 0, (size_t)2 * (w.B_pad / 128) * 4, s));
   k_dense_init<<<(unsigned)w.B_pad, 256, 0, s>>>(x, t, h->d_cf, h->n, h->n_pad, w.B, w.B_pad, (float)h->lambda, w.y,
                                                  w.u, w.tau, w.tq, w.qiter, w.qdone, w.sq, w.taus);
   HOPF_CUDA(cudaGetLastError());

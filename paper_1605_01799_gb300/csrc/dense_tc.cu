@@ -77,17 +77,17 @@ struct TcArgs {
   float* u[2];
   uint16_t* p1[2];
   uint16_t* p2[2];
-  float* scale[2];
   float* taus[2];     // t / lambda by slot
-  int* qact[2];       // 1 active, 2 retiring in this decision, 0 otherwise
+  int* qact[2][2];    // [set][parity of the decision]: 1 active, 2 retiring in this decision, 0 otherwise
   int* sq[2];         // slot -> query
   uint16_t* g;
-  float* part;
+  float* part[2];     // by set: [parity][2][rt][B_pad] partial sums of |du|^2, |u|^2
   double* fpart;
   float* tau;
   int* qiter;
   int* qdone;
-  int* tile_act;
+  int* tile_k;        // per column tile: the last decision that found active slots in it
+  int* tile_cnt;      // per column tile: the number it found
   float* ufin;
   float* sfin;
   const float* x;     // the caller's queries [B][n] (final pass: y = x - c)
@@ -105,7 +105,9 @@ struct TcArgs {
 struct Ctx {
   int cb;     // current buffer set
   int ct_on;  // column tiles in use (the active prefix)
-  int fresh;  // compacted in this iteration: every tile below ct_on holds active slots
+  int fresh;  // compacted before this iteration: every tile below ct_on holds active slots
+  int k;      // iteration
+  int par;    // parity of this iteration's decision (k & 1)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -232,7 +234,9 @@ struct Smem {
   int abort;
   int epi_abort;  // snapshot of abort read by all epilogue warps after a barrier
   int first;
-  float qtau[BN], qscale[BN];
+  int cnt[4];  // active slots per warp of the decision (row tile 0)
+  alignas(16) float qtau[BN];
+  alignas(16) float qscale[BN];
   int qact[BN];
   int qid[BN];
   int base[1024];  // compaction: first new slot of each column tile
@@ -262,9 +266,22 @@ __device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
   return c;
 }
 
+// Decision k is taken in the epilogue of phase A (or P) of iteration k, by
+// every row tile of a column from the same partial sums; row tile 0 records
+// it.  tile_k[c] only grows (row tile 0 sets it to k when decision k finds
+// active slots in column c), so a column that has emptied stays out:
+// phase A of iteration k runs the columns with tile_k >= k - 1 (all of them in
+// the first iteration and right after a compaction), phase B those with
+// tile_k == k.  Values left from before a compaction are older than the
+// iteration, so they never count.
+__device__ __forceinline__ int tile_count(const TcArgs& a, const Ctx& x, int c) {
+  return a.tile_k[c] == x.k ? a.tile_cnt[c] : 0;
+}
 __device__ __forceinline__ bool tile_on(const TcArgs& a, const Ctx& x, int ph, int c) {
   if (ph == PH_F) return (int64_t)c * BN < a.B;
-  return c < x.ct_on && (x.fresh || a.tile_act[c] > 0);
+  if (c >= x.ct_on) return false;
+  if (ph == PH_B) return a.tile_k[c] == x.k;
+  return x.k == 1 || x.fresh || a.tile_k[c] >= x.k - 1;
 }
 __device__ __forceinline__ int phase_items(const TcArgs& a, const Ctx& x, int ph) {
   return a.rt * (ph == PH_F ? a.ct : x.ct_on);
@@ -290,7 +307,9 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
                           : ph == PH_B ? &a.mG
                                        : (((k - 1) & 1) ? &a.mP2 : &a.mP1);
   const CUtensorMap* B1 = (ph == PH_A && x.cb) ? &a.mP2b : &a.mP2;
-  const uint32_t bytes = (uint32_t)(cfg.na + cfg.nb) * TILE_BYTES;
+  // phases with one operand pair (B, P) fill a stage with two k-blocks
+  const int kstep = cfg.na == 1 ? 2 : 1;
+  const uint32_t bytes = 4u * TILE_BYTES;
   const int nk = a.np / BK, items = phase_items(a, x, ph);
   const int nsub = ph == PH_F ? 2 : 1;  // PH_F: {A1, A2 | p1, p2} then {A1, A3 | p3, p1}
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
@@ -302,7 +321,7 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
       tma_prefetch_l2(&a.mU[x.cb], r * BM, c * BN);
       if (ph != PH_B) tma_prefetch_l2(&a.mY[x.cb], r * BM, c * BN);
     }
-    for (int kb = 0; kb < nk; ++kb) {
+    for (int kb = 0; kb < nk; kb += kstep) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
         const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
         if (!mbar_wait(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort)) return;
@@ -310,13 +329,21 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
         mbar_expect_tx(full, bytes);
         uint8_t* base = stages + (size_t)s * STAGE_BYTES;
         const int kx = kb * BK;
-        const CUtensorMap* a1 = sub ? &a.mAl2 : A1;
-        const CUtensorMap* b0 = sub ? &a.mP3 : B0;
-        const CUtensorMap* b1 = sub ? &a.mP1 : B1;
-        tma_load(sa(base), A0, full, kx, r * BM);
-        if (cfg.na > 1) tma_load(sa(base + TILE_BYTES), a1, full, kx, r * BM);
-        tma_load(sa(base + 2 * TILE_BYTES), b0, full, kx, c * BN);
-        if (cfg.nb > 1) tma_load(sa(base + 3 * TILE_BYTES), b1, full, kx, c * BN);
+        if (kstep == 2) {
+          // {M_kb, M_kb+1 | g_kb, g_kb+1}
+          tma_load(sa(base), A0, full, kx, r * BM);
+          tma_load(sa(base + TILE_BYTES), A0, full, kx + BK, r * BM);
+          tma_load(sa(base + 2 * TILE_BYTES), B0, full, kx, c * BN);
+          tma_load(sa(base + 3 * TILE_BYTES), B0, full, kx + BK, c * BN);
+        } else {
+          const CUtensorMap* a1 = sub ? &a.mAl2 : A1;
+          const CUtensorMap* b0 = sub ? &a.mP3 : B0;
+          const CUtensorMap* b1 = sub ? &a.mP1 : B1;
+          tma_load(sa(base), A0, full, kx, r * BM);
+          tma_load(sa(base + TILE_BYTES), a1, full, kx, r * BM);
+          tma_load(sa(base + 2 * TILE_BYTES), b0, full, kx, c * BN);
+          tma_load(sa(base + 3 * TILE_BYTES), b1, full, kx, c * BN);
+        }
         st.last_par[s] = use & 1;
         st.used[s] = true;
       }
@@ -399,19 +426,32 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
         }
         continue;
       }
+      if (cfg.na == 1 && (kb & 1)) continue;  // B, P: the stage of kb holds kb + 1 too
       const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
       ++st.kb;
       if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
       tc_fence_after();
       const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
+      if (cfg.na == 1) {
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        for (int tm = 0; tm < cfg.nterm; ++tm) {
-          const uint64_t ad = smem_desc(base + cfg.ta[tm] * TILE_BYTES) + (uint64_t)(kk * 2);
-          const uint64_t bd = smem_desc(base + (2 + cfg.tb[tm]) * TILE_BYTES) + (uint64_t)(kk * 2);
-          // the first product into an accumulator overwrites it
-          const bool first_into = (kb == 0 && kk == 0) && (tm == 0 || cfg.td[tm] != cfg.td[tm - 1]);
-          mma_f16(d0 + cfg.td[tm] * BN, ad, bd, cfg.idesc, first_into ? 0u : 1u);
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = smem_desc(base + h * TILE_BYTES) + (uint64_t)(kk * 2);
+            const uint64_t bd = smem_desc(base + (2 + h) * TILE_BYTES) + (uint64_t)(kk * 2);
+            mma_f16(d0, ad, bd, cfg.idesc, (kb == 0 && h == 0 && kk == 0) ? 0u : 1u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          for (int tm = 0; tm < cfg.nterm; ++tm) {
+            const uint64_t ad = smem_desc(base + cfg.ta[tm] * TILE_BYTES) + (uint64_t)(kk * 2);
+            const uint64_t bd = smem_desc(base + (2 + cfg.tb[tm]) * TILE_BYTES) + (uint64_t)(kk * 2);
+            // the first product into an accumulator overwrites it
+            const bool first_into = (kb == 0 && kk == 0) && (tm == 0 || cfg.td[tm] != cfg.td[tm - 1]);
+            mma_f16(d0 + cfg.td[tm] * BN, ad, bd, cfg.idesc, first_into ? 0u : 1u);
+          }
         }
       }
       st.issued = true;
@@ -430,19 +470,14 @@ struct EpiState {
 };
 
 // Load the per-query data of column tile c into shared memory.
-__device__ void epi_stage_queries(const TcArgs& a, Smem& S, int ph, int c, int k, const Ctx& x, int et) {
+// Final pass: the per-query data of column tile c (query-indexed).
+__device__ void epi_stage_final(const TcArgs& a, Smem& S, int c, int et) {
   if (et >= BN) return;
-  const int64_t sl = (int64_t)c * BN + et;  // slot (the query itself in the final pass)
-  if (ph == PH_F) {
-    S.qtau[et] = a.tau[sl];
-    S.qscale[et] = a.sfin[sl];
-    S.qact[et] = sl < a.B;
-  } else {
-    S.qtau[et] = a.taus[x.cb][sl];
-    S.qscale[et] = a.scale[x.cb][sl];
-    S.qact[et] = a.qact[x.cb][sl] == 1;
-  }
-  if (et == 0) S.first = (ph != PH_F) && k == 1;
+  const int64_t q = (int64_t)c * BN + et;
+  S.qtau[et] = a.tau[q];
+  S.qscale[et] = a.sfin[q];
+  S.qact[et] = q < a.B;
+  if (et == 0) S.first = 0;
 }
 
 // Transpose-reduce over 16 columns: lane L holds v[0..15] (one value per
@@ -464,6 +499,68 @@ __device__ __forceinline__ void transpose_reduce16(float v[16], int lane) {
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
+// Per-slot data of an item's column: t / lambda, query, prox scale and state.
+// Phases A and P take decision k here from the partial sums of iteration
+// k - 1 (every row tile of the column alike):  0 inactive, 1 active,
+// 2 stops converged, 3 stops at max_iter.  Phase B reads the recorded state.
+__device__ __forceinline__ void slot_data(const TcArgs& a, const Ctx& x, int ph, int64_t sl, float& tau, float& sc,
+                                          int& act, int& qid) {
+  const int cb = x.cb;
+  tau = a.taus[cb][sl];
+  qid = a.sq[cb][sl];
+  sc = 1.f;
+  if (ph == PH_B) {
+    act = a.qact[cb][x.par][sl];
+    return;
+  }
+  if (x.k == 1) {
+    act = qid < a.B ? 1 : 0;
+    return;
+  }
+  // every load issued before any is used (one memory latency)
+  const int prev = a.qact[cb][x.par ^ 1][sl];
+  const float* P = a.part[cb] + (int64_t)((x.par ^ 1) * 2) * a.rt * a.B_pad + sl;
+  const int64_t rs = a.B_pad, ns = (int64_t)a.rt * a.B_pad;
+  float dv[8], nv[8];
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    dv[rr] = rr < a.rt ? P[rr * rs] : 0.f;
+    nv[rr] = rr < a.rt ? P[ns + rr * rs] : 0.f;
+  }
+  float du2 = 0.f, nu2 = 0.f;
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    du2 += dv[rr];
+    nu2 += nv[rr];
+  }
+  for (int rr = 8; rr < a.rt; ++rr) {
+    du2 += P[rr * rs];
+    nu2 += P[ns + rr * rs];
+  }
+  act = 0;
+  if (prev != 1) return;
+  sc = shrink2_scale(sqrtf(nu2), tau);
+  const int kprev = x.k - 1;
+  if (kprev >= 2 && du2 <= a.tol * fmaxf(1.f, nu2)) act = 2;
+  else if (kprev >= a.max_iter) act = 3;
+  else act = 1;
+}
+
+// Ask L1 for the slot data that slot_data() will read for slot sl.
+__device__ __forceinline__ void slot_prefetch(const TcArgs& a, const Ctx& x, int ph, int64_t sl) {
+  const int cb = x.cb;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a.taus[cb] + sl));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a.sq[cb] + sl));
+  if (ph == PH_B) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.qact[cb][x.par] + sl));
+    return;
+  }
+  if (x.k == 1) return;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a.qact[cb][x.par ^ 1] + sl));
+  const float* P = a.part[cb] + (int64_t)((x.par ^ 1) * 2) * a.rt * a.B_pad + sl;
+  for (int rr = 0; rr < 2 * a.rt; ++rr) asm volatile("prefetch.global.L1 [%0];" ::"l"(P + (int64_t)rr * a.B_pad));
+}
+
 template <int ph>
 __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -475,18 +572,13 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   const int np = a.np, hk = a.h_kind;
   const float lam = a.lam;
   const int cb = x.cb;
-  // the query data (tau, scale, active) of the next item is loaded into
-  // registers while the current item is processed
+  // the slot data (and, in phases A and P, the decision) of the next item is
+  // loaded into registers while the current item is processed
   int it = blockIdx.x;
   while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
   float pf_tau = 0.f, pf_sc = 1.f;
-  int pf_act = 0;
-  if (it < items && et < BN) {
-    const int64_t sl = (int64_t)(it / a.rt) * BN + et;
-    pf_tau = a.taus[cb][sl];
-    pf_sc = a.scale[cb][sl];
-    pf_act = a.qact[cb][sl] == 1;
-  }
+  int pf_act = 0, pf_qid = 0;
+  if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
   while (it < items) {
     const int r = it % a.rt, c = it / a.rt;
     int it_next = it + gridDim.x;
@@ -495,32 +587,72 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     st.nb ^= 1;
     const uint32_t use = st.uf[buf]++;
     epi_sync();  // previous item's readers of the shared query data are done
+    const bool record = ph != PH_B && r == 0;  // row tile 0 records decision k
     if (et < BN) {
       S.qtau[et] = pf_tau;
       S.qscale[et] = pf_sc;
       S.qact[et] = pf_act;
-      if (it_next < items) {
-        const int64_t sl = (int64_t)(it_next / a.rt) * BN + et;
-        pf_tau = a.taus[cb][sl];
-        pf_sc = a.scale[cb][sl];
-        pf_act = a.qact[cb][sl] == 1;
+      S.qid[et] = pf_qid;
+      if (record) {
+        const int64_t sl = (int64_t)c * BN + et;
+        a.qact[cb][x.par][sl] = pf_act >= 2 ? 2 : pf_act;
+        if (pf_act >= 2) {
+          a.qdone[pf_qid] = pf_act == 2 ? 1 : 2;
+          a.qiter[pf_qid] = pf_act == 2 ? k - 1 : a.max_iter;
+          a.sfin[pf_qid] = pf_sc;
+        }
+        const int cnt = __reduce_add_sync(0xffffffffu, pf_act == 1 ? 1 : 0);
+        if ((et & 31) == 0) S.cnt[et >> 5] = cnt;
       }
+      // one lane in 32 asks for each 128-byte line of the next item's slot data
+      if (it_next < items && (et & 31) == 0)
+        slot_prefetch(a, x, ph, (int64_t)(it_next / a.rt) * BN + et);
     }
     if (et == 0) {
       S.first = k == 1;
       S.epi_abort = S.abort;
     }
     epi_sync();
-    if (S.epi_abort) return;  // the same decision in all eight warps
-    // a failed wait skips the work of this item but keeps the warp in step
-    // with the others at the named barriers below
-    const bool good = mbar_wait(sa(&S.tfull[buf]), use & 1, a.err, &S.abort);
-    if (good) tc_fence_after();
+    if (S.epi_abort) return;  // the same decision in all epilogue warps
+    if (record && et == 0) {
+      const int tot = S.cnt[0] + S.cnt[1] + S.cnt[2] + S.cnt[3];
+      if (tot) {
+        a.tile_cnt[c] = tot;
+        a.tile_k[c] = k;
+        atomicAdd(a.bar + 2 + (k % 3), (unsigned)tot);
+      }
+    }
     const int row = r * BM + rloc;
     const float wr = a.w[row];
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
     const bool first = S.first;
+    // The state a chunk reads from global memory does not depend on this
+    // item's products: the first chunk's loads go out before the wait for
+    // the accumulator, each later chunk's when its predecessor is done.
+    // am: active slots of the 16-column chunk, rm (phases A and P): slots
+    // that stop in this decision (lanes 0-15 vote).
+    float uu[16], yy[16];
+    uint32_t am = 0, rm = 0;
+    auto load = [&](int j0) {
+      const int qa = lane < 16 ? S.qact[j0 + (lane & 15)] : 0;
+      am = __ballot_sync(0xffffffffu, qa == 1);
+      rm = ph == PH_B ? 0u : __ballot_sync(0xffffffffu, qa >= 2);
+      const int64_t col0 = ((int64_t)c * BN + j0) * np + row;
+      const float* ucol = a.u[cb] + col0;
+      const float* ycol = a.y[cb] + col0;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        uu[jj] = ((am | rm) >> jj & 1u) ? ucol[(int64_t)jj * np] : 0.f;
+        if constexpr (ph != PH_B) yy[jj] = (am >> jj & 1u) ? __ldg(ycol + (int64_t)jj * np) : 0.f;
+      }
+    };
+    load(jbase);
+    // a failed wait skips the work of this item but keeps the warp in step
+    // with the others at the named barriers below
+    const bool good = mbar_wait(sa(&S.tfull[buf]), use & 1, a.err, &S.abort);
+    if (good) tc_fence_after();
     for (int j0 = jbase; good && j0 < jbase + CPW; j0 += 16) {
+      if (j0 != jbase) load(j0);
       float d1[16];
       tmem_ld16(tbase + j0, d1);
       if constexpr (ph == PH_A) {
@@ -530,53 +662,73 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) d1[jj] += d2[jj] * (1.f / kLoScale);
       }
-      // active queries of this 16-column chunk as a bit mask (lanes 0-15 vote)
-      const uint32_t am = __ballot_sync(0xffffffffu, lane < 16 && S.qact[j0 + (lane & 15)] != 0);
       const int64_t col0 = ((int64_t)c * BN + j0) * np + row;
+      if (rm) {
+        // a stopping slot leaves its u^{k-1} row segment in the final array
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          if (rm >> jj & 1u) a.ufin[(int64_t)S.qid[j0 + jj] * np + row] = uu[jj];
+      }
       if constexpr (ph == PH_A) {
-        const float* ucol = a.u[cb] + col0;
-        const float* ycol = a.y[cb] + col0;
-        // all loads first (independent, in flight together), then the stores
-        float uu[16], yy[16];
+        // b = u - prox(u) in place of u, column by column (the branches are
+        // uniform): l1 and weighted l1 shrink by tau w, l2 scales u (and A u)
+        // by the query's s; in the first iteration p = y
+        if (first) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const bool on = am >> jj & 1u;
-          uu[jj] = on ? ucol[(int64_t)jj * np] : 0.f;
-          yy[jj] = on ? __ldg(ycol + (int64_t)jj * np) : 0.f;
+          for (int jj = 0; jj < 16; ++jj) uu[jj] -= yy[jj];
+        } else if (hk == H_L2) {
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 s4 = *reinterpret_cast<const float4*>(&S.qscale[j0 + 4 * q4]);
+            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              uu[4 * q4 + e] -= sv[e] * uu[4 * q4 + e];
+              d1[4 * q4 + e] *= sv[e];  // the operand held u: A p = s A u
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[j0 + 4 * q4]);
+            const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) uu[4 * q4 + e] -= shrink1(uu[4 * q4 + e], tv[e] * wr);
+          }
         }
+        uint16_t* gcol = a.g + col0;
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          if (!(am >> jj & 1u)) continue;
-          const int j = j0 + jj;
-          const float tau = S.qtau[j], sc = S.qscale[j];
-          const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, sc, hk);
-          float ap = d1[jj];
-          if (hk == H_L2 && !first) ap *= sc;  // l2: the operand held u, p = sc u
-          const float g = yy[jj] - ap - lam * (uu[jj] - p);
-          a.g[col0 + (int64_t)jj * np] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+          const float g = yy[jj] - d1[jj] - lam * uu[jj];
+          if (am >> jj & 1u) gcol[(int64_t)jj * np] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
         }
       } else if constexpr (ph == PH_B) {
         // d1 becomes |u^k - u^{k-1}|^2 and uu becomes |u^k|^2 in place
         float* U = a.u[cb] + col0;
         uint16_t* P1 = a.p1[cb] + col0;
         uint16_t* P2 = a.p2[cb] + col0;
-        float uu[16];
+        // the operand planes hold p (l1, weighted l1) or u itself (l2)
+        const bool l2 = hk == H_L2;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) uu[jj] = (am >> jj & 1u) ? U[(int64_t)jj * np] : 0.f;
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[j0 + 4 * q4]);
+          const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const bool on = am >> jj & 1u;
-          const float du = on ? d1[jj] : 0.f;
-          const float un = uu[jj] + du;
-          if (on) {
-            const float pn = hk == H_L2 ? un : shrink1(un, S.qtau[j0 + jj] * wr);
-            const __half hi = __float2half_rn(pn);
-            P1[(int64_t)jj * np] = __half_as_ushort(hi);
-            P2[(int64_t)jj * np] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
-            U[(int64_t)jj * np] = un;
+          for (int e = 0; e < 4; ++e) {
+            const int jj = 4 * q4 + e;
+            const bool on = am >> jj & 1u;
+            const float du = on ? d1[jj] : 0.f;
+            const float un = uu[jj] + du;
+            if (on) {
+              const float pn = l2 ? un : shrink1(un, tv[e] * wr);
+              const __half hi = __float2half_rn(pn);
+              P1[(int64_t)jj * np] = __half_as_ushort(hi);
+              P2[(int64_t)jj * np] = __half_as_ushort(__float2half_rn((pn - __half2float(hi)) * kLoScale));
+              U[(int64_t)jj * np] = un;
+            }
+            d1[jj] = du * du;
+            uu[jj] = on ? un * un : 0.f;
           }
-          d1[jj] = du * du;
-          uu[jj] = on ? un * un : 0.f;
         }
         transpose_reduce16(d1, lane);
         transpose_reduce16(uu, lane);
@@ -586,15 +738,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         }
       } else if constexpr (ph == PH_P) {
         float* U = a.u[cb] + col0;
-        const float* ycol = a.y[cb] + col0;
         uint16_t* rbuf = ((k & 1) ? a.p2[cb] : a.p1[cb]) + col0;  // BF16 form: no compaction, set 0
-        float uu[16], yy[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const bool on = am >> jj & 1u;
-          uu[jj] = on ? U[(int64_t)jj * np] : 0.f;
-          yy[jj] = on ? __ldg(ycol + (int64_t)jj * np) : 0.f;
-        }
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           float du = 0.f, un = 0.f;
@@ -626,15 +770,17 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     ++st.ue[buf];
     if constexpr (ph != PH_A) {
       epi_sync();
-      if (et < BN && S.qact[et]) {
+      if (et < BN && S.qact[et] == 1) {
         const int64_t q = (int64_t)c * BN + et;
         const float s0 = S.red[0][et][0] + S.red[1][et][0] + S.red[2][et][0] + S.red[3][et][0];
         const float s1 = S.red[0][et][1] + S.red[1][et][1] + S.red[2][et][1] + S.red[3][et][1];
         const int par = k & 1;
-        a.part[((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
-        a.part[((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
+        a.part[cb][((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
+        a.part[cb][((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
       }
     }
+    // the next item's slot data (and decision), from lines asked for above
+    if (et < BN && it_next < items) slot_data(a, x, ph, (int64_t)(it_next / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
     it = it_next;
   }
 }
@@ -653,7 +799,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, x, PH_F, c)) continue;
     epi_sync();
-    epi_stage_queries(a, S, PH_F, c, 0, x, et);
+    epi_stage_final(a, S, c, et);
     if (et == 0) S.epi_abort = S.abort;
     epi_sync();
     if (S.epi_abort) return;
@@ -738,94 +884,30 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
   }
 }
 
-// Decision for iteration k (convergence of iteration k-1), one thread per
-// slot of a column tile.  A slot that stops (converged, or at max_iter) is
-// retired at once: its u and l2 scale go to the query-indexed final arrays,
-// the epilogue threads copying the row together.
-__device__ __noinline__ void prepass(const TcArgs& a, Smem& S, int k, const Ctx& x) {
-  const int et = threadIdx.x - 64;
-  int* const QA = a.qact[x.cb];
-  float* const SC = a.scale[x.cb];
-  const int* const SQ = a.sq[x.cb];
-  const float* const U = a.u[x.cb];
-  for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
-    if (et < BN) {
-      const int64_t sl = (int64_t)c * BN + et;
-      const int qid = SQ[sl];
-      int act = 0;
-      if (k == 1) {
-        act = qid < a.B;
-        SC[sl] = 1.f;
-      } else if (QA[sl] == 1) {
-        const int par = (k - 1) & 1;
-        float du2 = 0.f, nu2 = 0.f;
-        for (int rr = 0; rr < a.rt; ++rr) {
-          du2 += a.part[((int64_t)(par * 2 + 0) * a.rt + rr) * a.B_pad + sl];
-          nu2 += a.part[((int64_t)(par * 2 + 1) * a.rt + rr) * a.B_pad + sl];
-        }
-        const int kprev = k - 1;
-        const float sc = shrink2_scale(sqrtf(nu2), a.taus[x.cb][sl]);
-        SC[sl] = sc;
-        if (kprev >= 2 && du2 <= a.tol * fmaxf(1.f, nu2)) {
-          a.qdone[qid] = 1;
-          a.qiter[qid] = kprev;
-          a.sfin[qid] = sc;
-          act = 2;
-        } else if (kprev >= a.max_iter) {
-          a.qdone[qid] = 2;
-          a.qiter[qid] = a.max_iter;
-          a.sfin[qid] = sc;
-          act = 2;
-        } else {
-          act = 1;
-        }
-      }
-      QA[sl] = act;
-      S.qact[et] = act;
-      S.qid[et] = qid;
-      const int cnt = __reduce_add_sync(0xffffffffu, act == 1 ? 1 : 0);
-      if ((et & 31) == 0) S.red[et >> 5][0][0] = __int_as_float(cnt);
-    }
-    epi_sync();
-    if (et == 0) {
-      int tot = 0;
-      for (int i = 0; i < 4; ++i) tot += __float_as_int(S.red[i][0][0]);
-      a.tile_act[c] = tot;
-      if (tot) atomicAdd(a.bar + 2 + (k % 3), (unsigned)tot);
-    }
-    // retire the slots that stopped in this decision (rows streamed together)
-    const int per_row = a.np / 4;
-    for (int e = et; e < BN * per_row; e += NEPI) {
-      const int j = e / per_row, i = (e - j * per_row) * 4;
-      if (S.qact[j] != 2) continue;
-      *reinterpret_cast<float4*>(a.ufin + (int64_t)S.qid[j] * a.np + i) =
-          *reinterpret_cast<const float4*>(U + ((int64_t)c * BN + j) * a.np + i);
-    }
-    epi_sync();
-  }
-}
-
-// Compaction: the active slots (qact == 1) of buffer set x.cb move, in order,
-// to the front of the other set: y, u and the FP16 split of p by rows, the
-// slot's query and scale with them.  Every CTA scans the per-tile active counts
-// itself; tile c's active slots start at base[c].  Slots past the active count
-// in the last new tile are marked inactive.
+// Compaction after phase B of iteration k: the slots active after decision k
+// move, in order, to the front of the other buffer set: y, u and the FP16
+// split of p by rows, with the slot's query, t / lambda, state and the partial
+// sums of iteration k (decision k + 1 reads them).  Every CTA scans the
+// per-tile active counts itself; tile c's active slots start at base[c].
+// Slots past the active count in the last new tile are marked inactive.
 __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int n_active) {
   const int et = threadIdx.x - 64;
-  const int cb = x.cb, nb = cb ^ 1;
+  const int cb = x.cb, nb = cb ^ 1, par = x.par;
   if (et == 0) {
     int acc = 0;
     for (int c = 0; c < x.ct_on; ++c) {
       S.base[c] = acc;
-      acc += a.tile_act[c];
+      acc += tile_count(a, x, c);
     }
   }
   epi_sync();
-  const int np = a.np;
+  const int np = a.np, rt = a.rt;
+  const int64_t pstride = (int64_t)rt * a.B_pad;
   for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
+    if (tile_count(a, x, c) == 0) continue;  // the same for every thread
     if (et < BN) {
       const int64_t sl = (int64_t)c * BN + et;
-      const bool act = a.qact[cb][sl] == 1;
+      const bool act = a.qact[cb][par][sl] == 1;
       const unsigned m = __ballot_sync(0xffffffffu, act);
       if ((et & 31) == 0) S.red[et >> 5][1][0] = __int_as_float(__popc(m));
       epi_sync_half();
@@ -835,9 +917,11 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
       if (act) {
         const int d = S.base[c] + rank;
         a.sq[nb][d] = a.sq[cb][sl];
-        a.scale[nb][d] = a.scale[cb][sl];
         a.taus[nb][d] = a.taus[cb][sl];
-        a.qact[nb][d] = 1;
+        a.qact[nb][par][d] = 1;
+        const float* P0 = a.part[cb] + (int64_t)(par * 2) * pstride;
+        float* P1 = a.part[nb] + (int64_t)(par * 2) * pstride;
+        for (int rr = 0; rr < 2 * rt; ++rr) P1[rr * a.B_pad + d] = P0[rr * a.B_pad + sl];
       }
     }
     epi_sync();
@@ -877,9 +961,8 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
   // the tail of the last new tile
   const int need = (n_active + BN - 1) / BN;
   for (int64_t sl = (int64_t)n_active + blockIdx.x * NEPI + et; sl < (int64_t)need * BN; sl += (int64_t)gridDim.x * NEPI) {
-    a.qact[nb][sl] = 0;
+    a.qact[nb][par][sl] = 0;
     a.sq[nb][sl] = 0;
-    a.scale[nb][sl] = 1.f;
     a.taus[nb][sl] = 0.f;
   }
 }
@@ -956,6 +1039,8 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
   cx.cb = 0;
   cx.ct_on = a.ct;
   cx.fresh = 0;
+  cx.k = 0;
+  cx.par = 0;
   auto run = [&](int ph, int k) {
     if (warp == 0) {
       if (lane == 0) {
@@ -973,17 +1058,26 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     }
   };
 
+  // Iteration k: phase A (decision k in its epilogue, then g), barrier,
+  // phase B (u, p and the partial sums), barrier, and a compaction when it
+  // frees at least an eighth of the column tiles in use.  The BF16 form has
+  // the single phase P.
   bool ok = true;
   for (int k = 1; ok; ++k) {
+    cx.k = k;
+    cx.par = k & 1;
+    // the count slot that decision k + 1 fills (last read at iteration
+    // k - 2, which every CTA has left)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
-    if (warp >= 2) prepass(a, S, k, cx);
+    run(a.form == FORM_MIXED ? PH_A : PH_P, k);
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
     const int n_active = (int)ld_acquire_u32(a.bar + 2 + (k % 3));
     if (n_active == 0) break;
-    // pack the active slots when at least an eighth of the tiles in use would
-    // be freed (every CTA takes the same decision from the same count)
+    if (a.form != FORM_MIXED) continue;
+    run(PH_B, k);
+    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+    // every CTA takes the same decision from the same count
     const int need = (n_active + BN - 1) / BN;
-    cx.fresh = 0;
     if (a.compact && need + (cx.ct_on + 7) / 8 <= cx.ct_on) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
@@ -991,15 +1085,9 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
       cx.cb ^= 1;
       cx.ct_on = need;
       cx.fresh = 1;
-    }
-    if (a.form == FORM_MIXED) {
-      run(PH_A, k);
-      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
-      run(PH_B, k);
     } else {
-      run(PH_P, k);
+      cx.fresh = 0;
     }
-    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
   }
   if (ok) {
     if (warp >= 2) prep_final_operand(a);
@@ -1143,21 +1231,23 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.p1[1] = w.ph_b;
   a.p2[0] = w.pl;
   a.p2[1] = w.pl_b;
-  a.scale[0] = w.scale;
-  a.scale[1] = w.scale_b;
   a.taus[0] = w.taus;
   a.taus[1] = w.taus + w.B_pad;
-  a.qact[0] = w.qact;
-  a.qact[1] = w.qact_b;
+  a.qact[0][0] = w.qact;
+  a.qact[0][1] = w.qact + w.B_pad;
+  a.qact[1][0] = w.qact_b;
+  a.qact[1][1] = w.qact_b + w.B_pad;
   a.sq[0] = w.sq;
   a.sq[1] = w.sq + w.B_pad;
   a.g = w.g;
-  a.part = w.part;
+  a.part[0] = w.part;
+  a.part[1] = w.part + (int64_t)2 * 2 * w.rt * w.B_pad;
   a.fpart = w.fpart;
   a.tau = w.tau;
   a.qiter = w.qiter;
   a.qdone = w.qdone;
-  a.tile_act = w.tile_act;
+  a.tile_k = w.tile_act;
+  a.tile_cnt = w.tile_act + w.B_pad / 128;
   a.ufin = w.ufin;
   a.sfin = w.sfin;
   a.x = x;

@@ -82,15 +82,15 @@ struct DenseWs {
   uint16_t* ph = nullptr;    // [B_pad][n_pad] tensor-core operand 1 (BF16 r, or FP16 split of p)
   uint16_t* pl = nullptr;    // [B_pad][n_pad] tensor-core operand 2 (FP16 split of p, scaled)
   uint16_t* g = nullptr;     // [B_pad][n_pad] BF16 residual g
-  float* part = nullptr;     // [2][2][rt][B_pad] residual / norm partials by parity
+  float* part = nullptr;     // [set][2][2][rt][B_pad] residual / norm partials by parity (tensor-core solver: by buffer set)
   double* fpart = nullptr;   // [2][rt][B_pad] final phi partials
   float* tau = nullptr;      // [B_pad] t / lambda
   float* tq = nullptr;       // [B_pad] t
   float* scale = nullptr;    // [B_pad] l2 prox scale of the current iterate
   int* qiter = nullptr;      // [B_pad]
   int* qdone = nullptr;      // [B_pad]
-  int* qact = nullptr;       // [B_pad] updated in the current iteration
-  int* tile_act = nullptr;   // [B_pad / 128] active queries per column tile
+  int* qact = nullptr;       // [2][B_pad] by parity of the decision
+  int* tile_act = nullptr;   // [2][B_pad / 128] per column tile (tensor-core solver: last decision with active slots; count)
   // tensor-core path: slots (columns of the operand planes) are compacted as
   // queries converge; a second buffer set receives the packed slots, and a
   // converged query's u and l2 scale are retired to query-indexed arrays
@@ -100,7 +100,7 @@ struct DenseWs {
   uint16_t* pl_b = nullptr;  // [B_pad][n_pad]
   float* scale_b = nullptr;  // [B_pad]
   float* taus = nullptr;     // [2][B_pad] t / lambda by slot (moves with its query)
-  int* qact_b = nullptr;     // [B_pad]
+  int* qact_b = nullptr;     // [2][B_pad]
   int* sq = nullptr;         // [2][B_pad] slot -> query
   float* ufin = nullptr;     // [B_pad][n_pad] u of converged queries, by query
   float* sfin = nullptr;     // [B_pad] l2 scale of converged queries, by query
