@@ -33,8 +33,8 @@ METRIC = "Hopf evals/s (phi, grad phi at 1e-6 rel), n=1024, batch 64K, dense A, 
 # the dominant kernel at the default workload, from the ncu capture summarised
 # in profiles/k_dense_tc_n1024_b65536.md; reported only while the kernel
 # source still has the hash it had at capture.
-MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "494e6637505d2dc5",
-                              "bytes": 153.0e9, "n": 1024, "batch": 65536}}
+MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "2cce1413e1c4e15b",
+                              "bytes": 161.4e9, "n": 1024, "batch": 65536}}
 TOL = 1e-13
 MAX_ITER = 1000
 
@@ -312,7 +312,7 @@ def run_ragged(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, threads, done, secs, ninst = ragged_cpu_sample(inst, descs, counts, max(8, args.cpu_sample // 2))
+        rate, threads, done, secs, ninst = ragged_cpu_sample(inst, descs, counts, max(8, args.cpu_sample))
         cpu = {"value": rate, "unit": "evals/s", "cores": threads, "kind": "oracle",
                "sample": "%d queries drawn uniformly over the batch (%d instances), FP64 oracle, same stop rule; "
                          "%.1f s of solves, per-instance factorisation excluded" % (done, ninst, secs)}

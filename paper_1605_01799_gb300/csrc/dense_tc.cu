@@ -1078,7 +1078,9 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
     // every CTA takes the same decision from the same count
     const int need = (n_active + BN - 1) / BN;
-    if (a.compact && need + (cx.ct_on + 7) / 8 <= cx.ct_on) {
+    // (the packing offsets of the column tiles live in shared memory)
+    if (a.compact && cx.ct_on <= (int)(sizeof(S.base) / sizeof(S.base[0])) &&
+        need + (cx.ct_on + 7) / 8 <= cx.ct_on) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
       if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;

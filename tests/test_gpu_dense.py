@@ -162,3 +162,27 @@ def test_compaction_does_not_change_results(hg, orc):
         x[:64].astype(np.float64), t[:64].astype(np.float64))
     phi = outs[0]["phi"][:64].cpu().numpy()
     assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= PHI_TOL
+
+
+def test_batch_beyond_the_compaction_table(hg, orc):
+    """More column tiles (1,094 for 140,000 queries) than the shared-memory
+    table of packing offsets holds (1,024): the solver runs without packing
+    until the active tiles fit, with the same results as the oracle on
+    sampled queries (first, middle, and the ragged last tile)."""
+    import torch
+    n, B = 128, 140000
+    A, Q, s = wl.spd_matrix(11901, 11902, n)
+    x = wl.normal(11904, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(11905, B, 0.1, 3.0).astype(np.float32)
+    h = hg.Hopf(A, 0, tol=TOL, max_iter=3000, precision=hg.P_MIXED)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == hg.Q_OK).all()
+    idx = np.array([0, 1, 70000, 70001, B - 2, B - 1])
+    ref = orc.Problem(A, 0, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
+        x[idx].astype(np.float64), t[idx].astype(np.float64))
+    phi = out["phi"].cpu().numpy()[idx]
+    g = out["grad"].cpu().numpy()[idx].astype(np.float64)
+    assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= PHI_TOL
+    eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+    assert eg.max() <= GRAD_MAX, eg.max()
