@@ -10,6 +10,8 @@ d phi/dt) per second.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant mixed|fp32|bf16]
     python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
     python bench.py --workload ragged      # 512-instance ragged batch (one graph replay per step)
+    python bench.py --workload union       # union of 16 ellipsoids: phi, argmin, distance, closest point
+    python bench.py --workload grad        # n = 2048 forward + envelope-theorem backward
 
 For N > 1 launch under torch.distributed.run: every rank evaluates its own
 65,536 queries (weak scaling, no collective on the data path); the time is the
@@ -51,7 +53,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=192)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="dense", choices=["dense", "ragged"])
+    p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad"])
     return p.parse_args()
 
 
@@ -333,12 +335,232 @@ def run_ragged(args):
         torch.distributed.destroy_process_group()
 
 
+def init_device():
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local, torch.device("cuda", torch.cuda.current_device())
+
+
+def time_steps(fn, steps, ws, local):
+    """Run fn() `steps` times between CUDA events on the current stream with
+    the clocks sampled; returns (ms per step, clocks)."""
+    import torch
+    clk_path = tempfile.mktemp(suffix=".csv")
+    clk = sample_clocks(clk_path)
+    time.sleep(0.5)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    if clk:
+        clk.terminate()
+        clk.wait()
+    ms = e0.elapsed_time(e1) / steps
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = tt.item()
+    return ms, read_clocks(clk_path, local)
+
+
+ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 lanes x 2 flop (FMA) x max SM clock, TFLOP/s
+ALU_SRC = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived) %.1f TFLOP/s" % ALU_PEAK
+UNION_FLOP_PER_COORD = 12.0  # one split Bregman step of the diagonal l2 solve, per coordinate
+
+
+def run_union(args):
+    """Union of K = 16 ellipsoids in n = 256, 16,384 exterior queries: one step
+    is hopf_union_eval (phi, argmin, gradient) followed by hopf_union_closest
+    (distance and closest point by Newton on s)."""
+    import torch
+    import paper_1605_01799_gb300 as hg
+    import workloads as wl
+    ws, rank, local, dev = init_device()
+    d = wl.ellipsoid_union()
+    K, n, B = d["K"], d["n"], len(d["t"])
+    tol, max_iter, s_tol, max_newton = 1e-12, 5000, 1e-6, 60
+    parts = [hg.Hopf(d["a"][k], hg.H_L2, centre=d["centres"][k], tol=tol, max_iter=max_iter, precision=hg.P_FP32,
+                     stop_rule=hg.STOP_UREL) for k in range(K)]
+    xd = torch.from_numpy(d["x"]).to(dev)
+    td = torch.from_numpy(d["t"]).to(dev)
+    st = {}
+
+    def step():
+        st["u"] = hg.union_eval(parts, xd, td, out=st.get("u"), workspace=st.get("u", {}).get("workspace"))
+        st["c"] = hg.union_closest(parts, xd, s_tol=s_tol, max_newton=max_newton, out=st.get("c"),
+                                   workspace=st["u"]["workspace"])
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ms, clocks = time_steps(step, args.steps, ws, local)
+    # the two calls timed apart (their shares of the step)
+    ms_eval, _ = time_steps(lambda: hg.union_eval(parts, xd, td, out=st["u"], workspace=st["u"]["workspace"]),
+                            args.steps, ws, local)
+    # work of the phi pass: every part's solve for every query, counted by
+    # evaluating each part alone on the same queries (same kernel, untimed)
+    iters_total = 0
+    for P in parts:
+        o = P.eval(xd, td)
+        iters_total += int(o["iters"].sum().item())
+    flops = UNION_FLOP_PER_COORD * n * iters_total
+    achieved = flops / (ms_eval * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK,
+            "traffic": None, "kernel": "k_union_parts + k_union_pick (the phi pass)", "ms_phi_pass": ms_eval,
+            "algorithmic_flops_per_launch": flops, "peak_source": ALU_SRC,
+            "work": "%d split Bregman iterations over %d query-part pairs, %.0f flop per coordinate-iteration"
+                    % (iters_total, K * B, UNION_FLOP_PER_COORD)}
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(d["x"]).pin_memory()
+        th = torch.from_numpy(d["t"]).pin_memory()
+        outs = {"phi": torch.empty(B, dtype=torch.float64).pin_memory(),
+                "grad": torch.empty(B, n, dtype=torch.float32).pin_memory(),
+                "dist": torch.empty(B, dtype=torch.float32).pin_memory(),
+                "closest": torch.empty(B, n, dtype=torch.float32).pin_memory()}
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            step()
+            outs["phi"].copy_(st["u"]["phi"], non_blocking=True)
+            outs["grad"].copy_(st["u"]["grad"], non_blocking=True)
+            outs["dist"].copy_(st["c"]["dist"], non_blocking=True)
+            outs["closest"].copy_(st["c"]["closest"], non_blocking=True)
+
+        ems, _ = time_steps(e2e_step, max(2, min(args.steps, 5)), ws, local)
+        e2e = {"value": ws * B / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(d["x"].nbytes + d["t"].nbytes),
+               "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        oparts = [oracle.Problem(d["a"][k], oracle.H_L2, centre=d["centres"][k], tol=tol, max_iter=max_iter,
+                                 stop_rule=oracle.STOP_UREL) for k in range(K)]
+        m = min(B, max(8, 20 * args.cpu_sample))
+        t0 = time.perf_counter()
+        oracle.union_eval(oparts, d["x"][:m].astype(np.float64), d["t"][:m].astype(np.float64))
+        oracle.union_closest(oparts, d["x"][:m].astype(np.float64), s_tol=s_tol, max_newton=max_newton)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "first %d queries, FP64 oracle union_eval + union_closest, same tolerances (%.1f s)" % (m, dt)}
+    if rank == 0:
+        line = {"metric": "union evals/s (phi, argmin, grad phi, distance, closest point), K=16 ellipsoids, n=256",
+                "value": ws * B / (ms * 1e-3), "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "ellipsoid_union_k16_n256_b16384", "K": K, "n": n, "batch_per_gpu": B,
+                           "tol_urel": tol, "s_tol": s_tol, "max_newton": max_newton,
+                           "l2": "inputs of 16 MiB fit L2; each step recomputes every solve from x"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * args.steps,
+                "status_ok_frac": float((st["u"]["status"] == 0).float().mean().item()),
+                "newton_mean": float(st["c"]["newton"].float().mean().item())}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_grad(args):
+    """Differentiation workload: n = 2048, H = l1, 32,768 queries.  One step is
+    hopf_eval (MIXED) followed by hopf_backward for g_x, g_t and the dense
+    g_A = -1/2 V^T diag(g) V."""
+    import torch
+    import paper_1605_01799_gb300 as hg
+    import workloads as wl
+    ws, rank, local, dev = init_device()
+    d = wl.dense_l1_grad()
+    A, n, B = d["A"], d["n"], len(d["t"])
+    h = hg.Hopf(A, hg.H_L1, tol=TOL, max_iter=MAX_ITER, precision=hg.P_MIXED)
+    xd = torch.from_numpy(d["x"]).to(dev)
+    td = torch.from_numpy(d["t"]).to(dev)
+    gd = torch.from_numpy(wl.normal(5008, B, 1.0).astype(np.float32)).to(dev)
+    wsb = h.workspace(B)
+    st = {}
+
+    def fwd():
+        st["o"] = h.eval(xd, td, out=st.get("o"), workspace=wsb)
+
+    def bwd():
+        st["b"] = h.backward(gd, st["o"]["grad"])
+
+    def step():
+        fwd()
+        bwd()
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ms, clocks = time_steps(step, args.steps, ws, local)
+    ms_b, _ = time_steps(bwd, args.steps, ws, local)
+    iters = st["o"]["iters"].cpu().numpy().astype(np.float64)
+    pk = peaks()
+    tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
+    f_fwd = float(np.sum(2.0 * n * n * (4.0 * iters + 3.0)))
+    f_bwd = 2.0 * n * n * B  # g_A = -1/2 V^T diag(g) V on FP32 CUDA cores
+    t_roof = f_fwd / (tc_peak * 1e12) + f_bwd / (ALU_PEAK * 1e12)
+    frac = t_roof / (ms * 1e-3)
+    roof = {"bound": "tensor+alu (work-weighted)", "achieved": frac, "peak": 1.0,
+            "unit": "fraction of the work-weighted roofline time", "frac": frac, "traffic": None,
+            "roofline_ms": 1e3 * t_roof, "forward_tensor_flops": f_fwd, "backward_alu_flops": f_bwd,
+            "backward_ms": ms_b, "backward_alu_frac": f_bwd / (ms_b * 1e-3) / 1e12 / ALU_PEAK,
+            "peak_source": "tensor: MEASURED_PEAKS.json bf16_tflops_sustained (measured) %.1f TFLOP/s; alu: %s"
+                           % (tc_peak, ALU_SRC)}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        P = oracle.Problem(A, oracle.H_L1, tol=TOL, max_iter=MAX_ITER, stop_rule=oracle.STOP_UREL)
+        m = max(8, args.cpu_sample)
+        P.eval(np.zeros((0, n)), np.zeros(0))  # factorisation, timed apart below
+        t0 = time.perf_counter()
+        P.eval(np.zeros((0, n)), np.zeros(0))
+        t_fact = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = P.eval(d["x"][:m].astype(np.float64), d["t"][:m].astype(np.float64))
+        oracle.backward(n, oracle.A_DENSE, oracle.H_L1, None, np.ones(m), r["grad"], d["t"][:m].astype(np.float64))
+        dt = max(time.perf_counter() - t0 - t_fact, 1e-9)
+        cpu = {"value": m / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "first %d queries: FP64 oracle eval + backward (g_A included), same stop rule; %.1f s, "
+                         "the factorisation of A + lambda I excluded" % (m, dt)}
+    if rank == 0:
+        line = {"metric": "Hopf evals/s forward + backward (phi, grad phi, d/dx, d/dt, d/dA), n=2048, dense A, l1",
+                "value": ws * B / (ms * 1e-3), "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16+f16 forward (fp32 accumulate), f32 backward",
+                "data": "synthetic",
+                "config": {"workload": "dense_l1_grad_n2048_b32768", "n": n, "batch_per_gpu": B, "tol_urel": TOL,
+                           "l2": "inputs larger than L2 (x is %d MiB per step)" % (d["x"].nbytes >> 20)},
+                "iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clocks, "gpu_launches": 6 * args.steps}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "union":
+        return run_union(args)
+    if args.workload == "grad":
+        return run_grad(args)
     import torch
     import paper_1605_01799_gb300 as hg
 

@@ -266,38 +266,50 @@ def _parts_array(parts):
     return arr
 
 
-def union_eval(parts, x, t, stream=None):
-    """phi = min_i phi_i over diagonal parts (Section 2.2)."""
+def _union_ws(arr, K, B, device, workspace):
+    import torch
+    b = ctypes.c_size_t()
+    _check(lib().hopf_union_workspace_size(arr, K, B, ctypes.byref(b)))
+    if workspace is not None and workspace.numel() >= b.value:
+        return workspace
+    return torch.empty(max(b.value, 1), dtype=torch.uint8, device=device)
+
+
+def union_eval(parts, x, t, out=None, workspace=None, stream=None):
+    """phi = min_i phi_i over diagonal parts (Section 2.2).  ``out`` (a dict
+    returned by an earlier call) and ``workspace`` may be passed back in to
+    reuse their buffers."""
     import torch
     B, n = x.shape
     arr = _parts_array(parts)
-    b = ctypes.c_size_t()
-    _check(lib().hopf_union_workspace_size(arr, len(parts), B, ctypes.byref(b)))
-    ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
-    out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
-           "grad": torch.empty(B, n, dtype=torch.float32, device=x.device),
-           "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
-           "iters": torch.empty(B, dtype=torch.int32, device=x.device),
-           "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    ws = _union_ws(arr, len(parts), B, x.device, workspace)
+    if out is None:
+        out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
+               "grad": torch.empty(B, n, dtype=torch.float32, device=x.device),
+               "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
+               "iters": torch.empty(B, dtype=torch.int32, device=x.device),
+               "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    out["workspace"] = ws
     _check(lib().hopf_union_eval(arr, len(parts), B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]),
                                  _ptr(out["argmin"]), _ptr(out["iters"]), _ptr(out["status"]), _ptr(ws), ws.numel(),
                                  _stream(stream)))
     return out
 
 
-def union_closest(parts, x, s_tol=1e-6, max_newton=50, stream=None):
-    """Distance and closest point to the union of {J_i <= 0} (Section 3.2)."""
+def union_closest(parts, x, s_tol=1e-6, max_newton=50, out=None, workspace=None, stream=None):
+    """Distance and closest point to the union of {J_i <= 0} (Section 3.2).
+    ``out`` and ``workspace`` as for union_eval."""
     import torch
     B, n = x.shape
     arr = _parts_array(parts)
-    b = ctypes.c_size_t()
-    _check(lib().hopf_union_workspace_size(arr, len(parts), B, ctypes.byref(b)))
-    ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=x.device)
-    out = {"dist": torch.empty(B, dtype=torch.float32, device=x.device),
-           "closest": torch.empty(B, n, dtype=torch.float32, device=x.device),
-           "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
-           "newton": torch.empty(B, dtype=torch.int32, device=x.device),
-           "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    ws = _union_ws(arr, len(parts), B, x.device, workspace)
+    if out is None:
+        out = {"dist": torch.empty(B, dtype=torch.float32, device=x.device),
+               "closest": torch.empty(B, n, dtype=torch.float32, device=x.device),
+               "argmin": torch.empty(B, dtype=torch.int32, device=x.device),
+               "newton": torch.empty(B, dtype=torch.int32, device=x.device),
+               "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    out["workspace"] = ws
     _check(lib().hopf_union_closest(arr, len(parts), B, _ptr(x), float(s_tol), int(max_newton), _ptr(out["dist"]),
                                     _ptr(out["closest"]), _ptr(out["argmin"]), _ptr(out["newton"]),
                                     _ptr(out["status"]), _ptr(ws), ws.numel(), _stream(stream)))

@@ -62,6 +62,21 @@ struct Group {
       }
     }
   }
+  // Sum of two values (the two shuffle chains run side by side).
+  __device__ static void sum2(T& a, T& b) {
+    if constexpr (G == 1) {
+      return;
+    } else if constexpr (G == 32) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+    } else {
+      T c = T(0);
+      sum3(a, b, c);
+    }
+  }
   __device__ static T sum(T a) {
     T b = T(0), c = T(0);
     sum3(a, b, c);
@@ -116,9 +131,24 @@ struct Query {
   }
 
   // Runs split Bregman at time t from the current (v, d, b); returns the
-  // iteration count, sets *conv.
+  // iteration count, sets *conv.  One loop per Hamiltonian family (shrink_1
+  // thresholds or the l2 scale) and stop rule, so each keeps only the state
+  // it reads.
   __device__ int solve(const DiagPart<T>& P, T t, bool* conv) {
+    if (P.h_kind == H_L2) {
+      return P.stop_rule == STOP_PAPER ? solve_rule<true, true>(P, t, conv) : solve_rule<true, false>(P, t, conv);
+    }
+    return P.stop_rule == STOP_PAPER ? solve_rule<false, true>(P, t, conv) : solve_rule<false, false>(P, t, conv);
+  }
+
+  template <bool L2, bool PAPER>
+  __device__ int solve_rule(const DiagPart<T>& P, T t, bool* conv) {
     const T lam = P.lam, tau = t / P.lam;
+    T thr[VPT];  // shrink_1 thresholds tau w_i
+    if constexpr (!L2) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) thr[j] = tau * wt(j);
+    }
     int k;
     *conv = false;
     for (k = 1; k <= P.max_iter; ++k) {
@@ -130,41 +160,54 @@ struct Query {
         z[j] = vn[j] + b[j];                                  // u^k = v^k + b^{k-1}
         zz += z[j] * z[j];
       }
-      T s2 = T(1);
-      if (P.h_kind == H_L2) {
-        const T nz = sqrt(Group<G, T>::sum(zz));
-        s2 = shrink2_scale(nz, tau);
-      }
-      T r1 = T(0), r2 = T(0), r3 = T(0);
+      if constexpr (!PAPER) {
+        // relative rule: |u^k - u^{k-1}|^2 and |u^k|^2 are both known before
+        // the prox, so one group reduction serves the l2 scale and the test
+        T r1 = T(0);
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) {
-        const T dn = P.h_kind == H_L2 ? s2 * z[j] : shrink1(z[j], tau * wt(j));  // eq. 3.4(b)
-        if (P.stop_rule == STOP_PAPER) {
+        for (int j = 0; j < VPT; ++j) {
+          const T du = z[j] - (d[j] + b[j]);  // u^{k-1} = d^{k-1} + b^{k-1}
+          r1 += du * du;
+        }
+        Group<G, T>::sum2(r1, zz);
+        T s2 = T(1);
+        if constexpr (L2) s2 = shrink2_scale(sqrt(zz), tau);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+          T dn;
+          if constexpr (L2) dn = s2 * z[j];            // eq. 3.4(b)
+          else dn = shrink1(z[j], thr[j]);
+          b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
+          d[j] = dn;
+        }
+        if (k >= 2 && r1 <= P.tol * (zz > T(1) ? zz : T(1))) {
+          *conv = true;
+          break;
+        }
+      } else {
+        T s2 = T(1);
+        if constexpr (L2) s2 = shrink2_scale(sqrt(Group<G, T>::sum(zz)), tau);
+        T r1 = T(0), r2 = T(0), r3 = T(0);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+          T dn;
+          if constexpr (L2) dn = s2 * z[j];            // eq. 3.4(b)
+          else dn = shrink1(z[j], thr[j]);
           r1 += (vn[j] - v[j]) * (vn[j] - v[j]);
           r2 += (dn - d[j]) * (dn - d[j]);
           r3 += (dn - vn[j]) * (dn - vn[j]);
-        } else {
-          const T du = z[j] - (d[j] + b[j]);  // u^k - u^{k-1}, u^{k-1} = d^{k-1} + b^{k-1}
-          r1 += du * du;
+          b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
+          d[j] = dn;
+          v[j] = vn[j];
         }
-        b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
-        d[j] = dn;
-        v[j] = vn[j];
-      }
-      if (P.stop_rule == STOP_PAPER) {
         Group<G, T>::sum3(r1, r2, r3);
         if (r1 <= P.tol && r2 <= P.tol && r3 <= P.tol) {
           *conv = true;
           break;
         }
-      } else {
-        Group<G, T>::sum3(r1, zz, r2);
-        if (k >= 2 && r1 <= P.tol * (zz > T(1) ? zz : T(1))) {
-          *conv = true;
-          break;
-        }
       }
     }
+    // (v is kept only by the paper rule, the one reader of it)
     return k > P.max_iter ? P.max_iter : k;
   }
 
