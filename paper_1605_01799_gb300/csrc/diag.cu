@@ -62,6 +62,20 @@ struct Group {
       }
     }
   }
+  // Value of the group's first thread, in every thread of the group.
+  __device__ static T bcast0(T a) {
+    if constexpr (G == 1) {
+      return a;
+    } else if constexpr (G == 32) {
+      return __shfl_sync(0xffffffffu, a, 0);
+    } else {
+      __shared__ T s0;
+      __syncthreads();
+      if (threadIdx.x == 0) s0 = a;
+      __syncthreads();
+      return s0;
+    }
+  }
   // Sum of two values (the two shuffle chains run side by side).
   __device__ static void sum2(T& a, T& b) {
     if constexpr (G == 1) {
@@ -348,6 +362,7 @@ struct UnionArgs {
   float* s_parts;       // [batch][K] Newton root per part (closest point)
   int32_t* it_parts;    // [batch][K]
   uint8_t* st_parts;    // [batch][K]
+  unsigned* best;       // [batch] smallest root found so far (float bits; closest point)
   float s_tol;
   int max_newton;
   // outputs
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(block_of<G>()) k_closest_parts(UnionArgs U) {
   Q.load(P, U.x + q * U.n, U.n);
   Q.cold_start();
   double s = 0.0;
-  bool ok = false, finite = true;
+  bool ok = false, finite = true, pruned = false;
   int l;
   for (l = 0; l < U.max_newton; ++l) {
     bool conv;
@@ -449,12 +464,26 @@ __global__ void __launch_bounds__(block_of<G>()) k_closest_parts(UnionArgs U) {
     if (fabs(ds) <= (double)U.s_tol * (s > 1.0 ? s : 1.0)) {
       ok = true;
       ++l;
+      if (group_lane<G>() == 0 && s >= 0.0) atomicMin(U.best + q, __float_as_uint((float)s));
+      break;
+    }
+    // psi is convex and non-increasing in s (a maximum of affine functions of
+    // s with slopes -H(v) <= 0), so Newton from s = 0 rises monotonically to
+    // the part's root: an iterate already past another part's root by a
+    // clear margin (1e-3, far above the Newton tolerance) cannot be the
+    // nearest part's, and the part stops.  The decision is the group's first
+    // thread's, so the group stays together.
+    float bs = __uint_as_float(*((volatile unsigned*)(U.best + q)));
+    bs = Group<G, float>::bcast0(bs);
+    if (s > (double)bs + 1e-3 * ((double)bs > 1.0 ? (double)bs : 1.0)) {
+      pruned = true;
+      ++l;
       break;
     }
   }
   if (group_lane<G>() == 0) {
     U.s_parts[pair] = (float)s;
-    U.phi_parts[pair] = s;
+    U.phi_parts[pair] = pruned ? INFINITY : s;  // a pruned part is not the nearest
     U.it_parts[pair] = l;
     U.st_parts[pair] = !finite ? Q_NONFINITE : (ok ? Q_OK : Q_NOT_CONVERGED);
   }
@@ -504,7 +533,8 @@ __global__ void __launch_bounds__(block_of<G>()) k_closest_pick(UnionArgs U) {
 size_t union_workspace(int K, int n, int64_t batch) {
   (void)n;
   size_t b = (size_t)batch * K;
-  return round_up(b * 8, 256) + round_up(b * 4, 256) + round_up(b * 4, 256) + round_up(b, 256);
+  return round_up(b * 8, 256) + round_up(b * 4, 256) + round_up(b * 4, 256) + round_up(b, 256) +
+         round_up((size_t)batch * 4, 256);
 }
 
 static hopf_status carve_union(const hopf_handle* parts, int K, int64_t batch, void* ws, UnionArgs* U) {
@@ -518,6 +548,8 @@ static hopf_status carve_union(const hopf_handle* parts, int K, int64_t batch, v
   U->it_parts = (int32_t*)p;
   p += round_up(b * 4, 256);
   U->st_parts = (uint8_t*)p;
+  p += round_up(b, 256);
+  U->best = (unsigned*)p;
   for (int i = 0; i < K; ++i) U->parts[i] = part_of<float>(parts[i]);
   U->K = K;
   U->n = parts[0]->n;
@@ -581,6 +613,8 @@ hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const 
   U.argmin = argmin;
   U.iters = newton;
   U.qstatus = qstatus;
+  // best roots start at a huge positive float (bytes 0x7f: 3.4e38)
+  HOPF_CUDA(cudaMemsetAsync(U.best, 0x7f, (size_t)batch * 4, stream));
   return dispatch_union(U, true, stream);
 }
 
