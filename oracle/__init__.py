@@ -12,8 +12,10 @@ Pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``:
 closed forms of Section 1 (l1 with a diagonal ellipsoid, l2 with a sphere),
 their weighted / diagonal generalisations, phi(x,0) = J(x), an exact
 active-set (KKT) solve, duality-gap bounds, brute-force Hopf-Lax minimisation
-at n = 2, finite differences in x and t, and the ellipsoid projection of
-Section 4.3.  Parity unpinned: iteration counts (the paper prints none).
+at n = 2, finite differences in x and t, the ellipsoid projection of
+Section 4.3, the control's membership in dH and the Hopf-Lax value
+J(x_T) = phi, and brute-force minimisation at n = 2 of the Hopf formula with
+the Hamiltonian min_i H_i.  Parity unpinned: iteration counts (the paper prints none).
 """
 import ctypes
 import os
@@ -64,6 +66,8 @@ def lib():
         _lib.orc_eval_batch.restype = ctypes.c_int
         _lib.orc_union_eval.restype = ctypes.c_int
         _lib.orc_union_closest.restype = ctypes.c_int
+        _lib.orc_maxH_eval.restype = ctypes.c_int
+        _lib.orc_control.restype = None
         _lib.orc_factor.restype = ctypes.c_int
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_H.restype = ctypes.c_double
@@ -166,3 +170,37 @@ def backward(n, a_kind, h_kind, w, g_phi, vstar, t, want_A=True):
     lib().orc_backward(n, a_kind, h_kind, _p(w), ctypes.c_int64(B), _p(g_phi), _p(vstar), _p(t),
                        _p(g_x), _p(g_t), _p(g_A))
     return {"g_x": g_x, "g_t": g_t, "g_A": g_A}
+
+
+def control(problem, x, t, grad):
+    """Optimal control beta = (x - c - A p) / t in dH(p) for the minimiser p
+    (= grad phi), and the terminal point x_T = x - t beta (Section 2: the
+    control beta = grad H(grad phi); the Hopf-Lax minimiser).  beta = 0 and
+    x_T = x at t = 0."""
+    n = problem.n
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, n)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+    grad = np.ascontiguousarray(grad, dtype=np.float64).reshape(-1, n)
+    B = x.shape[0]
+    beta = np.empty_like(x)
+    x_T = np.empty_like(x)
+    st = problem._struct()
+    lib().orc_control(ctypes.byref(st), ctypes.c_int64(B), _p(x), _p(t), _p(grad), _p(beta), _p(x_T))
+    return {"beta": beta, "x_T": x_T}
+
+
+def maxH_eval(parts, x, t):
+    """phi = max_i phi_i over parts that share J and differ in H (Section 2.2:
+    the solution for the Hamiltonian min_i H_i), argmax (ties -> smallest),
+    gradient of the maximising part, and the summed iteration count."""
+    n = parts[0].n
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, n)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+    B = x.shape[0]
+    arr = (_Problem * len(parts))(*[p._struct() for p in parts])
+    phi = np.empty(B); grad = np.empty_like(x)
+    am = np.empty(B, np.int32); it = np.empty(B, np.int32)
+    rc = lib().orc_maxH_eval(arr, len(parts), ctypes.c_int64(B), _p(x), _p(t), _p(phi), _p(grad), _p(am), _p(it))
+    if rc != 0:
+        raise ValueError("oracle: A + lambda I is not SPD")
+    return {"phi": phi, "grad": grad, "argmax": am, "iters": it}

@@ -458,3 +458,79 @@ void orc_backward(int32_t n, int32_t a_kind, int32_t h_kind, const double *w, in
     }
     (void)t;
 }
+
+/* ---- optimal control and terminal point (Section 2, the control remark and
+ *      the Hopf-Lax discussion at the end of Section 2.2) ------------------- */
+
+/* For the minimiser p of eq. 3.3 at (x, t), t > 0, the optimality condition
+ * 0 in A p + c - x + t dH(p) gives the control as the element of dH(p)
+ *     beta = (x - c - A p) / t,
+ * which equals grad H(p) wherever H is differentiable (the paper's
+ * beta(t) = grad H(grad phi)), and the terminal point of the optimal
+ * trajectory, the minimiser of the Hopf-Lax formula, x_T = x - t beta
+ * (= c + A p).  At t = 0 the control is taken as 0 and x_T = x.
+ * beta and x_T hold batch x n values; grad holds the minimisers. */
+void orc_control(const orc_problem *p, int64_t batch, const double *x, const double *t, const double *grad,
+                 double *beta, double *x_T)
+{
+    const int n = p->n;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < batch; ++q) {
+        const double *g = grad + q * n;
+        for (int i = 0; i < n; ++i) {
+            double ap = 0.0;
+            if (p->a_kind == ORC_A_DIAG) ap = p->A[i] * g[i];
+            else
+                for (int j = 0; j < n; ++j) ap += p->A[(int64_t)i * n + j] * g[j];
+            const double xi = x[q * n + i];
+            const double b = t[q] > 0.0 ? (xi - (p->c ? p->c[i] : 0.0) - ap) / t[q] : 0.0;
+            beta[q * n + i] = b;
+            x_T[q * n + i] = xi - t[q] * b;
+        }
+    }
+}
+
+/* ---- maximum over Hamiltonians (Section 2.2, the remark on the minimum of
+ *      Hamiltonians): for k Hamiltonians H_i and one initial data J,
+ *      max_i phi_i solves the HJ equation with Hamiltonian min_i H_i. ------- */
+
+/* parts[i] share n, A, c and c0 and differ in H (kind and weights).  phi[q]
+ * = max_i phi_i(x_q, t_q), argmax[q] = the first maximising i, grad = the
+ * gradient of that part, iters = the iterations summed over parts. */
+int orc_maxH_eval(const orc_problem *parts, int32_t K, int64_t batch, const double *x, const double *t,
+                  double *phi, double *grad, int32_t *argmax, int32_t *iters)
+{
+    const int n = parts[0].n;
+    double *L = NULL;
+    if (parts[0].a_kind == ORC_A_DENSE) {
+        L = (double *)malloc(sizeof(double) * (size_t)n * n);
+        if (orc_factor(n, parts[0].A, parts[0].lambda, L) != 0) { free(L); return -1; }
+    }
+#pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * 6 * (size_t)n);
+        double *g = (double *)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < batch; ++q) {
+            double best = -INFINITY;
+            int bi = -1, it = 0;
+            for (int i = 0; i < K; ++i) {
+                orc_result r;
+                orc_solve(&parts[i], L, x + q * n, t[q], g, &r, work, NULL);
+                it += r.iters;
+                if (r.phi > best) {
+                    best = r.phi;
+                    bi = i;
+                    memcpy(grad + q * n, g, sizeof(double) * (size_t)n);
+                }
+            }
+            phi[q] = best;
+            argmax[q] = bi;
+            iters[q] = it;
+        }
+        free(work);
+        free(g);
+    }
+    free(L);
+    return 0;
+}

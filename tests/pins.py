@@ -114,10 +114,16 @@ def hopf_lax_upper(Ainv, A, y, t, w, v, c0=0.5, h="wl1"):
 
 
 def hopf_lax_bruteforce_2d(Ainv, y, t, w, c0=0.5, h="wl1"):
-    """n = 2 brute force of min_{c in C} J(y - t c).  For the box the convex
-    quadratic's minimum is enumerated over the interior, the four edges
-    (clamped 1-D minimum) and the four corners; for the disk, over the interior
-    minimum and a 200,001-point sweep of the circle refined by golden section."""
+    """n = 2 brute force of min_{c in C} J(y - t c) (the value)."""
+    return hopf_lax_argmin_2d(Ainv, y, t, w, c0, h)[0]
+
+
+def hopf_lax_argmin_2d(Ainv, y, t, w, c0=0.5, h="wl1"):
+    """n = 2 brute force of min_{c in C} J(y - t c): returns (value, c at the
+    minimum).  For the box the convex quadratic's minimum is enumerated over
+    the interior, the four edges (clamped 1-D minimum) and the four corners;
+    for the disk, over the interior minimum and a 200,001-point sweep of the
+    circle refined by golden section."""
     q = lambda c: J_value(Ainv, y - t * c, c0)
     P = t * t * Ainv
     cands = []
@@ -157,7 +163,8 @@ def hopf_lax_bruteforce_2d(Ainv, y, t, w, c0=0.5, h="wl1"):
             for s1 in (-1, 1):
                 cands.append(np.array([s0 * w[0], s1 * w[1]]))
     vals = [q(c) for c in cands]
-    return min(vals)
+    k = int(np.argmin(vals))
+    return vals[k], cands[k]
 
 
 def ellipsoid_projection(yv, semi, tol=1e-15, max_iter=200):

@@ -314,3 +314,111 @@ def test_golden_section1_example(orc):
         r = P.eval(x[None], [t])
         assert abs(r["phi"][0] - phi) <= 1e-10 * max(1, abs(phi))
         assert np.abs(r["grad"][0] - g).max() <= 1e-10
+
+
+# ---- P9: optimal control and terminal point (Section 2) ---------------------
+
+def _dual_ball_excess(beta, h, w):
+    """How far beta lies outside the unit ball of the dual norm of H."""
+    if h == "l2":
+        return max(0.0, np.linalg.norm(beta) - 1.0)
+    return max(0.0, float(np.max(np.abs(beta) - w)))
+
+
+@pytest.mark.parametrize("h", ["l1", "wl1", "l2"])
+@pytest.mark.parametrize("dense", [False, True])
+def test_control_is_a_subgradient_and_the_hopf_lax_minimiser(orc, h, dense):
+    """beta = (x - c - A p)/t must lie in dH(p): equal to grad H(p) where H is
+    differentiable (w_i sign p_i for p_i != 0; p / |p| for l2), inside the dual
+    ball where it is not, and <beta, p> = H(p) (1-homogeneity).  The terminal
+    point x_T = x - t beta must be the Hopf-Lax minimiser: x - x_T in t C and
+    J(x_T) = phi(x, t)."""
+    n, B = 12, 24
+    kind = {"l1": orc.H_L1, "wl1": orc.H_WL1, "l2": orc.H_L2}[h]
+    w = wl.uniform(9101, n, 0.5, 1.5) if h == "wl1" else np.ones(n)
+    c = wl.normal(9106, n, 0.5)
+    if dense:
+        A, Ainv = _dense(n, 9102, 0.3, 3.0)
+    else:
+        A = wl.uniform(9102, n, 0.5, 2.0)
+        Ainv = np.diag(1.0 / A)
+    x = wl.normal(9104, B * n, 2.0).reshape(B, n)
+    t = wl.uniform(9105, B, 0.2, 2.0)
+    P = orc.Problem(A, kind, w=w if h == "wl1" else None, centre=c, tol=1e-30, max_iter=50000,
+                    stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    ctl = orc.control(P, x, t, r["grad"])
+    beta, xT = ctl["beta"], ctl["x_T"]
+    for q in range(B):
+        p = r["grad"][q]
+        if h == "l2":
+            if np.linalg.norm(p) > 1e-9:
+                assert np.allclose(beta[q], p / np.linalg.norm(p), atol=1e-7)
+        else:
+            on = np.abs(p) > 1e-9
+            assert np.allclose(beta[q][on], (w * np.sign(p))[on], atol=1e-7)
+        assert _dual_ball_excess(beta[q], h, w) <= 1e-7
+        Hp = P.H(p)
+        assert abs(beta[q] @ p - Hp) <= 1e-8 * max(1.0, Hp)
+        # Hopf-Lax: x_T = x - t beta attains phi
+        z = xT[q] - c
+        J = 0.5 * z @ Ainv @ z - 0.5
+        assert abs(J - r["phi"][q]) <= 1e-8 * max(1.0, abs(r["phi"][q]))
+    # t = 0: no control, the point stays
+    ctl0 = orc.control(P, x[:2], np.zeros(2), r["grad"][:2])
+    assert np.all(ctl0["beta"] == 0) and np.array_equal(ctl0["x_T"], x[:2])
+
+
+@pytest.mark.parametrize("h", ["wl1", "l2"])
+def test_terminal_point_bruteforce_n2(orc, h):
+    """n = 2: the terminal point against brute-force minimisation of J over
+    the set x - t C (Hopf-Lax), which shares nothing with split Bregman."""
+    rng = np.random.default_rng(17)
+    for trial in range(10):
+        G = rng.normal(size=(2, 2))
+        A = G @ G.T + 0.3 * np.eye(2)
+        Ainv = np.linalg.inv(A)
+        w = rng.uniform(0.5, 1.5, 2) if h == "wl1" else np.ones(2)
+        x = rng.normal(scale=2, size=2)
+        t = rng.uniform(0.1, 2.0)
+        P = orc.Problem(A, orc.H_WL1 if h == "wl1" else orc.H_L2, w=w if h == "wl1" else None, tol=1e-30,
+                        max_iter=50000, stop_rule=orc.STOP_UREL)
+        r = P.eval(x[None], [t])
+        xT = orc.control(P, x[None], [t], r["grad"])["x_T"][0]
+        val, cbest = pins.hopf_lax_argmin_2d(Ainv, x, t, w, h=h)
+        assert np.linalg.norm(xT - (x - t * cbest)) <= 1e-5 * max(1.0, np.linalg.norm(xT)), (trial, xT, x - t * cbest)
+
+
+# ---- P10: maximum over Hamiltonians (Section 2.2) --------------------------
+
+def test_max_over_hamiltonians_solves_the_min_hamiltonian_pde(orc):
+    """With one J and Hamiltonians H_1 = weighted l1 (weights 0.3 and 1.5, so
+    it lies below l2 along one axis and above it along the other) and
+    H_2 = l2, max_i phi_i must equal brute-force Hopf-Lax values per part and
+    satisfy d phi/dt = -min_i H_i(grad phi) (central differences in t)."""
+    rng = np.random.default_rng(23)
+    w = np.array([0.3, 1.5])
+    seen = set()
+    for trial in range(16):
+        G = rng.normal(size=(2, 2))
+        A = G @ G.T + 0.3 * np.eye(2)
+        Ainv = np.linalg.inv(A)
+        x = rng.normal(scale=2, size=2)
+        t = rng.uniform(0.3, 2.0)
+        parts = [orc.Problem(A, orc.H_WL1, w=w, tol=1e-30, max_iter=50000, stop_rule=orc.STOP_UREL),
+                 orc.Problem(A, orc.H_L2, tol=1e-30, max_iter=50000, stop_rule=orc.STOP_UREL)]
+        r = orc.maxH_eval(parts, x[None], [t])
+        bf = max(pins.hopf_lax_bruteforce_2d(Ainv, x, t, w, h="wl1"),
+                 pins.hopf_lax_bruteforce_2d(Ainv, x, t, np.ones(2), h="l2"))
+        assert abs(r["phi"][0] - bf) <= 1e-9 * max(1, abs(bf))
+        seen.add(int(r["argmax"][0]))
+        hh = 1e-5
+        rp = orc.maxH_eval(parts, x[None], [t + hh])
+        rm = orc.maxH_eval(parts, x[None], [t - hh])
+        if rp["argmax"][0] != r["argmax"][0] or rm["argmax"][0] != r["argmax"][0]:
+            continue  # at a switch between parts phi is not differentiable in t
+        dphidt = (rp["phi"][0] - rm["phi"][0]) / (2 * hh)
+        p = r["grad"][0]
+        Hmin = min(float(np.abs(p) @ w), float(np.linalg.norm(p)))
+        assert abs(dphidt + Hmin) <= 1e-6 * max(1, Hmin), (trial, dphidt, Hmin)
+    assert seen == {0, 1}  # both Hamiltonians win somewhere
