@@ -12,6 +12,8 @@ d phi/dt) per second.
     python bench.py --workload ragged      # 512-instance ragged batch (one graph replay per step)
     python bench.py --workload union       # union of 16 ellipsoids: phi, argmin, distance, closest point
     python bench.py --workload grad        # n = 2048 forward + envelope-theorem backward
+    python bench.py --workload control     # the dense workload with the optimal control and terminal point
+    python bench.py --workload maxh        # maximum over three Hamiltonians, diagonal J, n = 256
 
 For N > 1 launch under torch.distributed.run: every rank evaluates its own
 65,536 queries (weak scaling, no collective on the data path); the time is the
@@ -53,7 +55,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=192)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad"])
+    p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh"])
     return p.parse_args()
 
 
@@ -551,6 +553,178 @@ def run_grad(args):
         torch.distributed.destroy_process_group()
 
 
+def run_control(args):
+    """The metric's dense workload (n = 1024, 65,536 queries, weighted l1,
+    MIXED) through hopf_eval_control: phi, grad phi, d phi/dt, the control
+    beta in dH(grad phi) and the terminal point x - t beta."""
+    import torch
+    import paper_1605_01799_gb300 as hg
+    ws, rank, local, dev = init_device()
+    n, B = args.n, args.batch
+    A, w, x, t = workload(n, B, rank)
+    h = hg.Hopf(A, hg.H_WL1, w=w, tol=TOL, max_iter=MAX_ITER, precision=hg.P_MIXED)
+    xd = torch.from_numpy(x).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    wsb = h.workspace(B)
+    st = {}
+
+    def step():
+        st["o"] = h.eval_control(xd, td, out=st.get("o"), workspace=wsb)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record()
+    ev[1].record()
+    h.profile_events(*ev)
+    ms, clocks = time_steps(step, args.steps, ws, local)
+    h.profile_events(None, None)
+    kern_ms = ev[0].elapsed_time(ev[1])  # the last step's solver launch
+    iters = st["o"]["iters"].cpu().numpy().astype(np.float64)
+    pk = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    flops = float(np.sum(2.0 * n * n * (4.0 * iters + 3.0)))
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        th = torch.from_numpy(t).pin_memory()
+        outs = {k: torch.empty(st["o"][k].shape, dtype=st["o"][k].dtype).pin_memory()
+                for k in ("phi", "grad", "dphidt", "beta", "x_final")}
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            step()
+            for k, v in outs.items():
+                v.copy_(st["o"][k], non_blocking=True)
+
+        ems, _ = time_steps(e2e_step, max(2, min(args.steps, 5)), ws, local)
+        e2e = {"value": ws * B / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+               "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        rate, threads, r, dt = oracle_sample(A, w, x, t, args.cpu_sample, TOL)
+        P = oracle.Problem(A, oracle.H_WL1, w=w, tol=TOL, max_iter=MAX_ITER, stop_rule=oracle.STOP_UREL)
+        m = args.cpu_sample
+        t0 = time.perf_counter()
+        oracle.control(P, x[:m].astype(np.float64), t[:m].astype(np.float64), r["grad"])
+        dt += time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "evals/s", "cores": threads, "kind": "oracle",
+               "sample": "first %d queries: FP64 oracle eval + control, same stop rule (%.1f s; the factorisation "
+                         "of A + lambda I excluded)" % (m, dt)}
+    if rank == 0:
+        line = {"metric": "Hopf evals/s with optimal control and terminal point, n=1024, batch 64K, dense A, "
+                          "weighted l1", "value": ws * B / (ms * 1e-3), "unit": "evals/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f16 (fp32 accumulate)", "data": "synthetic",
+                "config": {"workload": "dense_wl1_n%d_b%d_control" % (n, B), "n": n, "batch_per_gpu": B,
+                           "tol_urel": TOL, "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
+                "iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * args.steps}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def maxh_workload(n=256, B=16384, w_=7):
+    import workloads as wl
+    a = wl.uniform(1000 * w_ + 2, n, 0.5, 2.0)
+    c = wl.normal(1000 * w_ + 6, n, 0.5)
+    wt = wl.uniform(1000 * w_ + 3, n, 0.03, 0.15)
+    x = wl.normal(1000 * w_ + 4, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(1000 * w_ + 5, B, 0.1, 3.0).astype(np.float32)
+    return a, c, wt, x, t
+
+
+def run_maxh(args):
+    """Maximum over three Hamiltonians (l1, weighted l1 with weights in
+    [0.03, 0.15], l2) for one diagonal J, n = 256, 16,384 queries: one step
+    is hopf_maxH_eval.  (With these weights the weighted l1 and the l2 parts
+    each take the maximum on part of the batch; l1 never lies below l2.)"""
+    import torch
+    import paper_1605_01799_gb300 as hg
+    ws, rank, local, dev = init_device()
+    n, B = 256, 16384
+    a, c, wt, x, t = maxh_workload(n, B)
+    tol, max_iter = 1e-12, 3000
+    kinds = [(hg.H_L1, None), (hg.H_WL1, wt), (hg.H_L2, None)]
+    parts = [hg.Hopf(a, hk, w=ww, centre=c, tol=tol, max_iter=max_iter, precision=hg.P_FP32,
+                     stop_rule=hg.STOP_UREL) for hk, ww in kinds]
+    xd = torch.from_numpy(x).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    st = {}
+
+    def step():
+        st["m"] = hg.maxH_eval(parts, xd, td, out=st.get("m"), workspace=st.get("m", {}).get("workspace"))
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ms, clocks = time_steps(step, args.steps, ws, local)
+    iters_total = 0
+    for P in parts:
+        o = P.eval(xd, td)
+        iters_total += int(o["iters"].sum().item())
+    flops = UNION_FLOP_PER_COORD * n * iters_total
+    achieved = flops / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK,
+            "traffic": None, "kernel": "k_union_parts + k_union_pick (maximum mode)",
+            "algorithmic_flops_per_launch": flops, "peak_source": ALU_SRC,
+            "work": "%d split Bregman iterations over %d query-part pairs, %.0f flop per coordinate-iteration"
+                    % (iters_total, 3 * B, UNION_FLOP_PER_COORD)}
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        th = torch.from_numpy(t).pin_memory()
+        outs = {"phi": torch.empty(B, dtype=torch.float64).pin_memory(),
+                "grad": torch.empty(B, n, dtype=torch.float32).pin_memory(),
+                "argmax": torch.empty(B, dtype=torch.int32).pin_memory()}
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            step()
+            for k, v in outs.items():
+                v.copy_(st["m"][k], non_blocking=True)
+
+        ems, _ = time_steps(e2e_step, max(2, min(args.steps, 5)), ws, local)
+        e2e = {"value": ws * B / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+               "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        oparts = [oracle.Problem(a, hk, w=ww, centre=c, tol=tol, max_iter=max_iter, stop_rule=oracle.STOP_UREL)
+                  for hk, ww in kinds]
+        m = B  # the whole batch takes well under the 10-30 s budget
+        t0 = time.perf_counter()
+        oracle.maxH_eval(oparts, x[:m].astype(np.float64), t[:m].astype(np.float64))
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "the whole batch (%d queries), FP64 oracle maxH_eval, same tolerances (%.1f s)" % (m, dt)}
+    if rank == 0:
+        am = st["m"]["argmax"].cpu().numpy()
+        line = {"metric": "evals/s of the maximum over 3 Hamiltonians (phi, argmax, grad phi), diagonal J, n=256",
+                "value": ws * B / (ms * 1e-3), "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "maxh_k3_n256_b16384", "K": 3, "n": n, "batch_per_gpu": B, "tol_urel": tol,
+                           "l2": "inputs of 16 MiB fit L2; each step recomputes every solve from x"},
+                "argmax_counts": np.bincount(am, minlength=3).tolist(),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * args.steps}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -561,6 +735,10 @@ def main():
         return run_union(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "control":
+        return run_control(args)
+    if args.workload == "maxh":
+        return run_maxh(args)
     import torch
     import paper_1605_01799_gb300 as hg
 

@@ -147,9 +147,38 @@ hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const d
                           double* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
                           cudaStream_t stream);
 
+/* Optimal control and terminal point (Section 2: the control of the optimal
+ * trajectory is beta = grad H(grad_x phi); for a 1-homogeneous H the terminal
+ * point is the Hopf-Lax minimiser x - t beta).  Same call as hopf_eval, plus
+ *   beta    [batch][n] float: the control.  At the fixed point the optimality
+ *           condition of eq. 3.3 gives lambda b = y - A p, so the library
+ *           returns beta = b / (t / lambda) = (u - prox(u)) / (t / lambda),
+ *           which lies in the subdifferential dH(p) (equal to grad H(p)
+ *           where H is differentiable); 0 when t = 0.  Device, required.
+ *   x_final [batch][n] float: x - t beta (device, may be NULL).
+ * FP32-output handles (diagonal FP32, dense FP32 / MIXED / BF16); FP64
+ * handles return HOPF_EUNSUPPORTED.  Workspace as for hopf_eval. */
+hopf_status hopf_eval_control(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                              float* dphidt, int32_t* iters, uint8_t* qstatus, float* beta, float* x_final,
+                              void* workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Maximum over Hamiltonians (Section 2.2: for one convex initial data J and
+ * Hamiltonians H_1..H_K, max_i phi_i solves the HJ equation with the
+ * Hamiltonian min_i H_i).  parts: K diagonal FP32 handles that share n and
+ * J (A, centre, c0; not checked beyond n) and may differ in h_kind and
+ * weights.  phi [batch] double = max_i phi_i; grad [batch][n] = the gradient
+ * of the maximising part; argmax [batch] int32 (ties -> smallest i); iters
+ * [batch] (iterations of that part, may be NULL); qstatus [batch] (may be
+ * NULL); all device.  workspace: hopf_union_workspace_size(parts, K, batch)
+ * bytes. */
+hopf_status hopf_maxH_eval(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, const float* t,
+                           double* phi, float* grad, int32_t* argmax, int32_t* iters, uint8_t* qstatus,
+                           void* workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* Union of initial data (Section 2.2: the pointwise minimum of the solutions
  * for convex J_i solves the problem with initial data min_i J_i).
- * parts: K handles, all diagonal FP32 with the same n and h_kind.
+ * parts: K handles, all diagonal FP32 with the same n and h_kind
+ * (hopf_union_workspace_size asks for the same n only).
  *   phi [batch] double = min_i phi_i; grad [batch][n] float = grad of the
  *   minimising part; argmin [batch] int32 (ties -> smallest i); iters [batch]
  *   (iterations of the minimising part), qstatus [batch]; all device.

@@ -29,7 +29,8 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
            "hopf_backward",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
-           "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_last_error", "hopf_version"]
+           "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
+           "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -76,6 +77,9 @@ def lib():
             "hopf_batch_workspace_size": ([_vp, _vp, ctypes.POINTER(_sz)], ctypes.c_int),
             "hopf_batch_eval": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "hopf_eval_control": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+                                  ctypes.c_int),
+            "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
             "hopf_version": ([], ctypes.c_char_p),
         }
@@ -169,6 +173,28 @@ class Hopf:
         f = lib().hopf_eval_f64 if fp64 else lib().hopf_eval
         _check(f(self.handle, B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]), _ptr(out.get("dphidt")),
                  _ptr(out.get("iters")), _ptr(out.get("status")), _ptr(ws), nbytes, _stream(stream)))
+        return out
+
+    def eval_control(self, x, t, out=None, workspace=None, stream=None):
+        """eval plus the optimal control beta in dH(grad phi) and the terminal
+        point x_final = x - t beta (Section 2), both [B, n] float32."""
+        import torch
+        assert x.dtype == torch.float32 and t.dtype == torch.float32 and x.is_cuda
+        B = x.shape[0]
+        if out is None:
+            out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
+                   "grad": torch.empty(B, self.n, dtype=torch.float32, device=x.device),
+                   "dphidt": torch.empty(B, dtype=torch.float32, device=x.device),
+                   "iters": torch.empty(B, dtype=torch.int32, device=x.device),
+                   "status": torch.empty(B, dtype=torch.uint8, device=x.device),
+                   "beta": torch.empty(B, self.n, dtype=torch.float32, device=x.device),
+                   "x_final": torch.empty(B, self.n, dtype=torch.float32, device=x.device)}
+        ws = workspace if workspace is not None else self.workspace(B)
+        nbytes = 0 if ws is None else ws.numel()
+        _check(lib().hopf_eval_control(self.handle, B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]),
+                                       _ptr(out.get("dphidt")), _ptr(out.get("iters")), _ptr(out.get("status")),
+                                       _ptr(out["beta"]), _ptr(out.get("x_final")), _ptr(ws), nbytes,
+                                       _stream(stream)))
         return out
 
     def profile_events(self, start=None, stop=None):
@@ -293,6 +319,26 @@ def union_eval(parts, x, t, out=None, workspace=None, stream=None):
     _check(lib().hopf_union_eval(arr, len(parts), B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]),
                                  _ptr(out["argmin"]), _ptr(out["iters"]), _ptr(out["status"]), _ptr(ws), ws.numel(),
                                  _stream(stream)))
+    return out
+
+
+def maxH_eval(parts, x, t, out=None, workspace=None, stream=None):
+    """phi = max_i phi_i over diagonal parts that share J and differ in H
+    (Section 2.2: the solution for the Hamiltonian min_i H_i)."""
+    import torch
+    B, n = x.shape
+    arr = _parts_array(parts)
+    ws = _union_ws(arr, len(parts), B, x.device, workspace)
+    if out is None:
+        out = {"phi": torch.empty(B, dtype=torch.float64, device=x.device),
+               "grad": torch.empty(B, n, dtype=torch.float32, device=x.device),
+               "argmax": torch.empty(B, dtype=torch.int32, device=x.device),
+               "iters": torch.empty(B, dtype=torch.int32, device=x.device),
+               "status": torch.empty(B, dtype=torch.uint8, device=x.device)}
+    out["workspace"] = ws
+    _check(lib().hopf_maxH_eval(arr, len(parts), B, _ptr(x), _ptr(t), _ptr(out["phi"]), _ptr(out["grad"]),
+                                _ptr(out["argmax"]), _ptr(out["iters"]), _ptr(out["status"]), _ptr(ws), ws.numel(),
+                                _stream(stream)))
     return out
 
 

@@ -37,6 +37,9 @@ struct SimtArgs {
   float lam, tol;
   DenseWs ws;
   float* grad;      // [B][n] user output
+  const float* x;   // [B][n] the caller's queries (terminal point)
+  float* beta;      // optional: control in dH(grad phi) [B][n]
+  float* xfin;      // optional: terminal point x - t beta [B][n]
 };
 
 // Per-query data of the current column tile, decided at the start of an item.
@@ -328,7 +331,16 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
           f0[jj] += (double)yv[e] * pd - 0.5 * pd * (double)acc[hh * 4 + e][jj];
           f1[jj] += a.h_kind == H_L2 ? pd * pd : (double)wv[e] * fabs(pd);
           const int row = row0 + e;
-          if (tq.act[j] && row < a.n) a.grad[q * a.n + row] = p;
+          if (tq.act[j] && row < a.n) {
+            a.grad[q * a.n + row] = p;
+            if (a.beta) {
+              // control (y - A p) / t = (u - p) / tau at the fixed point
+              const float tau = tq.tau[j];
+              const float bt = tau > 0.f ? (uo[e] - p) / tau : 0.f;
+              a.beta[q * a.n + row] = bt;
+              if (a.xfin) a.xfin[q * a.n + row] = a.x[q * a.n + row] - tau * a.lam * bt;
+            }
+          }
         }
       }
     }
@@ -358,7 +370,8 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
 }  // namespace
 
 hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                            float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
+                            float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
+                            float* xfin) {
   hopf_status s = dense_init(h, w, x, t, stream);
   if (s != HOPF_OK) return s;
   SimtArgs a;
@@ -375,6 +388,9 @@ hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const flo
   a.tol = (float)h->tol;
   a.ws = w;
   a.grad = grad;
+  a.x = x;
+  a.beta = beta;
+  a.xfin = xfin;
   int per_sm = 0;
   HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_simt, NT, 0));
   if (per_sm < 1) return fail(HOPF_ECUDA, "dense FP32 solver: kernel does not fit on an SM");

@@ -96,6 +96,8 @@ struct TcArgs {
   int* err;
   const float* w;
   float* grad;
+  float* beta;        // optional: control in dH(grad phi) [B][n]
+  float* xfin;        // optional: terminal point x - t beta [B][n]
   int64_t B, B_pad;
   int n, np, rt, ct, h_kind, max_iter, form, compact;
   float lam, tol;
@@ -855,7 +857,17 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
           const double pd = p;
           f0 = (double)yy * pd - 0.5 * pd * (double)ap;
           f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
-          if (row < a.n) a.grad[q * a.n + row] = p;
+          if (row < a.n) {
+            a.grad[q * a.n + row] = p;
+            if (a.beta) {
+              // control (y - A p) / t = (u - p) / tau at the fixed point, an
+              // element of dH(p) by the prox (u - prox(u) in tau dH)
+              const float tau = S.qtau[j];
+              const float bt = tau > 0.f ? (uu - p) / tau : 0.f;
+              a.beta[q * a.n + row] = bt;
+              if (a.xfin) a.xfin[q * a.n + row] = a.x[q * a.n + row] - tau * a.lam * bt;
+            }
+          }
         }
         f0 = warp_sum(f0);
         f1 = warp_sum(f1);
@@ -1201,7 +1213,8 @@ hopf_status dense_tc_prepare() {
 }
 
 hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
+                          float* xfin) {
   using namespace tc;
   const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : FORM_BF16;
   if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
@@ -1258,6 +1271,8 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.err = w.err;
   a.w = h->d_wf;
   a.grad = grad;
+  a.beta = beta;
+  a.xfin = xfin;
   a.B = w.B;
   a.B_pad = w.B_pad;
   a.n = h->n;

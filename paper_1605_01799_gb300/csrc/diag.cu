@@ -255,6 +255,8 @@ struct DiagEvalArgs {
   T* dphidt;
   int32_t* iters;
   uint8_t* qstatus;
+  T* beta;  // optional: control in dH(grad phi), [batch][n]
+  T* xfin;  // optional: terminal point x - t beta, [batch][n]
 };
 
 template <int G>
@@ -279,6 +281,20 @@ __global__ void __launch_bounds__(block_of<G>()) k_diag_eval(DiagEvalArgs<T> A) 
   for (int j = 0; j < VPT; ++j) {
     const int i = l + G * j;
     if (i < A.n) A.grad[q * A.n + i] = Q.d[j];
+  }
+  if (A.beta) {
+    // at the fixed point lambda b = y - A d, so the control
+    // (y - A p) / t = b / tau lies in dH(p) (b = u - prox(u) in tau dH)
+    const T tau = tq / A.P.lam;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const int i = l + G * j;
+      if (i < A.n) {
+        const T bt = tau > T(0) ? Q.b[j] / tau : T(0);
+        A.beta[q * A.n + i] = bt;
+        if (A.xfin) A.xfin[q * A.n + i] = A.x[q * A.n + i] - tq * bt;
+      }
+    }
   }
   if (l == 0) {
     A.phi[q] = phi;
@@ -329,8 +345,9 @@ DiagPart<double> part_of<double>(hopf_handle h) {
 }
 
 hopf_status diag_eval_f32(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream) {
-  DiagEvalArgs<float> a{part_of<float>(h), h->n, batch, x, t, phi, grad, dphidt, iters, qstatus};
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
+                          float* xfin) {
+  DiagEvalArgs<float> a{part_of<float>(h), h->n, batch, x, t, phi, grad, dphidt, iters, qstatus, beta, xfin};
   if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
   hopf_status s = dispatch_eval(a, stream);
   if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
@@ -363,6 +380,7 @@ struct UnionArgs {
   int32_t* it_parts;    // [batch][K]
   uint8_t* st_parts;    // [batch][K]
   unsigned* best;       // [batch] smallest root found so far (float bits; closest point)
+  int maximize;         // phi pass: keep the largest phi_i (maximum over Hamiltonians)
   float s_tol;
   int max_newton;
   // outputs
@@ -406,11 +424,14 @@ template <int G, int VPT>
 __global__ void __launch_bounds__(block_of<G>()) k_union_pick(UnionArgs U) {
   const int64_t q = group_index<G>();
   if (q >= U.batch) return;
+  // the minimum over initial data (unions) or the maximum over Hamiltonians;
+  // ties go to the smallest index
   int best = 0;
   double bv = U.phi_parts[q * U.K];
   for (int i = 1; i < U.K; ++i) {
     const double v = U.phi_parts[q * U.K + i];
-    if (v < bv || (isnan(bv) && !isnan(v))) {
+    const bool better = U.maximize ? v > bv : v < bv;
+    if (better || (isnan(bv) && !isnan(v))) {
       bv = v;
       best = i;
     }
@@ -584,10 +605,11 @@ static hopf_status dispatch_union(UnionArgs& U, bool closest, cudaStream_t s) {
 
 hopf_status union_eval(const hopf_handle* parts, int K, int64_t batch, const float* x, const float* t, double* phi,
                        float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus, void* ws, size_t,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, bool maximize) {
   UnionArgs U{};
   hopf_status s = carve_union(parts, K, batch, ws, &U);
   if (s != HOPF_OK) return s;
+  U.maximize = maximize ? 1 : 0;
   U.x = x;
   U.t = t;
   U.phi = phi;

@@ -256,6 +256,24 @@ hopf_status hopf_eval(hopf_handle h, int64_t batch, const float* x, const float*
   return dense_eval_tc(h, w, x, t, phi, grad, dphidt, iters, qstatus, stream);
 }
 
+hopf_status hopf_eval_control(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
+                              float* dphidt, int32_t* iters, uint8_t* qstatus, float* beta, float* x_final,
+                              void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_eval(h, batch, x, t, phi, grad, workspace, ws_bytes);
+  if (s != HOPF_OK || batch == 0) return s;
+  if (!beta) return fail(HOPF_EINVAL, "hopf_eval_control: null beta");
+  if (h->precision == HOPF_P_FP64) return fail(HOPF_EUNSUPPORTED, "hopf_eval_control: FP32-output handles only");
+  if (h->a_kind == HOPF_A_DIAG)
+    return diag_eval_f32(h, batch, x, t, phi, grad, dphidt, iters, qstatus, stream, beta, x_final);
+  DenseWs w;
+  s = dense_carve(h, batch, workspace, ws_bytes, &w);
+  if (s != HOPF_OK) return s;
+  if (h->precision == HOPF_P_FP32)
+    return dense_eval_simt(h, w, x, t, phi, grad, dphidt, iters, qstatus, stream, beta, x_final);
+  return dense_eval_tc(h, w, x, t, phi, grad, dphidt, iters, qstatus, stream, beta, x_final);
+}
+
 hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
                           double* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,
                           cudaStream_t stream) {
@@ -267,13 +285,13 @@ hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const d
   return diag_eval_f64(h, batch, x, t, phi, grad, dphidt, iters, qstatus, stream);
 }
 
-static hopf_status check_parts(const hopf_handle* parts, int32_t K, bool need_l2) {
+static hopf_status check_parts(const hopf_handle* parts, int32_t K, bool need_l2, bool same_h = true) {
   if (!parts || K < 1) return fail(HOPF_EINVAL, "hopf_union: need K >= 1 parts");
   for (int i = 0; i < K; ++i) {
     if (!parts[i]) return fail(HOPF_EINVAL, "hopf_union: null part");
     if (parts[i]->a_kind != HOPF_A_DIAG || parts[i]->precision != HOPF_P_FP32)
       return fail(HOPF_EUNSUPPORTED, "hopf_union: parts must be diagonal FP32 handles");
-    if (parts[i]->n != parts[0]->n || parts[i]->h_kind != parts[0]->h_kind)
+    if (parts[i]->n != parts[0]->n || (same_h && parts[i]->h_kind != parts[0]->h_kind))
       return fail(HOPF_EINVAL, "hopf_union: parts must share n and h_kind");
     if (need_l2 && parts[i]->h_kind != HOPF_H_L2)
       return fail(HOPF_EINVAL, "hopf_union_closest: parts must use H = l2");
@@ -283,7 +301,7 @@ static hopf_status check_parts(const hopf_handle* parts, int32_t K, bool need_l2
 
 hopf_status hopf_union_workspace_size(const hopf_handle* parts, int32_t K, int64_t batch, size_t* bytes) {
   set_error("");
-  hopf_status s = check_parts(parts, K, false);
+  hopf_status s = check_parts(parts, K, false, false);  // (the size does not depend on H)
   if (s != HOPF_OK) return s;
   if (!bytes || batch < 0) return fail(HOPF_EINVAL, "hopf_union_workspace_size: bad argument");
   *bytes = union_workspace(K, parts[0]->n, batch);
@@ -302,6 +320,20 @@ hopf_status hopf_union_eval(const hopf_handle* parts, int32_t K, int64_t batch, 
   if (!workspace || ws_bytes < union_workspace(K, parts[0]->n, batch))
     return fail(HOPF_EINVAL, "hopf_union_eval: workspace too small");
   return union_eval(parts, K, batch, x, t, phi, grad, argmin, iters, qstatus, workspace, ws_bytes, stream);
+}
+
+hopf_status hopf_maxH_eval(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, const float* t,
+                           double* phi, float* grad, int32_t* argmax, int32_t* iters, uint8_t* qstatus,
+                           void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  hopf_status s = check_parts(parts, K, false, false);
+  if (s != HOPF_OK) return s;
+  if (batch < 0) return fail(HOPF_EINVAL, "hopf_maxH_eval: negative batch");
+  if (batch == 0) return HOPF_OK;
+  if (!x || !t || !phi || !grad || !argmax) return fail(HOPF_EINVAL, "hopf_maxH_eval: null output");
+  if (!workspace || ws_bytes < union_workspace(K, parts[0]->n, batch))
+    return fail(HOPF_EINVAL, "hopf_maxH_eval: workspace too small");
+  return union_eval(parts, K, batch, x, t, phi, grad, argmax, iters, qstatus, workspace, ws_bytes, stream, true);
 }
 
 hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batch, const float* x, float s_tol,

@@ -57,13 +57,15 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
 // ---- diagonal path (diag.cu) ----
 size_t diag_workspace(const hopf_handle h, int64_t batch);
 hopf_status diag_eval_f32(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,
+                          float* xfin = nullptr);
 hopf_status diag_eval_f64(hopf_handle h, int64_t batch, const double* x, const double* t, double* phi, double* grad,
                           double* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
 size_t union_workspace(int K, int n, int64_t batch);
+// maximize: pick the largest phi_i (maximum over Hamiltonians) instead of the smallest
 hopf_status union_eval(const hopf_handle* parts, int K, int64_t batch, const float* x, const float* t, double* phi,
                        float* grad, int32_t* argmin, int32_t* iters, uint8_t* qstatus, void* ws, size_t ws_bytes,
-                       cudaStream_t stream);
+                       cudaStream_t stream, bool maximize = false);
 hopf_status union_closest(const hopf_handle* parts, int K, int64_t batch, const float* x, float s_tol,
                           int max_newton, float* dist, float* closest, int32_t* argmin, int32_t* newton,
                           uint8_t* qstatus, void* ws, size_t ws_bytes, cudaStream_t stream);
@@ -110,11 +112,13 @@ struct DenseWs {
 size_t dense_workspace(const hopf_handle h, int64_t batch);
 hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_bytes, DenseWs* d);
 hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                            float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+                            float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,
+                          float* xfin = nullptr);
 size_t tc_smem_bytes();
 hopf_status dense_tc_prepare();
 hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream);
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,
+                          float* xfin = nullptr);
 
 // ---- backward (backward.cu) ----
 hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,

@@ -118,3 +118,10 @@ def test_batch_rejects_bad_arguments(hg):
                              None) == hg.HOPF_EINVAL
     assert L.hopf_batch_info(None, None, None, None) == hg.HOPF_EINVAL
     L.hopf_batch_destroy(None)
+
+
+def test_control_and_maxH_reject_bad_arguments(hg):
+    L = hg.lib()
+    assert L.hopf_eval_control(None, 4, None, None, None, None, None, None, None, None, None, None, 0,
+                               None) == hg.HOPF_EINVAL
+    assert L.hopf_maxH_eval(None, 0, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
