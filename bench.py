@@ -14,6 +14,7 @@ d phi/dt) per second.
     python bench.py --workload grad        # n = 2048 forward + envelope-theorem backward
     python bench.py --workload control     # the dense workload with the optimal control and terminal point
     python bench.py --workload maxh        # maximum over three Hamiltonians, diagonal J, n = 256
+    python bench.py --workload paper       # the paper's Tables 1 and 4 (H = l1, l2; n = 4..16; FP64)
 
 For N > 1 launch under torch.distributed.run: every rank evaluates its own
 65,536 queries (weak scaling, no collective on the data path); the time is the
@@ -55,7 +56,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=192)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh"])
+    p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh", "paper"])
     return p.parse_args()
 
 
@@ -725,6 +726,102 @@ def run_maxh(args):
         torch.distributed.destroy_process_group()
 
 
+# The paper's single-core timings (s per evaluation, FP64, Intel i5-5300U, one
+# core; Section 4.5, Tables 1 and 4) for the initial data and Hamiltonians
+# this library shares with them.
+PAPER_S_PER_EVAL = {
+    ("l2sq", "l1"): {4: 6.36e-8, 8: 6.98e-8, 12: 8.72e-8, 16: 9.24e-8},
+    ("l2sq", "l2"): {4: 1.20e-7, 8: 1.28e-7, 12: 1.56e-7, 16: 1.50e-7},
+    ("diagD", "l1"): {4: 3.62e-7, 8: 3.83e-7, 12: 4.97e-7, 16: 5.92e-7},
+    ("diagD", "l2"): {4: 5.19e-7, 8: 5.25e-7, 12: 6.62e-7, 16: 6.88e-7},
+}
+
+
+def paper_setup(j, n):
+    """J = 1/2 |x|^2 (A = I) or J = 1/2 <x, D^-1 x> with D_ii = 1 + (i-1)/(n-1)
+    (Section 4.5); c = 0, c0 = 0."""
+    if j == "l2sq":
+        return np.ones(n)
+    return 1.0 + np.arange(n) / (n - 1.0)
+
+
+def paper_queries(n, B, seed):
+    import workloads as wl
+    x = wl.uniform(seed, B * n, -10.0, 10.0).reshape(B, n)
+    t = wl.uniform(seed + 1, B, 0.0, 10.0)
+    return x, t
+
+
+def run_paper(args):
+    """Section 4.5's protocol on the GPU: (x, t) ~ U[-10, 10]^n x U[0, 10],
+    FP64, lambda = 1, the paper's stop rule (the three squared residuals
+    <= 1e-8), 1,000,000 evaluations per configuration; J in {1/2|.|^2,
+    1/2 <., D^-1 .>}, H in {l1, l2}, n in {4, 8, 12, 16}."""
+    import torch
+    import paper_1605_01799_gb300 as hg
+    ws, rank, local, dev = init_device()
+    B = 1_000_000
+    table, total_evals, total_ms, clocks = [], 0, 0.0, None
+    for (j, hname), ref in PAPER_S_PER_EVAL.items():
+        for n in (4, 8, 12, 16):
+            a = paper_setup(j, n)
+            hk = hg.H_L1 if hname == "l1" else hg.H_L2
+            h = hg.Hopf(a, hk, c0=0.0, tol=1e-8, max_iter=10000, precision=hg.P_FP64, stop_rule=hg.STOP_PAPER)
+            x, t = paper_queries(n, B, 9000 + 10 * n + (0 if j == "l2sq" else 5))
+            xd = torch.from_numpy(x).to(dev)
+            td = torch.from_numpy(t).to(dev)
+            st = {}
+
+            def step():
+                st["o"] = h.eval(xd, td, out=st.get("o"))
+
+            for _ in range(max(args.warmup, 1)):
+                step()
+            torch.cuda.synchronize()
+            ms, clk = time_steps(step, args.steps, ws, local)
+            clocks = clk if clocks is None else clocks
+            it = st["o"]["iters"].float().mean().item()
+            ok = float((st["o"]["status"] == 0).float().mean().item())
+            s_eval = ms * 1e-3 / B
+            table.append({"J": j, "H": hname, "n": n, "s_per_eval": s_eval, "evals_per_s": B / (ms * 1e-3),
+                          "paper_s_per_eval_one_core": ref[n], "ratio_vs_paper_core": ref[n] / s_eval,
+                          "iters_mean": it, "status_ok_frac": ok})
+            total_evals += B
+            total_ms += ms
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        m = 200_000
+        x, t = paper_queries(16, m, 9000 + 160)
+        P = oracle.Problem(paper_setup("l2sq", 16), oracle.H_L1, c0=0.0, tol=1e-8, max_iter=10000,
+                           stop_rule=oracle.STOP_PAPER)
+        t0 = time.perf_counter()
+        P.eval(x, t)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "%d queries of the J = 1/2|x|^2, H = l1, n = 16 configuration, FP64 oracle, paper stop "
+                         "rule (%.1f s)" % (m, dt)}
+    if rank == 0:
+        line = {"metric": "Hopf evals/s, the paper's Tables 1 and 4 protocol (H = l1, l2; n = 4..16; FP64)",
+                "value": ws * total_evals / (total_ms * 1e-3), "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / len(table), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "paper_tables_1_4", "batch_per_config": B, "configs": len(table),
+                           "tol_paper_rule": 1e-8,
+                           "l2": "inputs of 32-128 MiB per configuration, comparable to L2; each step recomputes "
+                                 "every solve from x"},
+                "table": table,
+                "roofline": {"bound": "fp64 alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                             "traffic": None,
+                             "note": "one thread per query with the state in registers; FP64 throughput is not in "
+                                     "the measured peaks"},
+                "cpu_baseline": cpu, "e2e": None, "clocks": clocks, "gpu_launches": len(table) * args.steps}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -739,6 +836,8 @@ def main():
         return run_control(args)
     if args.workload == "maxh":
         return run_maxh(args)
+    if args.workload == "paper":
+        return run_paper(args)
     import torch
     import paper_1605_01799_gb300 as hg
 

@@ -124,3 +124,31 @@ def test_nonfinite_input_reports_status(hg):
     torch.cuda.synchronize()
     st = out["status"].cpu().numpy()
     assert st[0] == hg.Q_NONFINITE and st[1] == hg.Q_OK
+
+
+@pytest.mark.parametrize("j", ["l2sq", "diagD"])
+@pytest.mark.parametrize("h_kind", [0, 2])
+@pytest.mark.parametrize("n", [4, 16])
+def test_paper_tables_protocol_fp64(hg, orc, j, h_kind, n):
+    """Section 4.5's protocol (Tables 1 and 4): J = 1/2|x|^2 or 1/2 <x, D^-1 x>
+    with D_ii = 1 + (i-1)/(n-1), (x, t) ~ U[-10, 10]^n x U[0, 10], FP64,
+    lambda = 1, the paper's stop rule at 1e-8.  The GPU and the oracle run the
+    same iterates up to rounding: iteration counts agree (all but a handful
+    that meet the threshold within rounding), and where they agree phi and
+    the gradient agree to FP64 rounding."""
+    import torch
+    B = 2000
+    a = np.ones(n) if j == "l2sq" else 1.0 + np.arange(n) / (n - 1.0)
+    x = wl.uniform(9500 + n, B * n, -10.0, 10.0).reshape(B, n)
+    t = wl.uniform(9600 + n, B, 0.0, 10.0)
+    h = hg.Hopf(a, h_kind, c0=0.0, tol=1e-8, max_iter=10000, precision=hg.P_FP64, stop_rule=hg.STOP_PAPER)
+    out = h.eval(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
+    torch.cuda.synchronize()
+    ref = orc.Problem(a, h_kind, c0=0.0, tol=1e-8, max_iter=10000).eval(x, t)
+    it = out["iters"].cpu().numpy()
+    same = it == ref["iters"]
+    assert same.mean() >= 0.99 and np.abs(it - ref["iters"]).max() <= 1
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy()
+    assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"])))[same].max() <= 1e-10
+    assert np.abs(g - ref["grad"])[same].max() <= 1e-8
