@@ -15,7 +15,10 @@ active-set (KKT) solve, duality-gap bounds, brute-force Hopf-Lax minimisation
 at n = 2, finite differences in x and t, the ellipsoid projection of
 Section 4.3, the control's membership in dH and the Hopf-Lax value
 J(x_T) = phi, and brute-force minimisation at n = 2 of the Hopf formula with
-the Hamiltonian min_i H_i.  Parity unpinned: iteration counts (the paper prints none).
+the Hamiltonian min_i H_i, the new proxes against numerical minimisation of
+their definitions, closed forms through Hopf-Lax projections for J = 1/2|x|^2
+with H = l_inf and sqrt(sum w p^2), and brute-force Hopf objectives at n = 2
+for the non-quadratic initial data (with lambda != 1).  Parity unpinned: iteration counts (the paper prints none).
 """
 import ctypes
 import os
@@ -29,7 +32,9 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "hopf_oracle.c")
 
 A_DIAG, A_DENSE = 0, 1
+J_L1SQ, J_LINFSQ = 2, 3   # J = 1/2 |x - c|_1^2 - c0, 1/2 |x - c|_inf^2 - c0 (Section 4.4)
 H_L1, H_WL1, H_L2 = 0, 1, 2
+H_LINF, H_DNORM = 3, 4    # |p|_inf (Section 4.2), sqrt(sum w_i p_i^2) (Section 4.3)
 STOP_PAPER, STOP_UREL = 0, 1
 
 
@@ -68,6 +73,7 @@ def lib():
         _lib.orc_union_closest.restype = ctypes.c_int
         _lib.orc_maxH_eval.restype = ctypes.c_int
         _lib.orc_control.restype = None
+        _lib.orc_prox.restype = None
         _lib.orc_factor.restype = ctypes.c_int
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_H.restype = ctypes.c_double
@@ -88,10 +94,16 @@ class Problem:
     (vector ``a``) or dense (matrix ``A``); H in {l1, weighted l1, l2}."""
 
     def __init__(self, A, h_kind, w=None, centre=None, c0=0.5, lam=1.0, tol=1e-10,
-                 max_iter=500, stop_rule=STOP_PAPER):
-        A = np.ascontiguousarray(A, dtype=np.float64)
-        self.a_kind = A_DIAG if A.ndim == 1 else A_DENSE
-        self.n = A.shape[0]
+                 max_iter=500, stop_rule=STOP_PAPER, j_kind=None, n=None):
+        """A: the diagonal (1-D) or dense (2-D) matrix of a quadratic J, or None
+        with j_kind = J_L1SQ / J_LINFSQ and the dimension n."""
+        if A is None:
+            assert j_kind in (J_L1SQ, J_LINFSQ) and n is not None
+            self.a_kind, self.n = j_kind, int(n)
+        else:
+            A = np.ascontiguousarray(A, dtype=np.float64)
+            self.a_kind = A_DIAG if A.ndim == 1 else A_DENSE
+            self.n = A.shape[0]
         self.A = A
         self.w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
         self.c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
@@ -204,3 +216,12 @@ def maxH_eval(parts, x, t):
     if rc != 0:
         raise ValueError("oracle: A + lambda I is not SPD")
     return {"phi": phi, "grad": grad, "argmax": am, "iters": it}
+
+
+def prox(h_kind, tau, z, w=None):
+    """prox of tau H at z (the d-update, eq. 3.4(b)) as the oracle computes it."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty_like(z)
+    lib().orc_prox(int(h_kind), len(z), _p(w), ctypes.c_double(tau), _p(z), _p(out))
+    return out

@@ -11,8 +11,11 @@
  * Problem (Section 1, eq. 1.2 / Hopf formula; Section 3.1, eq. 3.3):
  *     phi(x,t) = -min_v { J*(v) + t H(v) - <x,v> }
  * with quadratic initial data J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0, whose
- * Fenchel transform (eq. 1.3) is J*(v) = 1/2 v^T A v + <c,v> + c0, and a
- * positively 1-homogeneous H: l1, weighted l1 (sum w_i |p_i|) or l2.
+ * Fenchel transform (eq. 1.3) is J*(v) = 1/2 v^T A v + <c,v> + c0, or the
+ * initial data of Section 4.4, J = 1/2 |x-c|_1^2 - c0 and 1/2 |x-c|_inf^2 - c0
+ * (J* = 1/2 |v|_inf^2 resp. 1/2 |v|_1^2, plus <c,v> + c0), and a positively
+ * 1-homogeneous H: l1, weighted l1 (sum w_i |p_i|), l2, l_inf (Section 4.2)
+ * or sqrt(sum w_i p_i^2) (Section 4.3, diagonal case).
  *
  * Algorithm: split Bregman, eq. 3.4(a)-(c), with the paper's start
  * v^0 = d^0 = x (read as y = x - c when a centre is present) and b^0 = 0:
@@ -37,8 +40,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_A_DIAG = 0, ORC_A_DENSE = 1 };
-enum { ORC_H_L1 = 0, ORC_H_WL1 = 1, ORC_H_L2 = 2 };
+/* Initial data: quadratic J with diagonal or dense A, or (Section 4.4)
+ * J = 1/2 |x - c|_1^2 - c0 and J = 1/2 |x - c|_inf^2 - c0 (A unused). */
+enum { ORC_A_DIAG = 0, ORC_A_DENSE = 1, ORC_J_L1SQ = 2, ORC_J_LINFSQ = 3 };
+/* Hamiltonians: l1, weighted l1, l2 (Section 1), l_inf (Section 4.2) and
+ * H(p) = sqrt(sum_i d_i p_i^2) with d = w (Section 4.3, diagonal case). */
+enum { ORC_H_L1 = 0, ORC_H_WL1 = 1, ORC_H_L2 = 2, ORC_H_LINF = 3, ORC_H_DNORM = 4 };
 enum { ORC_STOP_PAPER = 0, ORC_STOP_UREL = 1 };
 
 /* One problem instance: A (n diagonal entries or n*n row-major), centre c
@@ -103,20 +110,120 @@ static void chol_solve(int32_t n, const double *L, const double *r, double *v)
     }
 }
 
-/* v-update, eq. 3.4(a): v = (A + lambda I)^{-1} r. */
+/* ---- breakpoint algorithms (Sections 4.2 and 4.4) --------------------- */
+
+static int cmp_desc(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+/* beta with beta = alpha |shrink_1(z, beta)|_1 (Section 4.4, eq.
+ * optimality_beta_l1_2): the breakpoints |z_i| are sorted (decreasing here),
+ * the segment on which g(beta) = alpha |shrink_1(z, beta)|_1 - beta changes
+ * sign is found, and g, affine there, is interpolated:  on the segment where
+ * the k largest |z_i| are active, beta = alpha S_k / (1 + alpha k).
+ * tmp: n doubles. */
+static double l1sq_beta(const double *z, int n, double alpha, double *tmp)
+{
+    for (int i = 0; i < n; ++i) tmp[i] = fabs(z[i]);
+    qsort(tmp, (size_t)n, sizeof(double), cmp_desc);
+    double S = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        S += tmp[k - 1];
+        const double beta = alpha * S / (1.0 + alpha * k);
+        const double lo = k < n ? tmp[k] : 0.0;
+        if (beta >= lo && beta <= tmp[k - 1]) return beta;
+    }
+    return 0.0;  /* z = 0 */
+}
+
+/* mu with |shrink_1(z, mu)|_1 = radius, for |z|_1 > radius (Section 4.2:
+ * projection on the l1 ball by the Lagrange multiplier of eq.
+ * condition_mu_linfty): sorted breakpoints, then on the segment where the k
+ * largest |z_i| are active mu = (S_k - radius) / k.  tmp: n doubles. */
+static double l1ball_mu(const double *z, int n, double radius, double *tmp)
+{
+    for (int i = 0; i < n; ++i) tmp[i] = fabs(z[i]);
+    qsort(tmp, (size_t)n, sizeof(double), cmp_desc);
+    double S = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        S += tmp[k - 1];
+        const double mu = (S - radius) / k;
+        const double lo = k < n ? tmp[k] : 0.0;
+        if (mu >= lo && mu <= tmp[k - 1]) return mu;
+    }
+    return 0.0;
+}
+
+/* mu > 0 with sum_i s2_i z_i^2 / (s2_i + mu)^2 = 1, for a point outside the
+ * ellipsoid {y : sum y_i^2 / s2_i <= 1} (Section 4.3, eq.
+ * lagrange_multiplier_equation_ellipsoid): Newton's method on the derivative
+ * of F(mu) = sum s2_i z_i^2 / (s2_i + mu) + mu from mu_0 = 0, here run to
+ * |mu_{k+1} - mu_k| <= 1e-15 max(1, mu). */
+static double ellipsoid_mu(const double *z, const double *s2, int n)
+{
+    double mu = 0.0;
+    for (int it = 0; it < 500; ++it) {
+        double f1 = 1.0, f2 = 0.0;  /* F'(mu), F''(mu) */
+        for (int i = 0; i < n; ++i) {
+            const double q = s2[i] + mu;
+            f1 -= s2[i] * z[i] * z[i] / (q * q);
+            f2 += 2.0 * s2[i] * z[i] * z[i] / (q * q * q);
+        }
+        if (!(f2 > 0.0)) break;
+        const double dmu = -f1 / f2;
+        mu += dmu;
+        if (fabs(dmu) <= 1e-15 * (mu > 1.0 ? mu : 1.0)) break;
+    }
+    return mu;
+}
+
+/* v-update, eq. 3.4(a): v = argmin J*(v) - <x, v> + lambda/2 |d - v - b|^2
+ * with r = y + lambda (d - b):
+ *   quadratic J: v = (A + lambda I)^{-1} r;
+ *   J = 1/2 |.-c|_inf^2 (J* = 1/2 |.|_1^2 + <c,.> + c0): v = prox of
+ *     (alpha/2)|.|_1^2 at z = r / lambda, alpha = 1 / lambda, i.e.
+ *     shrink_1(z, beta) with beta = alpha |shrink_1(z, beta)|_1 (Section 4.4);
+ *   J = 1/2 |.-c|_1^2 (J* = 1/2 |.|_inf^2 + ...): v = prox of
+ *     (alpha/2)|.|_inf^2 at z, which by Moreau's identity is
+ *     z - prox of (1/(2 alpha))|.|_1^2 at z (Section 4.4 writes the identity
+ *     for alpha = 1). */
 static void v_update(const orc_problem *p, const double *L, const double *r, double *v)
 {
+    const int n = p->n;
     if (p->a_kind == ORC_A_DIAG) {
-        for (int i = 0; i < p->n; ++i) v[i] = r[i] / (p->A[i] + p->lambda);
+        for (int i = 0; i < n; ++i) v[i] = r[i] / (p->A[i] + p->lambda);
+    } else if (p->a_kind == ORC_A_DENSE) {
+        chol_solve(n, L, r, v);
     } else {
-        chol_solve(p->n, L, r, v);
+        const double lam = p->lambda;
+        double *tmp = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        double *z = tmp + n;
+        for (int i = 0; i < n; ++i) z[i] = r[i] / lam;
+        const double alpha = 1.0 / lam;
+        const double beta = l1sq_beta(z, n, p->a_kind == ORC_J_LINFSQ ? alpha : 1.0 / alpha, tmp);
+        for (int i = 0; i < n; ++i) {
+            const double sh = z[i] > beta ? z[i] - beta : (z[i] < -beta ? z[i] + beta : 0.0);
+            v[i] = p->a_kind == ORC_J_LINFSQ ? sh : z[i] - sh;
+        }
+        free(tmp);
     }
 }
 
-/* H(p): l1, weighted l1, or l2 norm (Section 4 list of Hamiltonians). */
+/* H(p): l1, weighted l1, l2, l_inf, or sqrt(sum_i w_i p_i^2) (Section 4.5
+ * list of Hamiltonians). */
 double orc_H(int32_t h_kind, int32_t n, const double *w, const double *q)
 {
     double s = 0.0;
+    if (h_kind == ORC_H_LINF) {
+        for (int i = 0; i < n; ++i) s = fabs(q[i]) > s ? fabs(q[i]) : s;
+        return s;
+    }
+    if (h_kind == ORC_H_DNORM) {
+        for (int i = 0; i < n; ++i) s += w[i] * q[i] * q[i];
+        return sqrt(s);
+    }
     if (h_kind == ORC_H_L2) {
         for (int i = 0; i < n; ++i) s += q[i] * q[i];
         return sqrt(s);
@@ -131,6 +238,42 @@ double orc_H(int32_t h_kind, int32_t n, const double *w, const double *q)
  *   l2: shrink_2(z, tau) = z/|z| max(|z| - tau, 0), and 0 at z = 0. */
 void orc_prox(int32_t h_kind, int32_t n, const double *w, double tau, const double *z, double *out)
 {
+    if (h_kind == ORC_H_LINF || h_kind == ORC_H_DNORM) {
+        /* Moreau's identity: prox of tau |.| = z - projection of z on tau
+         * times the dual unit ball (Sections 4.2 and 4.3): the l1 ball for
+         * l_inf, the ellipsoid {y : sum y_i^2 / w_i <= 1} for sqrt(sum w p^2) */
+        double *tmp = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        if (h_kind == ORC_H_LINF) {
+            double l1 = 0.0;
+            for (int i = 0; i < n; ++i) l1 += fabs(z[i]);
+            if (l1 <= tau) {
+                for (int i = 0; i < n; ++i) out[i] = 0.0;
+            } else {
+                const double mu = l1ball_mu(z, n, tau, tmp);
+                for (int i = 0; i < n; ++i) {
+                    const double pi = z[i] > mu ? z[i] - mu : (z[i] < -mu ? z[i] + mu : 0.0);
+                    out[i] = z[i] - pi;
+                }
+            }
+        } else {
+            double *s2 = tmp;
+            double inside = 0.0;
+            for (int i = 0; i < n; ++i) {
+                s2[i] = tau * tau * w[i];
+                inside += s2[i] > 0.0 ? z[i] * z[i] / s2[i] : (z[i] != 0.0 ? INFINITY : 0.0);
+            }
+            if (tau == 0.0) {
+                for (int i = 0; i < n; ++i) out[i] = z[i];
+            } else if (inside <= 1.0) {
+                for (int i = 0; i < n; ++i) out[i] = 0.0;
+            } else {
+                const double mu = ellipsoid_mu(z, s2, n);
+                for (int i = 0; i < n; ++i) out[i] = z[i] * mu / (s2[i] + mu);
+            }
+        }
+        free(tmp);
+        return;
+    }
     if (h_kind == ORC_H_L2) {
         double nz = 0.0;
         for (int i = 0; i < n; ++i) nz += z[i] * z[i];
@@ -151,10 +294,19 @@ void orc_prox(int32_t h_kind, int32_t n, const double *w, double tau, const doub
     }
 }
 
-/* v^T A v */
+/* 2 J*(v) without the linear part: v^T A v, |v|_inf^2 (J = 1/2|.|_1^2) or
+ * |v|_1^2 (J = 1/2|.|_inf^2) */
 static double quad_A(const orc_problem *p, const double *v)
 {
     double s = 0.0;
+    if (p->a_kind == ORC_J_L1SQ) {
+        for (int i = 0; i < p->n; ++i) s = fabs(v[i]) > s ? fabs(v[i]) : s;
+        return s * s;
+    }
+    if (p->a_kind == ORC_J_LINFSQ) {
+        for (int i = 0; i < p->n; ++i) s += fabs(v[i]);
+        return s * s;
+    }
     if (p->a_kind == ORC_A_DIAG) {
         for (int i = 0; i < p->n; ++i) s += p->A[i] * v[i] * v[i];
     } else {
@@ -477,6 +629,12 @@ void orc_control(const orc_problem *p, int64_t batch, const double *x, const dou
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < batch; ++q) {
         const double *g = grad + q * n;
+        if (p->a_kind != ORC_A_DIAG && p->a_kind != ORC_A_DENSE) {
+            /* J* is not differentiable there: the control is not defined by
+             * this formula */
+            for (int i = 0; i < n; ++i) beta[q * n + i] = x_T[q * n + i] = NAN;
+            continue;
+        }
         for (int i = 0; i < n; ++i) {
             double ap = 0.0;
             if (p->a_kind == ORC_A_DIAG) ap = p->A[i] * g[i];

@@ -185,3 +185,37 @@ def ellipsoid_projection(yv, semi, tol=1e-15, max_iter=200):
         if abs(step) <= tol * max(1.0, mu):
             break
     return d2 * yv / (d2 + mu), mu
+
+
+def l1ball_projection(z, r, iters=200):
+    """Projection on {y : |y|_1 <= r} by bisection on the threshold mu of
+    shrink_1(z, mu) (no sorting): |shrink_1(z, mu)|_1 decreases in mu."""
+    z = np.asarray(z, dtype=np.float64)
+    if np.abs(z).sum() <= r:
+        return z.copy()
+    lo, hi = 0.0, np.abs(z).max()
+    for _ in range(iters):
+        mu = 0.5 * (lo + hi)
+        if np.maximum(np.abs(z) - mu, 0).sum() > r:
+            lo = mu
+        else:
+            hi = mu
+    mu = 0.5 * (lo + hi)
+    return np.sign(z) * np.maximum(np.abs(z) - mu, 0)
+
+
+def min_convex(f, x0, scale):
+    """Minimum of a convex function of a few variables: Nelder-Mead from
+    several starts, refined."""
+    from scipy.optimize import minimize
+    best = None
+    rng = np.random.default_rng(5)
+    starts = [np.asarray(x0, dtype=np.float64)] + [np.asarray(x0) + scale * rng.normal(size=len(x0)) for _ in range(2)]
+    for s in starts:
+        r = minimize(f, s, method="Nelder-Mead", options={"xatol": 1e-12, "fatol": 1e-15, "maxiter": 40000,
+                                                           "maxfev": 80000})
+        r = minimize(f, r.x, method="Nelder-Mead", options={"xatol": 1e-13, "fatol": 1e-16, "maxiter": 40000,
+                                                             "maxfev": 80000})
+        if best is None or r.fun < best.fun:
+            best = r
+    return best.fun, best.x

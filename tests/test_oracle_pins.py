@@ -422,3 +422,85 @@ def test_max_over_hamiltonians_solves_the_min_hamiltonian_pde(orc):
         Hmin = min(float(np.abs(p) @ w), float(np.linalg.norm(p)))
         assert abs(dphidt + Hmin) <= 1e-6 * max(1, Hmin), (trial, dphidt, Hmin)
     assert seen == {0, 1}  # both Hamiltonians win somewhere
+
+
+# ---- P11: the other Hamiltonians and initial data (Sections 4.2-4.4) -------
+
+def _prox_by_definition(f, z):
+    val, u = pins.min_convex(lambda u: f(u) + 0.5 * np.sum((u - z) ** 2), z, 1.0)
+    return u
+
+
+@pytest.mark.parametrize("kind", ["linf", "dnorm"])
+def test_new_prox_against_their_definition(orc, kind):
+    """prox_{tau H}(z) = argmin tau H(u) + 1/2 |u - z|^2, by numerical
+    minimisation in 3-D, for z inside and outside the dual ball."""
+    rng = np.random.default_rng(31)
+    w = np.array([0.5, 1.3, 2.0])
+    for trial in range(8):
+        z = rng.normal(scale=1.5, size=3)
+        tau = rng.uniform(0.1, 2.5)
+        if kind == "linf":
+            H = lambda u: np.abs(u).max()
+            got = orc.prox(orc.H_LINF, tau, z)
+        else:
+            H = lambda u: np.sqrt(np.sum(w * u * u))
+            got = orc.prox(orc.H_DNORM, tau, z, w)
+        ref = _prox_by_definition(lambda u: tau * H(u), z)
+        assert np.abs(got - ref).max() <= 1e-6, (trial, got, ref)
+
+
+def test_l2sq_initial_data_closed_forms_new_H(orc):
+    """J = 1/2 |x|^2: phi(x,t) = min over y in x - tC of J(y) (Hopf-Lax), so
+    phi = 1/2 |x - pi_{tC}(x)|^2 and grad phi = x - pi_{tC}(x), with C the
+    l1 ball (H = l_inf) or the ellipsoid {sum y_i^2 / w_i <= 1}
+    (H = sqrt(sum w p^2)); the projections come from bisection and from the
+    secular-equation projection of Section 4.3 written independently."""
+    n, B = 7, 16
+    x = wl.uniform(9201, B * n, -3.0, 3.0).reshape(B, n)
+    t = wl.uniform(9202, B, 0.1, 2.0)
+    w = wl.uniform(9203, n, 0.5, 2.0)
+    for h in ("linf", "dnorm"):
+        P = orc.Problem(np.ones(n), orc.H_LINF if h == "linf" else orc.H_DNORM, w=w if h == "dnorm" else None,
+                        c0=0.0, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+        r = P.eval(x, t)
+        for q in range(B):
+            if h == "linf":
+                pi = pins.l1ball_projection(x[q], t[q])
+            else:
+                pi = pins.ellipsoid_projection(x[q], t[q] * np.sqrt(w))[0]
+            g = x[q] - pi
+            assert abs(r["phi"][q] - 0.5 * g @ g) <= 1e-9 * max(1, 0.5 * g @ g), (h, q)
+            assert np.abs(r["grad"][q] - g).max() <= 1e-7, (h, q)
+
+
+@pytest.mark.parametrize("j", ["l1sq", "linfsq"])
+@pytest.mark.parametrize("h", ["l1", "l2", "linf"])
+@pytest.mark.parametrize("lam", [1.0, 0.5, 2.5])
+def test_nonquadratic_initial_data_bruteforce_n2(orc, j, h, lam):
+    """J = 1/2 |x|_1^2 or 1/2 |x|_inf^2 (Section 4.4) at n = 2: phi against
+    direct minimisation of the Hopf objective J*(v) + t H(v) - <x, v>
+    (J* = 1/2 |v|_inf^2 resp. 1/2 |v|_1^2), phi(x, 0) = J(x), and
+    d phi/dt = -H(grad phi) by central differences.  phi does not depend on
+    the split Bregman lambda, which scales the prox of J* (the Moreau identity
+    with alpha = 1 / lambda): lambda != 1 checks that scaling."""
+    rng = np.random.default_rng(41)
+    jk = orc.J_L1SQ if j == "l1sq" else orc.J_LINFSQ
+    hk = {"l1": orc.H_L1, "l2": orc.H_L2, "linf": orc.H_LINF}[h]
+    Jstar = (lambda v: 0.5 * np.abs(v).max() ** 2) if j == "l1sq" else (lambda v: 0.5 * np.abs(v).sum() ** 2)
+    J = (lambda z: 0.5 * np.abs(z).sum() ** 2) if j == "l1sq" else (lambda z: 0.5 * np.abs(z).max() ** 2)
+    Hf = {"l1": lambda v: np.abs(v).sum(), "l2": np.linalg.norm, "linf": lambda v: np.abs(v).max()}[h]
+    P = orc.Problem(None, hk, c0=0.0, lam=lam, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL, j_kind=jk,
+                    n=2)
+    for trial in range(4):
+        x = rng.uniform(-3, 3, 2)
+        t = rng.uniform(0.2, 2.0)
+        r = P.eval(x[None], [t])
+        val, v = pins.min_convex(lambda v: Jstar(v) + t * Hf(v) - x @ v, np.zeros(2), 1.0)
+        assert abs(r["phi"][0] + val) <= 1e-7 * max(1, abs(val)), (trial, r["phi"][0], -val)
+        r0 = P.eval(x[None], [0.0])
+        assert abs(r0["phi"][0] - J(x)) <= 1e-9 * max(1, J(x))
+        hh = 1e-5
+        rp, rm = P.eval(x[None], [t + hh]), P.eval(x[None], [t - hh])
+        dphidt = (rp["phi"][0] - rm["phi"][0]) / (2 * hh)
+        assert abs(dphidt + Hf(r["grad"][0])) <= 1e-5 * max(1, abs(dphidt)), (trial, dphidt, Hf(r["grad"][0]))
