@@ -35,6 +35,18 @@ A_DIAG, A_DENSE = 0, 1
 J_L1SQ, J_LINFSQ = 2, 3   # J = 1/2 |x - c|_1^2 - c0, 1/2 |x - c|_inf^2 - c0 (Section 4.4)
 H_L1, H_WL1, H_L2 = 0, 1, 2
 H_LINF, H_DNORM = 3, 4    # |p|_inf (Section 4.2), sqrt(sum w_i p_i^2) (Section 4.3)
+H_ANORM = 5               # sqrt(<p, M p>), M symmetric positive definite (Section 4.3)
+
+
+def anorm_weights(M):
+    """The weight block of H = sqrt(<p, M p>): M, then its eigenvectors and
+    eigenvalues (M = P diag(l) P^T, numpy's symmetric eigensolver as the
+    library step), the layout the C oracle reads."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    l, P = np.linalg.eigh(0.5 * (M + M.T))
+    if not (l > 0).all():
+        raise ValueError("oracle: M is not positive definite")
+    return np.concatenate([M.ravel(), np.ascontiguousarray(P).ravel(), l])
 STOP_PAPER, STOP_UREL = 0, 1
 
 
@@ -91,7 +103,9 @@ def _p(a):
 
 class Problem:
     """One instance: J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0 with A diagonal
-    (vector ``a``) or dense (matrix ``A``); H in {l1, weighted l1, l2}."""
+    (vector ``a``) or dense (matrix ``A``), or a norm J (``j_kind``); H one of
+    l1, weighted l1, l2, l_inf, sqrt(sum w p^2) and sqrt(<p, M p>) (``w`` = M,
+    n x n)."""
 
     def __init__(self, A, h_kind, w=None, centre=None, c0=0.5, lam=1.0, tol=1e-10,
                  max_iter=500, stop_rule=STOP_PAPER, j_kind=None, n=None):
@@ -106,6 +120,8 @@ class Problem:
             self.n = A.shape[0]
         self.A = A
         self.w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        if self.w is not None and int(h_kind) == H_ANORM:
+            self.w = anorm_weights(self.w.reshape(self.n, self.n))
         self.c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
         self.c0, self.h_kind, self.lam, self.tol = float(c0), int(h_kind), float(lam), float(tol)
         self.max_iter, self.stop_rule = int(max_iter), int(stop_rule)
@@ -219,9 +235,12 @@ def maxH_eval(parts, x, t):
 
 
 def prox(h_kind, tau, z, w=None):
-    """prox of tau H at z (the d-update, eq. 3.4(b)) as the oracle computes it."""
+    """prox of tau H at z (the d-update, eq. 3.4(b)) as the oracle computes it
+    (w: the weights, or M for H_ANORM)."""
     z = np.ascontiguousarray(z, dtype=np.float64)
     w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    if w is not None and int(h_kind) == H_ANORM:
+        w = anorm_weights(w.reshape(len(z), len(z)))
     out = np.empty_like(z)
     lib().orc_prox(int(h_kind), len(z), _p(w), ctypes.c_double(tau), _p(z), _p(out))
     return out

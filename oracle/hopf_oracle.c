@@ -14,8 +14,9 @@
  * Fenchel transform (eq. 1.3) is J*(v) = 1/2 v^T A v + <c,v> + c0, or the
  * initial data of Section 4.4, J = 1/2 |x-c|_1^2 - c0 and 1/2 |x-c|_inf^2 - c0
  * (J* = 1/2 |v|_inf^2 resp. 1/2 |v|_1^2, plus <c,v> + c0), and a positively
- * 1-homogeneous H: l1, weighted l1 (sum w_i |p_i|), l2, l_inf (Section 4.2)
- * or sqrt(sum w_i p_i^2) (Section 4.3, diagonal case).
+ * 1-homogeneous H: l1, weighted l1 (sum w_i |p_i|), l2, l_inf (Section 4.2),
+ * sqrt(sum w_i p_i^2) (Section 4.3, diagonal case) or sqrt(<p, M p>) with a
+ * symmetric positive definite M (Section 4.3).
  *
  * Algorithm: split Bregman, eq. 3.4(a)-(c), with the paper's start
  * v^0 = d^0 = x (read as y = x - c when a centre is present) and b^0 = 0:
@@ -43,9 +44,13 @@
 /* Initial data: quadratic J with diagonal or dense A, or (Section 4.4)
  * J = 1/2 |x - c|_1^2 - c0 and J = 1/2 |x - c|_inf^2 - c0 (A unused). */
 enum { ORC_A_DIAG = 0, ORC_A_DENSE = 1, ORC_J_L1SQ = 2, ORC_J_LINFSQ = 3 };
-/* Hamiltonians: l1, weighted l1, l2 (Section 1), l_inf (Section 4.2) and
- * H(p) = sqrt(sum_i d_i p_i^2) with d = w (Section 4.3, diagonal case). */
-enum { ORC_H_L1 = 0, ORC_H_WL1 = 1, ORC_H_L2 = 2, ORC_H_LINF = 3, ORC_H_DNORM = 4 };
+/* Hamiltonians: l1, weighted l1, l2 (Section 1), l_inf (Section 4.2),
+ * H(p) = sqrt(sum_i d_i p_i^2) with d = w (Section 4.3, diagonal case) and
+ * H(p) = sqrt(<p, M p>) (Section 4.3).  For ORC_H_ANORM, w holds
+ * 2 n^2 + n doubles: M (n x n, row-major), then its eigenvectors P (n x n,
+ * row-major, column k the k-th eigenvector) and eigenvalues l (n), with
+ * M = P diag(l) P^T; H reads M, the prox reads P and l. */
+enum { ORC_H_L1 = 0, ORC_H_WL1 = 1, ORC_H_L2 = 2, ORC_H_LINF = 3, ORC_H_DNORM = 4, ORC_H_ANORM = 5 };
 enum { ORC_STOP_PAPER = 0, ORC_STOP_UREL = 1 };
 
 /* One problem instance: A (n diagonal entries or n*n row-major), centre c
@@ -224,6 +229,14 @@ double orc_H(int32_t h_kind, int32_t n, const double *w, const double *q)
         for (int i = 0; i < n; ++i) s += w[i] * q[i] * q[i];
         return sqrt(s);
     }
+    if (h_kind == ORC_H_ANORM) {
+        for (int i = 0; i < n; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < n; ++j) r += w[(int64_t)i * n + j] * q[j];
+            s += q[i] * r;
+        }
+        return sqrt(s > 0.0 ? s : 0.0);
+    }
     if (h_kind == ORC_H_L2) {
         for (int i = 0; i < n; ++i) s += q[i] * q[i];
         return sqrt(s);
@@ -238,6 +251,29 @@ double orc_H(int32_t h_kind, int32_t n, const double *w, const double *q)
  *   l2: shrink_2(z, tau) = z/|z| max(|z| - tau, 0), and 0 at z = 0. */
 void orc_prox(int32_t h_kind, int32_t n, const double *w, double tau, const double *z, double *out)
 {
+    if (h_kind == ORC_H_ANORM) {
+        /* Section 4.3: the dual ball of sqrt(<., M .>) is the ellipsoid
+         * {y : <y, M^-1 y> <= 1}, and with M = P diag(l) P^T the projection
+         * on it is P times the projection of P^T z on the axis-aligned
+         * ellipsoid with weights l; so the prox is the sqrt(sum l p^2) prox
+         * in the eigenbasis, rotated back. */
+        const double *P = w + (int64_t)n * n, *l = w + 2 * (int64_t)n * n;
+        double *zr = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        double *pr = zr + n;
+        for (int k = 0; k < n; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += P[(int64_t)i * n + k] * z[i];
+            zr[k] = s;
+        }
+        orc_prox(ORC_H_DNORM, n, l, tau, zr, pr);
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += P[(int64_t)i * n + k] * pr[k];
+            out[i] = s;
+        }
+        free(zr);
+        return;
+    }
     if (h_kind == ORC_H_LINF || h_kind == ORC_H_DNORM) {
         /* Moreau's identity: prox of tau |.| = z - projection of z on tau
          * times the dual unit ball (Sections 4.2 and 4.3): the l1 ball for

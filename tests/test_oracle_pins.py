@@ -504,3 +504,124 @@ def test_nonquadratic_initial_data_bruteforce_n2(orc, j, h, lam):
         rp, rm = P.eval(x[None], [t + hh]), P.eval(x[None], [t - hh])
         dphidt = (rp["phi"][0] - rm["phi"][0]) / (2 * hh)
         assert abs(dphidt + Hf(r["grad"][0])) <= 1e-5 * max(1, abs(dphidt)), (trial, dphidt, Hf(r["grad"][0]))
+
+
+# ---- P12: H = sqrt(<p, M p>) with a dense SPD M (Section 4.3) ---------------
+
+def _spd(rng, n, lo=0.3, hi=3.0):
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    return Q, (Q * rng.uniform(lo, hi, n)) @ Q.T
+
+
+def _ellipsoid_projection_dense(z, M, r):
+    """Projection of z on {y : <y, M^-1 y> <= r^2} from its optimality
+    condition alone: y = (I + mu M^-1)^-1 z = M (M + mu I)^-1 z with mu >= 0
+    found by bisection on <y, M^-1 y> = r^2 (dense solves, no
+    eigendecomposition)."""
+    Minv = np.linalg.inv(M)
+    if z @ Minv @ z <= r * r:
+        return z.copy()
+    n = len(z)
+    y_of = lambda mu: M @ np.linalg.solve(M + mu * np.eye(n), z)
+    g = lambda mu: y_of(mu) @ Minv @ y_of(mu) - r * r
+    lo, hi = 0.0, 1.0
+    while g(hi) > 0:
+        hi *= 2
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if g(mid) > 0 else (lo, mid)
+    return y_of(0.5 * (lo + hi))
+
+
+def test_anorm_prox_against_its_definition(orc):
+    """prox_{tau H}(z) = argmin tau sqrt(<u, M u>) + 1/2 |u - z|^2 by numerical
+    minimisation in 3-D, for a non-symmetric-eigenvector M (a transposed or
+    skipped rotation fails), z inside and outside tau times the dual ball."""
+    rng = np.random.default_rng(51)
+    Q, M = _spd(rng, 3)
+    for trial in range(8):
+        z = rng.normal(scale=1.5, size=3)
+        tau = rng.uniform(0.1, 2.5)
+        got = orc.prox(orc.H_ANORM, tau, z, M)
+        ref = _prox_by_definition(lambda u: tau * np.sqrt(max(u @ M @ u, 0.0)), z)
+        assert np.abs(got - ref).max() <= 1e-6, (trial, got, ref)
+    # inside the dual ball the prox is 0
+    z = 0.5 * np.linalg.cholesky(M) @ np.array([0.3, -0.2, 0.1])
+    assert np.abs(orc.prox(orc.H_ANORM, 1.0, z, M)).max() == 0.0
+
+
+def test_anorm_diagonal_M_is_the_dnorm(orc):
+    """M = diag(w): the same phi and gradient as H = sqrt(sum w p^2)."""
+    n, B = 6, 12
+    w = wl.uniform(9301, n, 0.5, 2.0)
+    a = wl.uniform(9302, n, 0.5, 2.0)
+    x = wl.normal(9303, B * n, 2.0).reshape(B, n)
+    t = wl.uniform(9304, B, 0.0, 3.0)
+    kw = dict(c0=0.5, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+    r1 = orc.Problem(a, orc.H_ANORM, w=np.diag(w), **kw).eval(x, t)
+    r2 = orc.Problem(a, orc.H_DNORM, w=w, **kw).eval(x, t)
+    assert np.abs(r1["phi"] - r2["phi"]).max() <= 1e-12 * max(1, np.abs(r2["phi"]).max())
+    assert np.abs(r1["grad"] - r2["grad"]).max() <= 1e-10
+
+
+def test_anorm_l2sq_initial_data_closed_form(orc):
+    """J = 1/2 |x|^2 (A = I): phi = 1/2 |x - pi(x)|^2 and grad phi = x - pi(x)
+    with pi the projection on t times the dual ball {y : <y, M^-1 y> <= 1}
+    (Hopf-Lax), computed by bisection on the multiplier with dense solves."""
+    rng = np.random.default_rng(52)
+    n, B = 5, 10
+    Q, M = _spd(rng, n)
+    x = rng.uniform(-3, 3, (B, n))
+    t = rng.uniform(0.1, 2.0, B)
+    P = orc.Problem(np.ones(n), orc.H_ANORM, w=M, c0=0.0, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    for q in range(B):
+        g = x[q] - _ellipsoid_projection_dense(x[q], M, t[q])
+        assert abs(r["phi"][q] - 0.5 * g @ g) <= 1e-9 * max(1, 0.5 * g @ g), q
+        assert np.abs(r["grad"][q] - g).max() <= 1e-7, q
+
+
+def test_anorm_rotation_invariance(orc):
+    """J = 1/2 |x|^2 is rotation invariant, so with M = Q diag(l) Q^T,
+    phi_M(x) = phi_{diag l}(Q^T x) and grad_M(x) = Q grad_{diag l}(Q^T x)."""
+    rng = np.random.default_rng(53)
+    n, B = 8, 10
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    l = rng.uniform(0.3, 3.0, n)
+    M = (Q * l) @ Q.T
+    x = rng.normal(scale=2.0, size=(B, n))
+    t = rng.uniform(0.0, 3.0, B)
+    kw = dict(c0=0.5, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+    rM = orc.Problem(np.ones(n), orc.H_ANORM, w=M, **kw).eval(x, t)
+    rD = orc.Problem(np.ones(n), orc.H_DNORM, w=l, **kw).eval(x @ Q, t)
+    assert np.abs(rM["phi"] - rD["phi"]).max() <= 1e-10 * max(1, np.abs(rD["phi"]).max())
+    assert np.abs(rM["grad"] - rD["grad"] @ Q.T).max() <= 1e-8
+
+
+@pytest.mark.parametrize("j", ["quad", "l1sq", "linfsq"])
+def test_anorm_bruteforce_n2(orc, j):
+    """n = 2: phi against direct minimisation of J*(v) + t sqrt(<v, M v>) -
+    <x, v> for quadratic and norm initial data, and d phi/dt = -H(grad phi)."""
+    rng = np.random.default_rng(54)
+    Q, M = _spd(rng, 2)
+    a = np.array([0.7, 1.6])
+    Hf = lambda v: np.sqrt(max(v @ M @ v, 0.0))
+    if j == "quad":
+        P = orc.Problem(a, orc.H_ANORM, w=M, c0=0.0, lam=0.5, tol=1e-30, max_iter=200000,
+                        stop_rule=orc.STOP_UREL)
+        Jstar = lambda v: 0.5 * (a * v * v).sum()
+    else:
+        jk = orc.J_L1SQ if j == "l1sq" else orc.J_LINFSQ
+        P = orc.Problem(None, orc.H_ANORM, w=M, c0=0.0, lam=2.5, tol=1e-30, max_iter=200000,
+                        stop_rule=orc.STOP_UREL, j_kind=jk, n=2)
+        Jstar = (lambda v: 0.5 * np.abs(v).max() ** 2) if j == "l1sq" else (lambda v: 0.5 * np.abs(v).sum() ** 2)
+    for trial in range(4):
+        x = rng.uniform(-3, 3, 2)
+        t = rng.uniform(0.2, 2.0)
+        r = P.eval(x[None], [t])
+        val, v = pins.min_convex(lambda v: Jstar(v) + t * Hf(v) - x @ v, np.zeros(2), 1.0)
+        assert abs(r["phi"][0] + val) <= 1e-7 * max(1, abs(val)), (trial, r["phi"][0], -val)
+        hh = 1e-5
+        rp, rm = P.eval(x[None], [t + hh]), P.eval(x[None], [t - hh])
+        dphidt = (rp["phi"][0] - rm["phi"][0]) / (2 * hh)
+        assert abs(dphidt + Hf(r["grad"][0])) <= 1e-5 * max(1, abs(dphidt)), (trial, dphidt)
