@@ -89,6 +89,7 @@ def lib():
         _lib.orc_factor.restype = ctypes.c_int
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_H.restype = ctypes.c_double
+        _lib.orc_l1sq_beta.restype = ctypes.c_double
         _lib.orc_neg_objective.restype = ctypes.c_double
     return _lib
 
@@ -232,6 +233,12 @@ def maxH_eval(parts, x, t):
     if rc != 0:
         raise ValueError("oracle: A + lambda I is not SPD")
     return {"phi": phi, "grad": grad, "argmax": am, "iters": it}
+
+
+def l1sq_beta(z, alpha):
+    """beta = alpha |shrink_1(z, beta)|_1 (Section 4.4) as the oracle finds it."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    return lib().orc_l1sq_beta(len(z), _p(z), ctypes.c_double(alpha))
 
 
 def prox(h_kind, tau, z, w=None):

@@ -127,7 +127,12 @@ static int cmp_desc(const void *a, const void *b)
  * optimality_beta_l1_2): the breakpoints |z_i| are sorted (decreasing here),
  * the segment on which g(beta) = alpha |shrink_1(z, beta)|_1 - beta changes
  * sign is found, and g, affine there, is interpolated:  on the segment where
- * the k largest |z_i| are active, beta = alpha S_k / (1 + alpha k).
+ * the k largest |z_i| are active, beta = alpha S_k / (1 + alpha k).  The
+ * segment is the first k whose value reaches the next breakpoint (beta_k >=
+ * |z|_(k+1)): g is positive at every breakpoint above the root, so for
+ * smaller k the value stays below the next breakpoint.  (A two-sided test
+ * of beta_k against both ends of its segment can reject both segments that
+ * meet at a root lying on a tied breakpoint, by one rounding each.)
  * tmp: n doubles. */
 static double l1sq_beta(const double *z, int n, double alpha, double *tmp)
 {
@@ -137,16 +142,26 @@ static double l1sq_beta(const double *z, int n, double alpha, double *tmp)
     for (int k = 1; k <= n; ++k) {
         S += tmp[k - 1];
         const double beta = alpha * S / (1.0 + alpha * k);
-        const double lo = k < n ? tmp[k] : 0.0;
-        if (beta >= lo && beta <= tmp[k - 1]) return beta;
+        if (k == n || beta >= tmp[k]) return beta;
     }
-    return 0.0;  /* z = 0 */
+    return 0.0;  /* n = 0 */
+}
+
+/* exported for the tests */
+double orc_l1sq_beta(int32_t n, const double *z, double alpha)
+{
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    const double b = l1sq_beta(z, n, alpha, tmp);
+    free(tmp);
+    return b;
 }
 
 /* mu with |shrink_1(z, mu)|_1 = radius, for |z|_1 > radius (Section 4.2:
  * projection on the l1 ball by the Lagrange multiplier of eq.
  * condition_mu_linfty): sorted breakpoints, then on the segment where the k
- * largest |z_i| are active mu = (S_k - radius) / k.  tmp: n doubles. */
+ * largest |z_i| are active mu = (S_k - radius) / k, the segment being the
+ * first k whose value reaches the next breakpoint (as in l1sq_beta).
+ * tmp: n doubles. */
 static double l1ball_mu(const double *z, int n, double radius, double *tmp)
 {
     for (int i = 0; i < n; ++i) tmp[i] = fabs(z[i]);
@@ -155,10 +170,9 @@ static double l1ball_mu(const double *z, int n, double radius, double *tmp)
     for (int k = 1; k <= n; ++k) {
         S += tmp[k - 1];
         const double mu = (S - radius) / k;
-        const double lo = k < n ? tmp[k] : 0.0;
-        if (mu >= lo && mu <= tmp[k - 1]) return mu;
+        if (k == n || mu >= tmp[k]) return mu;
     }
-    return 0.0;
+    return 0.0;  /* n = 0 */
 }
 
 /* mu > 0 with sum_i s2_i z_i^2 / (s2_i + mu)^2 = 1, for a point outside the

@@ -625,3 +625,47 @@ def test_anorm_bruteforce_n2(orc, j):
         rp, rm = P.eval(x[None], [t + hh]), P.eval(x[None], [t - hh])
         dphidt = (rp["phi"][0] - rm["phi"][0]) / (2 * hh)
         assert abs(dphidt + Hf(r["grad"][0])) <= 1e-5 * max(1, abs(dphidt)), (trial, dphidt)
+
+
+# ---- P13: breakpoint root finds at tied breakpoints (Sections 4.2, 4.4) -----
+
+def _tied(rng, m):
+    """|z| with a run of equal breakpoints at m, larger ones above and smaller
+    ones below, random signs."""
+    z = np.concatenate([rng.uniform(m, 3 * m, rng.integers(1, 4)), np.full(rng.integers(2, 6), m),
+                        rng.uniform(0, m, 3)])
+    return z * rng.choice([-1.0, 1.0], len(z))
+
+
+def test_l1ball_projection_root_on_a_tied_breakpoint(orc):
+    """prox of tau |.|_inf = z - projection on the l1 ball of radius tau; with
+    tau chosen so that the multiplier is exactly a tied breakpoint (a case that
+    a two-sided segment test rejects on both sides by rounding and returns 0),
+    against the projection by bisection."""
+    rng = np.random.default_rng(61)
+    for trial in range(300):
+        m = rng.uniform(0.1, 2.0)
+        z = _tied(rng, m)
+        tau = np.sum(np.maximum(np.abs(z) - m, 0))
+        got = orc.prox(orc.H_LINF, tau, z)
+        ref = z - pins.l1ball_projection(z, tau)
+        assert np.abs(got - ref).max() <= 1e-12 * max(1, np.abs(z).max()), (trial, got, ref)
+
+
+def test_l1sq_beta_fixed_point_including_ties(orc):
+    """beta = alpha |shrink_1(z, beta)|_1 to rounding, for random z and for z
+    whose root is exactly a tied breakpoint (alpha = m / sum (|z_i| - m)_+)."""
+    rng = np.random.default_rng(62)
+    for trial in range(300):
+        if trial % 2:
+            m = rng.uniform(0.1, 2.0)
+            z = _tied(rng, m)
+            alpha = m / np.sum(np.maximum(np.abs(z) - m, 0))
+        else:
+            z = rng.normal(size=rng.integers(1, 12))
+            alpha = rng.uniform(0.2, 5.0)
+        b = orc.l1sq_beta(z, alpha)
+        rhs = alpha * np.sum(np.maximum(np.abs(z) - b, 0))
+        assert abs(b - rhs) <= 1e-13 * max(1, abs(b)), (trial, b, rhs)
+        if trial % 2:
+            assert abs(b - m) <= 1e-13 * max(1, m)
