@@ -53,13 +53,25 @@ typedef enum {
   HOPF_EINVAL = 1,        /* bad argument (null pointer, size, t < 0, ...) */
   HOPF_ENOMEM = 2,        /* device allocation failed in hopf_create */
   HOPF_ECUDA = 3,         /* a CUDA runtime or driver call failed */
-  HOPF_ENOTSPD = 4,       /* A + lambda I is not symmetric positive definite */
+  HOPF_ENOTSPD = 4,       /* A + lambda I (or M of HOPF_H_ANORM) is not SPD */
   HOPF_EUNSUPPORTED = 5,  /* valid request this build does not implement */
   HOPF_ETIMEOUT = 6       /* a bounded device-side wait gave up (no hang) */
 } hopf_status;
 
-enum { HOPF_A_DIAG = 0, HOPF_A_DENSE = 1 };
-enum { HOPF_H_L1 = 0, HOPF_H_WL1 = 1, HOPF_H_L2 = 2 };
+/* Initial data J.  Quadratic, J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0, with a
+ * diagonal or dense SPD A; or the norms of Section 4.4 (no A):
+ * HOPF_J_L1SQ J = 1/2 |x-c|_1^2 - c0, HOPF_J_LINFSQ J = 1/2 |x-c|_inf^2 - c0
+ * (both run on the diagonal path: per-query state in registers). */
+enum { HOPF_A_DIAG = 0, HOPF_A_DENSE = 1, HOPF_J_L1SQ = 2, HOPF_J_LINFSQ = 3 };
+/* Hamiltonians: |p|_1, sum w_i |p_i|, |p|_2 (Section 1), |p|_inf (Section
+ * 4.2: prox by Moreau's identity and the projection on the l1 ball),
+ * sqrt(sum w_i p_i^2) (Section 4.3, diagonal D = diag(w): prox by the
+ * projection on an ellipsoid, Newton on its multiplier) and sqrt(<p, M p>)
+ * with M symmetric positive definite (Section 4.3: the same projection in
+ * M's eigenbasis; hopf_create computes M = P diag(l) P^T once, and each
+ * iteration rotates by P^T and back by P).  l_inf, sqrt(sum w p^2) and
+ * sqrt(<p, M p>) need the diagonal path; sqrt(<p, M p>) needs n <= 512. */
+enum { HOPF_H_L1 = 0, HOPF_H_WL1 = 1, HOPF_H_L2 = 2, HOPF_H_LINF = 3, HOPF_H_DNORM = 4, HOPF_H_ANORM = 5 };
 
 /* Arithmetic of the v-update (eq. 3.4(a)).
  *   FP64   diagonal A only; use hopf_eval_f64.
@@ -88,11 +100,15 @@ enum { HOPF_Q_OK = 0, HOPF_Q_NOT_CONVERGED = 1, HOPF_Q_NONFINITE = 2, HOPF_Q_ABO
 /* Problem description for hopf_create (host memory, copied).
  *   n          dimension, 1 <= n <= 8192 (diagonal) or 4096 (dense)
  *   a_kind     HOPF_A_DIAG: A points to n doubles > 0;
- *              HOPF_A_DENSE: A points to n*n doubles, row-major, symmetric
+ *              HOPF_A_DENSE: A points to n*n doubles, row-major, symmetric;
+ *              HOPF_J_L1SQ / HOPF_J_LINFSQ: A ignored (may be NULL)
  *   centre     n doubles, or NULL for c = 0
  *   c0         constant of J
- *   h_kind     HOPF_H_L1 / HOPF_H_WL1 / HOPF_H_L2
- *   w          n doubles > 0 for HOPF_H_WL1, else ignored (may be NULL)
+ *   h_kind     HOPF_H_L1 / HOPF_H_WL1 / HOPF_H_L2 / HOPF_H_LINF / HOPF_H_DNORM /
+ *              HOPF_H_ANORM
+ *   w          n doubles > 0 for HOPF_H_WL1 and HOPF_H_DNORM; for HOPF_H_ANORM
+ *              M, n*n doubles, row-major, symmetric positive definite (else
+ *              HOPF_ENOTSPD); else ignored (may be NULL)
  *   lambda     split Bregman parameter, > 0 (the paper uses 1)
  *   tol        stopping tolerance for stop_rule, > 0
  *   max_iter   cap on split Bregman iterations, >= 1
@@ -196,7 +212,7 @@ hopf_status hopf_union_eval(const hopf_handle* parts, int32_t K, int64_t batch, 
  * stopping when |delta s| <= s_tol * max(1, s) or after max_newton steps, each
  * step one split Bregman solve warm-started from the previous one.  Then
  * dist = min_i s_i and closest = y - s grad psi / |grad psi| for the nearest
- * part (eq. projection_when_s_known).  parts: diagonal, h_kind HOPF_H_L2, same
+ * part (eq. projection_when_s_known).  parts: diagonal quadratic J, h_kind HOPF_H_L2, same
  * n.  Queries must lie outside every set (J_i(x) > 0).
  *   dist [batch] float, closest [batch][n] float (may be NULL), argmin [batch]
  *   int32, newton [batch] int32 Newton steps of the nearest part (may be

@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libhopf_gb300.so")
 # constants of include/hopf.h
 HOPF_OK, HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA, HOPF_ENOTSPD, HOPF_EUNSUPPORTED, HOPF_ETIMEOUT = range(7)
 A_DIAG, A_DENSE = 0, 1
-H_L1, H_WL1, H_L2 = 0, 1, 2
+# initial data without a matrix: J = 1/2|x-c|_1^2 - c0, 1/2|x-c|_inf^2 - c0
+J_QUAD, J_L1SQ, J_LINFSQ = 0, 2, 3
+H_L1, H_WL1, H_L2, H_LINF, H_DNORM, H_ANORM = 0, 1, 2, 3, 4, 5  # H_ANORM: w = M (n x n)
 P_FP64, P_FP32, P_BF16, P_MIXED = 0, 1, 2, 5
 STOP_PAPER, STOP_UREL = 0, 1
 Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
@@ -110,22 +112,35 @@ def version():
     return lib().hopf_version().decode()
 
 
+def _a_kind(A, j_kind, n):
+    """(A as float64 or None, desc a_kind, n) for a quadratic J (A given) or a
+    norm J (j_kind, n given)."""
+    if int(j_kind) != J_QUAD:
+        assert A is None and n is not None, "a norm J takes n and no A"
+        return None, int(j_kind), int(n)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    return A, (A_DIAG if A.ndim == 1 else A_DENSE), A.shape[0]
+
+
 class Hopf:
-    """One problem instance J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0 with A diagonal
-    (1-D ``A``) or dense (2-D ``A``), H in {l1, weighted l1, l2}."""
+    """One problem instance: J(x) = 1/2 (x-c)^T A^{-1} (x-c) - c0 with A
+    diagonal (1-D ``A``) or dense (2-D ``A``), or with ``A=None``,
+    ``j_kind`` J_L1SQ / J_LINFSQ and ``n``, J = 1/2|x-c|_1^2 - c0 or
+    1/2|x-c|_inf^2 - c0; H one of H_L1, H_WL1, H_L2, H_LINF, H_DNORM and
+    H_ANORM (sqrt(<p, M p>), ``w`` = M, n x n)."""
 
     def __init__(self, A, h_kind, w=None, centre=None, c0=0.5, lam=1.0, tol=1e-14, max_iter=1000,
-                 precision=P_FP32, stop_rule=STOP_UREL, stream=None):
+                 precision=P_FP32, stop_rule=STOP_UREL, stream=None, j_kind=J_QUAD, n=None):
         import torch  # noqa: F401  (device context)
-        A = np.ascontiguousarray(A, dtype=np.float64)
-        self.n = A.shape[0]
-        self.a_kind = A_DIAG if A.ndim == 1 else A_DENSE
+        A, self.a_kind, self.n = _a_kind(A, j_kind, n)
+        self.j_kind = int(j_kind)
         self.h_kind, self.precision = int(h_kind), int(precision)
         self._keep = [A]
         wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
         cv = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
         self._keep += [wv, cv]
-        d = hopf_desc(self.n, self.a_kind, A.ctypes.data, None if cv is None else cv.ctypes.data, float(c0),
+        d = hopf_desc(self.n, self.a_kind, None if A is None else A.ctypes.data,
+                      None if cv is None else cv.ctypes.data, float(c0),
                       self.h_kind, None if wv is None else wv.ctypes.data, float(lam), float(tol), int(max_iter),
                       self.precision, int(stop_rule))
         h = ctypes.c_void_p()
@@ -213,7 +228,7 @@ class Hopf:
         gx = torch.empty_like(vstar) if want_x else None
         gt = torch.empty(B, dtype=torch.float32, device=vstar.device) if want_t else None
         gA = None
-        if want_A:
+        if want_A and self.j_kind == J_QUAD:  # a norm J has no matrix
             shape = (self.n, self.n) if self.a_kind == A_DENSE else (self.n,)
             gA = torch.empty(shape, dtype=torch.float32, device=vstar.device)
         _check(lib().hopf_backward(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
@@ -223,28 +238,28 @@ class Hopf:
 
 class HopfBatch:
     """A ragged batch of instances evaluated as one CUDA graph replay.
-    ``instances``: list of dicts with keys A (1-D diagonal or 2-D dense),
-    h_kind and optionally w, centre, c0, lam, tol, max_iter, precision,
-    stop_rule (as for Hopf)."""
+    ``instances``: list of dicts with keys A (1-D diagonal or 2-D dense; or
+    None with j_kind and n), h_kind and optionally w, centre, c0, lam, tol,
+    max_iter, precision, stop_rule (as for Hopf)."""
 
     def __init__(self, instances, stream=None):
         self._keep = []
         descs = (hopf_desc * len(instances))()
         self.ns = []
         for i, d in enumerate(instances):
-            A = np.ascontiguousarray(d["A"], dtype=np.float64)
+            A, a_kind, n = _a_kind(d.get("A"), d.get("j_kind", J_QUAD), d.get("n"))
             w = d.get("w")
             w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
             c = d.get("centre")
             c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
             self._keep += [A, w, c]
-            descs[i] = hopf_desc(A.shape[0], A_DIAG if A.ndim == 1 else A_DENSE, A.ctypes.data,
+            descs[i] = hopf_desc(n, a_kind, None if A is None else A.ctypes.data,
                                  None if c is None else c.ctypes.data, float(d.get("c0", 0.5)), int(d["h_kind"]),
                                  None if w is None else w.ctypes.data, float(d.get("lam", 1.0)),
                                  float(d.get("tol", 1e-13)), int(d.get("max_iter", 1000)),
-                                 int(d.get("precision", P_MIXED if A.ndim == 2 else P_FP32)),
+                                 int(d.get("precision", P_MIXED if a_kind == A_DENSE else P_FP32)),
                                  int(d.get("stop_rule", STOP_UREL)))
-            self.ns.append(A.shape[0])
+            self.ns.append(n)
         h = ctypes.c_void_p()
         _check(lib().hopf_batch_create(descs, len(instances), ctypes.byref(h), _stream(stream)))
         self.handle = h

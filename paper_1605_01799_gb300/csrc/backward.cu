@@ -15,19 +15,38 @@ namespace {
 
 // g_x and g_t: one warp per query.
 __global__ void k_bwd_xt(const float* __restrict__ g, const float* __restrict__ V, const float* __restrict__ w,
-                         int n, int64_t B, int h_kind, float* __restrict__ gx, float* __restrict__ gt) {
+                         const float* __restrict__ P, int n, int64_t B, int h_kind, float* __restrict__ gx,
+                         float* __restrict__ gt) {
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= B) return;
   const float gq = g[q];
-  double h = 0.0;
+  double h = 0.0;  // H(v): sum (l1 kinds), sum of squares (l2 kinds), max (l_inf)
   for (int i = lane; i < n; i += 32) {
     const float v = V[q * n + i];
     if (gx) gx[q * n + i] = gq * v;
-    h += h_kind == H_L2 ? (double)v * v : (double)w[i] * fabs((double)v);
+    const double av = fabs((double)v);
+    if (h_kind == H_L2) h += av * av;
+    else if (h_kind == H_DNORM) h += (double)w[i] * av * av;
+    else if (h_kind == H_LINF) h = av > h ? av : h;
+    else if (h_kind != H_ANORM) h += (double)w[i] * av;
   }
-  h = warp_sum(h);
-  if (lane == 0 && gt) gt[q] = (float)(-(double)gq * (h_kind == H_L2 ? sqrt(h) : h));
+  if (h_kind == H_ANORM) {
+    // sqrt(<v, M v>) = sqrt(sum_k l_k ((P^T v)_k)^2), l the weights
+    for (int k = lane; k < n; k += 32) {
+      double r = 0.0;
+      for (int i = 0; i < n; ++i) r += (double)P[(int64_t)i * n + k] * (double)V[q * n + i];
+      h += (double)w[k] * r * r;
+    }
+  }
+  if (h_kind == H_LINF) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+  } else {
+    h = warp_sum(h);
+  }
+  if (h_kind == H_L2 || h_kind == H_DNORM || h_kind == H_ANORM) h = sqrt(h);
+  if (lane == 0 && gt) gt[q] = (float)(-(double)gq * h);
 }
 
 // Diagonal g_A: column sums over the batch.
@@ -104,8 +123,8 @@ hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const flo
                      float* g_A, cudaStream_t stream) {
   const int n = h->n;
   if (g_x || g_t) {
-    k_bwd_xt<<<(unsigned)((batch * 32 + 255) / 256), 256, 0, stream>>>(g_phi, vstar, h->d_wf, n, batch, h->h_kind,
-                                                                        g_x, g_t);
+    k_bwd_xt<<<(unsigned)((batch * 32 + 255) / 256), 256, 0, stream>>>(g_phi, vstar, h->d_wf, h->d_Pf, n, batch,
+                                                                        h->h_kind, g_x, g_t);
     HOPF_CUDA(cudaGetLastError());
   }
   if (g_A) {

@@ -22,10 +22,14 @@ template <typename T>
 struct DiagPart {
   const T* a;    // [n] diagonal of A
   const T* c;    // [n] centre or null
-  const T* w;    // [n] weights (ones when unweighted)
+  const T* w;    // [n] weights (ones when unweighted); eigenvalues of M for H_ANORM
   double c0;
   T lam, tol;
   int max_iter, stop_rule, h_kind;
+  int jk;        // initial data: J_QUAD (uses a), J_L1SQ, J_LINFSQ
+  const T* P;    // H_ANORM: eigenvectors of M, [n][n] row-major (column k the k-th)
+  const T* PT;   // H_ANORM: their transpose
+  const double* P64;  // H_ANORM: the FP64 eigenvectors (H in the objective)
 };
 
 // Sum of three values over the G threads of a query group.
@@ -60,6 +64,28 @@ struct Group {
         b += s[1][k];
         c += s[2][k];
       }
+    }
+  }
+  // Maximum over the group.
+  __device__ static T max(T a) {
+    if constexpr (G == 1) {
+      return a;
+    } else if constexpr (G == 32) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      return a;
+    } else {
+      __shared__ T sm[G / 32];
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      __syncthreads();
+      if (lane == 0) sm[wid] = a;
+      __syncthreads();
+      a = sm[0];
+#pragma unroll
+      for (int k = 1; k < G / 32; ++k) a = fmax(a, sm[k]);
+      return a;
     }
   }
   // Value of the group's first thread, in every thread of the group.
@@ -123,7 +149,7 @@ struct Query {
       const bool in = i < n;
       const T xi = in ? x[i] : T(0);
       y[j] = in ? xi - (P.c ? P.c[i] : T(0)) : T(0);
-      ia[j] = in ? T(1) / (P.a[i] + P.lam) : T(0);
+      ia[j] = in && P.jk == J_QUAD ? T(1) / (P.a[i] + P.lam) : T(0);
     }
   }
   __device__ T wt(int j) const {
@@ -132,7 +158,7 @@ struct Query {
   }
   __device__ T at(int j) const {
     const int i = group_lane<G>() + G * j;
-    return i < n ? __ldg(a + i) : T(0);
+    return i < n && a ? __ldg(a + i) : T(0);
   }
   // The paper's start: v^0 = d^0 = y, b^0 = 0 (Section 3.1).
   __device__ void cold_start() {
@@ -147,8 +173,11 @@ struct Query {
   // Runs split Bregman at time t from the current (v, d, b); returns the
   // iteration count, sets *conv.  One loop per Hamiltonian family (shrink_1
   // thresholds or the l2 scale) and stop rule, so each keeps only the state
-  // it reads.
+  // it reads.  GEN selects the runtime-kind loop (solve_generic), compiled
+  // into kernels of its own so the common kinds keep their register budget.
+  template <bool GEN>
   __device__ int solve(const DiagPart<T>& P, T t, bool* conv) {
+    if constexpr (GEN) return solve_generic(P, t, conv);
     if (P.h_kind == H_L2) {
       return P.stop_rule == STOP_PAPER ? solve_rule<true, true>(P, t, conv) : solve_rule<true, false>(P, t, conv);
     }
@@ -225,8 +254,247 @@ struct Query {
     return k > P.max_iter ? P.max_iter : k;
   }
 
+  // ---- the initial data and Hamiltonians of Sections 4.2-4.4 ----------
+
+  // beta with beta = alpha |shrink_1(z, beta)|_1 (Section 4.4).  g(beta) =
+  // alpha |shrink_1(z, beta)|_1 - beta is convex, piecewise affine and
+  // decreasing, so Newton's method from beta = 0 rises to the root and is
+  // exact once a step stays on one affine piece (the count of active
+  // coordinates stops changing): at most n + 1 steps, one group reduction of
+  // the active sum and count each.
+  __device__ T l1sq_root(const T z[VPT], T alpha) const {
+    T beta = T(0);
+    T cprev = T(-1);
+    for (int it = 0; it <= n + 1; ++it) {
+      T S = T(0), c = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const T m = fabs(z[j]) - beta;
+        if (m > T(0)) {
+          S += m;
+          c += T(1);
+        }
+      }
+      Group<G, T>::sum2(S, c);
+      const T g = alpha * S - beta;
+      if (!(g > T(0)) || c == cprev) break;
+      cprev = c;
+      beta += g / (alpha * c + T(1));
+    }
+    return beta;
+  }
+
+  // mu with |shrink_1(z, mu)|_1 = r for |z|_1 > r (Section 4.2, eq.
+  // condition_mu_linfty), by the same Newton iteration on the convex,
+  // piecewise affine |shrink_1(z, mu)|_1 - r.
+  __device__ T l1ball_mu(const T z[VPT], T r) const {
+    T mu = T(0);
+    T cprev = T(-1);
+    for (int it = 0; it <= n + 1; ++it) {
+      T S = T(0), c = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const T m = fabs(z[j]) - mu;
+        if (m > T(0)) {
+          S += m;
+          c += T(1);
+        }
+      }
+      Group<G, T>::sum2(S, c);
+      const T h = S - r;
+      if (!(h > T(0)) || !(c > T(0)) || c == cprev) break;
+      cprev = c;
+      mu += h / c;
+    }
+    return mu;
+  }
+
+  // prox of tau H at u for any H kind (eq. 3.4(b)); l_inf and
+  // sqrt(sum w p^2) by Moreau's identity: u minus the projection of u on tau
+  // times the dual unit ball (the l1 ball; the ellipsoid sum y_i^2 / w_i <= 1,
+  // Section 4.3: Newton on its multiplier from 0).
+  __device__ void prox_any(const DiagPart<T>& P, T tau, const T u[VPT], const T wv[VPT], T out[VPT]) const {
+    if (P.h_kind == H_L1 || P.h_kind == H_WL1) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) out[j] = shrink1(u[j], tau * wv[j]);
+    } else if (P.h_kind == H_L2) {
+      T uu = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) uu += u[j] * u[j];
+      const T s2 = shrink2_scale(sqrt(Group<G, T>::sum(uu)), tau);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) out[j] = s2 * u[j];
+    } else if (P.h_kind == H_LINF) {
+      T l1 = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) l1 += fabs(u[j]);
+      l1 = Group<G, T>::sum(l1);
+      if (l1 <= tau) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) out[j] = T(0);
+      } else {
+        const T mu = l1ball_mu(u, tau);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) out[j] = u[j] - shrink1(u[j], mu);  // sign(u) min(|u|, mu)
+      }
+    } else if (P.h_kind == H_DNORM) {
+      dnorm_prox(tau, u, wv, out);
+    } else {  // H_ANORM: the H_DNORM prox in M's eigenbasis (Section 4.3)
+      if constexpr (G <= 32) {
+        T ur[VPT], pr[VPT];
+        matvec_cols(P.P, u, ur);  // P^T u
+        dnorm_prox(tau, ur, wv, pr);
+        matvec_cols(P.PT, pr, out);  // P pr
+      }
+    }
+  }
+
+  // prox of tau sqrt(sum w p^2) at u: u minus the projection of u on the
+  // ellipsoid sum y_i^2 / (tau^2 w_i) <= 1 (Moreau's identity, Section 4.3),
+  // Newton on the multiplier from 0.
+  __device__ void dnorm_prox(T tau, const T u[VPT], const T wv[VPT], T out[VPT]) const {
+    if (!(tau > T(0))) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) out[j] = u[j];
+      return;
+    }
+    T ins = T(0);
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) ins += wv[j] > T(0) ? u[j] * u[j] / (tau * tau * wv[j]) : T(0);
+    ins = Group<G, T>::sum(ins);
+    if (ins <= T(1)) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) out[j] = T(0);
+      return;
+    }
+    const T eps = sizeof(T) == 8 ? T(1e-14) : T(1e-6);
+    T mu = T(0);
+    for (int it = 0; it < 100; ++it) {
+      T f1 = T(0), f2 = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const T s2 = tau * tau * wv[j];
+        const T q = s2 + mu;
+        const T e = q > T(0) ? s2 * u[j] * u[j] / (q * q) : T(0);
+        f1 += e;
+        f2 += q > T(0) ? T(2) * e / q : T(0);
+      }
+      Group<G, T>::sum2(f1, f2);
+      f1 = T(1) - f1;
+      if (!(f2 > T(0))) break;
+      const T dmu = -f1 / f2;
+      mu += dmu;
+      // relative: the root can be far below 1 (small tau^2 w), and the
+      // projection's error follows the relative error of mu
+      if (fabs(dmu) <= eps * mu) break;
+    }
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const T s2 = tau * tau * wv[j];
+      out[j] = s2 + mu > T(0) ? u[j] * mu / (s2 + mu) : T(0);
+    }
+  }
+
+  // out_r = sum_c C[c n + r] in_c over the query's n coordinates, r and c
+  // laid out like the state (coordinate lane + G j): the thread's own values
+  // for G = 1, warp shuffles for G = 32.  Reads of C are coalesced along r.
+  template <typename C_T = T, typename A = T>
+  __device__ void matvec_cols(const C_T* __restrict__ C, const T in[VPT], A out[VPT]) const {
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) out[j] = A(0);
+    if constexpr (G == 1) {
+#pragma unroll
+      for (int c = 0; c < VPT; ++c) {
+        if (c < n) {
+#pragma unroll
+          for (int j = 0; j < VPT; ++j)
+            if (j < n) out[j] += (A)__ldg(C + c * n + j) * (A)in[c];
+        }
+      }
+    } else if constexpr (G == 32) {
+      const int lane = threadIdx.x & 31;
+#pragma unroll
+      for (int jc = 0; jc < VPT; ++jc) {
+        for (int l = 0; l < 32; ++l) {
+          const int c = l + 32 * jc;
+          if (c >= n) break;  // the same for every lane
+          const A v = (A)__shfl_sync(0xffffffffu, in[jc], l);
+#pragma unroll
+          for (int j = 0; j < VPT; ++j) {
+            const int r = lane + 32 * j;
+            if (r < n) out[j] += (A)__ldg(C + (size_t)c * n + r) * v;
+          }
+        }
+      }
+    }
+  }
+
+  // Split Bregman for any initial data and Hamiltonian (runtime kinds).  The
+  // v-update of eq. 3.4(a) for J = 1/2|x-c|_inf^2 is the prox of
+  // (1/(2 lambda)) |.|_1^2 at z = (d - b) + y / lambda: shrink_1(z, beta);
+  // for J = 1/2|x-c|_1^2 it is z minus the prox of (lambda / 2) |.|_1^2 at z
+  // (Moreau's identity with the scale 1 / lambda).
+  __device__ int solve_generic(const DiagPart<T>& P, T t, bool* conv) {
+    const T lam = P.lam, tau = t / P.lam;
+    const bool paper = P.stop_rule == STOP_PAPER;
+    T wv[VPT];
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) wv[j] = wt(j);
+    int k;
+    *conv = false;
+    for (k = 1; k <= P.max_iter; ++k) {
+      T vn[VPT], z[VPT];
+      if (P.jk == J_QUAD) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) vn[j] = (y[j] + lam * (d[j] - b[j])) * ia[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) z[j] = (d[j] - b[j]) + y[j] / lam;
+        const T beta = l1sq_root(z, P.jk == J_LINFSQ ? T(1) / lam : lam);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+          const T sh = shrink1(z[j], beta);
+          vn[j] = P.jk == J_LINFSQ ? sh : z[j] - sh;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) z[j] = vn[j] + b[j];  // u^k = v^k + b^{k-1}
+      T dn[VPT];
+      prox_any(P, tau, z, wv, dn);                        // eq. 3.4(b)
+      T r1 = T(0), r2 = T(0), r3 = T(0);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        if (paper) {
+          r1 += (vn[j] - v[j]) * (vn[j] - v[j]);
+          r2 += (dn[j] - d[j]) * (dn[j] - d[j]);
+          r3 += (dn[j] - vn[j]) * (dn[j] - vn[j]);
+        } else {
+          const T du = z[j] - (d[j] + b[j]);  // u^k - u^{k-1}
+          r1 += du * du;
+          r2 += z[j] * z[j];
+        }
+        b[j] = b[j] + vn[j] - dn[j];  // eq. 3.4(c)
+        d[j] = dn[j];
+        v[j] = vn[j];
+      }
+      Group<G, T>::sum3(r1, r2, r3);
+      if (paper) {
+        if (r1 <= P.tol && r2 <= P.tol && r3 <= P.tol) {
+          *conv = true;
+          break;
+        }
+      } else if (k >= 2 && r1 <= P.tol * (r2 > T(1) ? r2 : T(1))) {
+        *conv = true;
+        break;
+      }
+    }
+    return k > P.max_iter ? P.max_iter : k;
+  }
+
   // phi = <y, d> - 1/2 d^T A d - c0 - t H(d), FP64 accumulation; returns H(d).
+  template <bool GEN>
   __device__ double objective(const DiagPart<T>& P, double t, double* H) {
+    if constexpr (GEN) return objective_generic(P, t, H);
     double s = 0.0, h = 0.0, z = 0.0;
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
@@ -237,6 +505,38 @@ struct Query {
     }
     Group<G, double>::sum3(s, h, z);
     *H = P.h_kind == H_L2 ? sqrt(h) : h;
+    return s - P.c0 - t * (*H);
+  }
+
+  // The same for any kind: J*(d) without <c, d> + c0 is 1/2 d^T A d
+  // (quadratic J), 1/2 |d|_inf^2 (J = 1/2|.|_1^2) or 1/2 |d|_1^2
+  // (J = 1/2|.|_inf^2).
+  __device__ double objective_generic(const DiagPart<T>& P, double t, double* H) {
+    double s = 0.0, h = 0.0, q = 0.0, m = 0.0;
+    if (P.h_kind == H_ANORM) {  // H(d) = sqrt(sum_k l_k ((P^T d)_k)^2), FP64 P and sums
+      if constexpr (G <= 32) {
+        double r[VPT];
+        matvec_cols<double, double>(P.P64, d, r);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) h += (double)wt(j) * r[j] * r[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const double dj = (double)d[j];
+      if (P.jk == J_QUAD) s += (double)y[j] * dj - 0.5 * (double)at(j) * dj * dj;
+      else s += (double)y[j] * dj;
+      if (P.jk == J_LINFSQ) q += fabs(dj);
+      if (P.h_kind == H_L2) h += dj * dj;
+      else if (P.h_kind == H_DNORM) h += (double)wt(j) * dj * dj;
+      else if (P.h_kind == H_L1 || P.h_kind == H_WL1) h += (double)wt(j) * fabs(dj);
+      m = fabs(dj) > m ? fabs(dj) : m;
+    }
+    Group<G, double>::sum3(s, h, q);
+    if (P.jk == J_L1SQ || P.h_kind == H_LINF) m = Group<G, double>::max(m);
+    if (P.jk == J_LINFSQ) s -= 0.5 * q * q;
+    else if (P.jk == J_L1SQ) s -= 0.5 * m * m;
+    *H = P.h_kind == H_L2 || P.h_kind == H_DNORM || P.h_kind == H_ANORM ? sqrt(h) : (P.h_kind == H_LINF ? m : h);
     return s - P.c0 - t * (*H);
   }
 };
@@ -262,7 +562,7 @@ struct DiagEvalArgs {
 template <int G>
 constexpr int block_of() { return G == 1 || G == 32 ? 128 : G; }
 
-template <typename T, int G, int VPT>
+template <typename T, int G, int VPT, bool GEN>
 __global__ void __launch_bounds__(block_of<G>()) k_diag_eval(DiagEvalArgs<T> A) {
   const int64_t q = G == 1 ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
                            : (G == 32 ? ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : (int64_t)blockIdx.x);
@@ -272,9 +572,9 @@ __global__ void __launch_bounds__(block_of<G>()) k_diag_eval(DiagEvalArgs<T> A) 
   Q.cold_start();
   const T tq = A.t[q];
   bool conv;
-  const int k = Q.solve(A.P, tq, &conv);
+  const int k = Q.template solve<GEN>(A.P, tq, &conv);
   double H;
-  const double phi = Q.objective(A.P, (double)tq, &H);
+  const double phi = Q.template objective<GEN>(A.P, (double)tq, &H);
   const int l = group_lane<G>();
   bool finite = isfinite(phi);
 #pragma unroll
@@ -304,15 +604,27 @@ __global__ void __launch_bounds__(block_of<G>()) k_diag_eval(DiagEvalArgs<T> A) 
   }
 }
 
+template <typename T, int G, int VPT, bool GEN>
+static void launch_eval_kind(const DiagEvalArgs<T>& a, cudaStream_t s) {
+  if constexpr (G == 1) {
+    k_diag_eval<T, 1, VPT, GEN><<<(unsigned)((a.batch + 127) / 128), 128, 0, s>>>(a);
+  } else if constexpr (G == 32) {
+    k_diag_eval<T, 32, VPT, GEN><<<(unsigned)((a.batch + 3) / 4), 128, 0, s>>>(a);
+  } else {
+    k_diag_eval<T, G, VPT, GEN><<<(unsigned)a.batch, G, 0, s>>>(a);
+  }
+}
+
+// The H and J kinds that need the runtime-kind loop.
+template <typename T>
+__host__ __device__ inline bool generic_kind(const DiagPart<T>& P) {
+  return P.jk != J_QUAD || P.h_kind == H_LINF || P.h_kind == H_DNORM || P.h_kind == H_ANORM;
+}
+
 template <typename T, int G, int VPT>
 static void launch_eval(const DiagEvalArgs<T>& a, cudaStream_t s) {
-  if constexpr (G == 1) {
-    k_diag_eval<T, 1, VPT><<<(unsigned)((a.batch + 127) / 128), 128, 0, s>>>(a);
-  } else if constexpr (G == 32) {
-    k_diag_eval<T, 32, VPT><<<(unsigned)((a.batch + 3) / 4), 128, 0, s>>>(a);
-  } else {
-    k_diag_eval<T, G, VPT><<<(unsigned)a.batch, G, 0, s>>>(a);
-  }
+  if (generic_kind(a.P)) launch_eval_kind<T, G, VPT, true>(a, s);
+  else launch_eval_kind<T, G, VPT, false>(a, s);
 }
 
 // Pick the group shape from n.
@@ -337,11 +649,12 @@ static DiagPart<T> part_of(hopf_handle h);
 template <>
 DiagPart<float> part_of<float>(hopf_handle h) {
   return DiagPart<float>{h->d_af, h->d_c ? h->d_cf : nullptr, h->d_wf, h->c0, (float)h->lambda, (float)h->tol,
-                         h->max_iter, h->stop_rule, h->h_kind};
+                         h->max_iter, h->stop_rule, h->h_kind, h->j_kind, h->d_Pf, h->d_PTf, h->d_P};
 }
 template <>
 DiagPart<double> part_of<double>(hopf_handle h) {
-  return DiagPart<double>{h->d_A, h->d_c, h->d_w, h->c0, h->lambda, h->tol, h->max_iter, h->stop_rule, h->h_kind};
+  return DiagPart<double>{h->d_A, h->d_c, h->d_w, h->c0,        h->lambda,
+                          h->tol, h->max_iter, h->stop_rule, h->h_kind, h->j_kind, h->d_P, h->d_PT, h->d_P};
 }
 
 hopf_status diag_eval_f32(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
@@ -399,7 +712,7 @@ __device__ __forceinline__ int64_t group_index() {
   else return (int64_t)blockIdx.x;
 }
 
-template <int G, int VPT>
+template <int G, int VPT, bool GEN>
 __global__ void __launch_bounds__(block_of<G>()) k_union_parts(UnionArgs U) {
   const int64_t pair = group_index<G>();
   if (pair >= U.batch * U.K) return;
@@ -410,9 +723,9 @@ __global__ void __launch_bounds__(block_of<G>()) k_union_parts(UnionArgs U) {
   Q.load(P, U.x + q * U.n, U.n);
   Q.cold_start();
   bool conv;
-  const int k = Q.solve(P, U.t[q], &conv);
+  const int k = Q.template solve<GEN>(P, U.t[q], &conv);
   double H;
-  const double phi = Q.objective(P, (double)U.t[q], &H);
+  const double phi = Q.template objective<GEN>(P, (double)U.t[q], &H);
   if (group_lane<G>() == 0) {
     U.phi_parts[pair] = phi;
     U.it_parts[pair] = k;
@@ -420,7 +733,7 @@ __global__ void __launch_bounds__(block_of<G>()) k_union_parts(UnionArgs U) {
   }
 }
 
-template <int G, int VPT>
+template <int G, int VPT, bool GEN>
 __global__ void __launch_bounds__(block_of<G>()) k_union_pick(UnionArgs U) {
   const int64_t q = group_index<G>();
   if (q >= U.batch) return;
@@ -441,7 +754,7 @@ __global__ void __launch_bounds__(block_of<G>()) k_union_pick(UnionArgs U) {
   Q.load(P, U.x + q * U.n, U.n);
   Q.cold_start();
   bool conv;
-  Q.solve(P, U.t[q], &conv);
+  Q.template solve<GEN>(P, U.t[q], &conv);
   const int l = group_lane<G>();
 #pragma unroll
   for (int j = 0; j < VPT; ++j) {
@@ -472,9 +785,9 @@ __global__ void __launch_bounds__(block_of<G>()) k_closest_parts(UnionArgs U) {
   int l;
   for (l = 0; l < U.max_newton; ++l) {
     bool conv;
-    Q.solve(P, (float)s, &conv);
+    Q.template solve<false>(P, (float)s, &conv);
     double H;
-    const double psi = Q.objective(P, s, &H);
+    const double psi = Q.template objective<false>(P, s, &H);
     // |grad psi| = |d| (H = l2 here)
     if (!(H > 0.0) || !isfinite(psi)) {
       finite = isfinite(psi);
@@ -531,7 +844,7 @@ __global__ void __launch_bounds__(block_of<G>()) k_closest_pick(UnionArgs U) {
     Q.load(P, U.x + q * U.n, U.n);
     Q.cold_start();
     bool conv;
-    Q.solve(P, s, &conv);
+    Q.template solve<false>(P, s, &conv);
     float nn = 0.f;
 #pragma unroll
     for (int j = 0; j < VPT; ++j) nn += Q.d[j] * Q.d[j];
@@ -583,9 +896,14 @@ static void launch_union(UnionArgs& U, bool closest, cudaStream_t s) {
   const int64_t pairs = U.batch * U.K;
   const unsigned bx = G == 32 ? 128 : G;
   const int per = G == 32 ? 4 : 1;
-  if (!closest) {
-    k_union_parts<G, VPT><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
-    k_union_pick<G, VPT><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);
+  bool gen = false;
+  for (int i = 0; i < U.K; ++i) gen = gen || generic_kind(U.parts[i]);
+  if (!closest && gen) {
+    k_union_parts<G, VPT, true><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
+    k_union_pick<G, VPT, true><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);
+  } else if (!closest) {
+    k_union_parts<G, VPT, false><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
+    k_union_pick<G, VPT, false><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);
   } else {
     k_closest_parts<G, VPT><<<(unsigned)((pairs + per - 1) / per), bx, 0, s>>>(U);
     k_closest_pick<G, VPT><<<(unsigned)((U.batch + per - 1) / per), bx, 0, s>>>(U);

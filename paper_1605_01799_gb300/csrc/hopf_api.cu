@@ -32,10 +32,64 @@ int sm_count(int device) {
   return v;
 }
 
+// Symmetric eigendecomposition M = P diag(l) P^T by the cyclic Jacobi method
+// (row-by-row sweeps of plane rotations, each zeroing one off-diagonal pair;
+// Golub and Van Loan, Matrix Computations, the cyclic Jacobi algorithm).  P is
+// row-major with the k-th eigenvector in column k.  Returns false when 60
+// sweeps leave the off-diagonal mass above 1e-30 of the total.
+static bool sym_eig(int n, const double* M, std::vector<double>& P, std::vector<double>& l) {
+  std::vector<double> a((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = 0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]);
+  P.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) P[(size_t)i * n + i] = 1.0;
+  bool ok = false;
+  for (int sweep = 0; sweep < 60 && !ok; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = a[(size_t)i * n + j] * a[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) {
+      ok = true;
+      break;
+    }
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        // rotation [c s; -s c] in the (p, q) plane with (J^T A J)_pq = 0
+        const double theta = (a[(size_t)q * n + q] - a[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q of A J
+          const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+          a[(size_t)k * n + p] = c * akp - s * akq;
+          a[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q of J^T (A J)
+          const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+          a[(size_t)p * n + k] = c * apk - s * aqk;
+          a[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // P J
+          const double pkp = P[(size_t)k * n + p], pkq = P[(size_t)k * n + q];
+          P[(size_t)k * n + p] = c * pkp - s * pkq;
+          P[(size_t)k * n + q] = s * pkp + c * pkq;
+        }
+      }
+  }
+  l.resize(n);
+  for (int i = 0; i < n; ++i) l[i] = a[(size_t)i * n + i];
+  return ok;
+}
+
 static void free_handle(hopf_handle h) {
   if (!h) return;
   void* ptrs[] = {h->d_A, h->d_c, h->d_w, h->d_cf, h->d_wf, h->d_af, h->d_M64, h->d_M32, h->d_A32,
-                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf};
+                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf, h->d_P, h->d_PT, h->d_Pf, h->d_PTf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -116,13 +170,23 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
   if (!desc || !out) return fail(HOPF_EINVAL, "hopf_create: null desc or out");
   *out = nullptr;
   const hopf_desc& d = *desc;
-  if (d.a_kind != HOPF_A_DIAG && d.a_kind != HOPF_A_DENSE) return fail(HOPF_EINVAL, "hopf_create: bad a_kind");
-  const int nmax = d.a_kind == HOPF_A_DIAG ? 8192 : 4096;
+  if (d.a_kind != HOPF_A_DIAG && d.a_kind != HOPF_A_DENSE && d.a_kind != HOPF_J_L1SQ && d.a_kind != HOPF_J_LINFSQ)
+    return fail(HOPF_EINVAL, "hopf_create: bad a_kind");
+  const bool jnorm = d.a_kind == HOPF_J_L1SQ || d.a_kind == HOPF_J_LINFSQ;  // no matrix: the diagonal path
+  const int nmax = d.a_kind == HOPF_A_DENSE ? 4096 : 8192;
   if (d.n < 1 || d.n > nmax) return fail(HOPF_EINVAL, "hopf_create: n out of range");
-  if (!d.A) return fail(HOPF_EINVAL, "hopf_create: null A");
-  if (d.h_kind != HOPF_H_L1 && d.h_kind != HOPF_H_WL1 && d.h_kind != HOPF_H_L2)
+  if (!d.A && !jnorm) return fail(HOPF_EINVAL, "hopf_create: null A");
+  if (d.h_kind != HOPF_H_L1 && d.h_kind != HOPF_H_WL1 && d.h_kind != HOPF_H_L2 && d.h_kind != HOPF_H_LINF &&
+      d.h_kind != HOPF_H_DNORM && d.h_kind != HOPF_H_ANORM)
     return fail(HOPF_EINVAL, "hopf_create: bad h_kind");
-  if (d.h_kind == HOPF_H_WL1 && !d.w) return fail(HOPF_EINVAL, "hopf_create: weighted l1 needs w");
+  const bool weighted = d.h_kind == HOPF_H_WL1 || d.h_kind == HOPF_H_DNORM;
+  const bool anorm = d.h_kind == HOPF_H_ANORM;
+  if (weighted && !d.w) return fail(HOPF_EINVAL, "hopf_create: weighted l1 and sqrt(sum w p^2) need w");
+  if (anorm && !d.w) return fail(HOPF_EINVAL, "hopf_create: sqrt(<p, M p>) needs M in w");
+  if (anorm && d.n > 512) return fail(HOPF_EUNSUPPORTED, "hopf_create: sqrt(<p, M p>) needs n <= 512");
+  if (d.a_kind == HOPF_A_DENSE && (d.h_kind == HOPF_H_LINF || d.h_kind == HOPF_H_DNORM || anorm))
+    return fail(HOPF_EUNSUPPORTED,
+                "hopf_create: H = l_inf, sqrt(sum w p^2) and sqrt(<p, M p>) run on the diagonal path only");
   if (!(d.lambda > 0) || !std::isfinite(d.lambda)) return fail(HOPF_EINVAL, "hopf_create: lambda must be > 0");
   if (!(d.tol > 0) || !std::isfinite(d.tol)) return fail(HOPF_EINVAL, "hopf_create: tol must be > 0");
   if (d.max_iter < 1) return fail(HOPF_EINVAL, "hopf_create: max_iter must be >= 1");
@@ -137,16 +201,34 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
     return fail(HOPF_EUNSUPPORTED, "hopf_create: dense A uses the relative u stop rule (HOPF_STOP_UREL)");
   const int n = d.n;
   for (int i = 0; i < n; ++i) {
-    if (d.h_kind == HOPF_H_WL1 && !(d.w[i] > 0)) return fail(HOPF_EINVAL, "hopf_create: weights must be > 0");
+    if (weighted && !(d.w[i] > 0 && std::isfinite(d.w[i]))) return fail(HOPF_EINVAL, "hopf_create: weights must be > 0");
     if (d.centre && !std::isfinite(d.centre[i])) return fail(HOPF_EINVAL, "hopf_create: non-finite centre");
     if (d.a_kind == HOPF_A_DIAG && !(d.A[i] > 0 && std::isfinite(d.A[i])))
       return fail(HOPF_ENOTSPD, "hopf_create: diagonal A must be positive");
   }
 
+  // H = sqrt(<p, M p>): symmetric M, eigendecomposition, positive spectrum
+  std::vector<double> eP, el;
+  if (anorm) {
+    double mx = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) {
+      if (!std::isfinite(d.w[i])) return fail(HOPF_EINVAL, "hopf_create: non-finite M");
+      mx = std::fmax(mx, std::fabs(d.w[i]));
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j)
+        if (std::fabs(d.w[(size_t)i * n + j] - d.w[(size_t)j * n + i]) > 1e-12 * mx)
+          return fail(HOPF_EINVAL, "hopf_create: M must be symmetric");
+    if (!sym_eig(n, d.w, eP, el)) return fail(HOPF_ENOTSPD, "hopf_create: eigendecomposition of M did not converge");
+    for (int i = 0; i < n; ++i)
+      if (!(el[i] > 0.0)) return fail(HOPF_ENOTSPD, "hopf_create: M must be positive definite");
+  }
+
   hopf_handle h = new hopf_handle_s();
   h->n = n;
   h->n_pad = (int)round_up(n, 128);
-  h->a_kind = d.a_kind;
+  h->a_kind = jnorm ? HOPF_A_DIAG : d.a_kind;
+  h->j_kind = jnorm ? d.a_kind : 0;
   h->h_kind = d.h_kind;
   h->precision = d.precision;
   h->stop_rule = d.stop_rule;
@@ -180,8 +262,30 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
 
   const int np = h->n_pad;
   std::vector<double> wv(n, 1.0);
-  if (d.h_kind == HOPF_H_WL1)
+  if (weighted)
     for (int i = 0; i < n; ++i) wv[i] = d.w[i];
+  if (anorm) {  // the eigenvalues serve as the weights of the rotated problem
+    wv = el;
+    std::vector<double> PT((size_t)n * n);
+    std::vector<float> Pf((size_t)n * n), PTf((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        const double v = eP[(size_t)i * n + k];
+        PT[(size_t)k * n + i] = v;
+        Pf[(size_t)i * n + k] = (float)v;
+        PTf[(size_t)k * n + i] = (float)v;
+      }
+    const size_t b64 = sizeof(double) * n * n, b32 = sizeof(float) * n * n;
+    H_ALLOC(h->d_P, b64);
+    H_ALLOC(h->d_PT, b64);
+    H_ALLOC(h->d_Pf, b32);
+    H_ALLOC(h->d_PTf, b32);
+    H_CALL(cudaMemcpyAsync(h->d_P, eP.data(), b64, cudaMemcpyHostToDevice, stream));
+    H_CALL(cudaMemcpyAsync(h->d_PT, PT.data(), b64, cudaMemcpyHostToDevice, stream));
+    H_CALL(cudaMemcpyAsync(h->d_Pf, Pf.data(), b32, cudaMemcpyHostToDevice, stream));
+    H_CALL(cudaMemcpyAsync(h->d_PTf, PTf.data(), b32, cudaMemcpyHostToDevice, stream));
+    H_CALL(cudaStreamSynchronize(stream));  // the host vectors die at the end of this block
+  }
   std::vector<float> wf(np, 1.0f), cf(np, 0.0f);
   for (int i = 0; i < n; ++i) {
     wf[i] = (float)wv[i];
@@ -197,7 +301,9 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
     H_ALLOC(h->d_c, sizeof(double) * n);
     H_CALL(cudaMemcpyAsync(h->d_c, d.centre, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
   }
-  if (d.a_kind == HOPF_A_DIAG) {
+  if (jnorm) {
+    H_CALL(cudaStreamSynchronize(stream));  // no matrix: the data copies only
+  } else if (d.a_kind == HOPF_A_DIAG) {
     H_ALLOC(h->d_A, sizeof(double) * n);
     H_CALL(cudaMemcpyAsync(h->d_A, d.A, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
     std::vector<float> af(np, 1.0f);
@@ -293,8 +399,8 @@ static hopf_status check_parts(const hopf_handle* parts, int32_t K, bool need_l2
       return fail(HOPF_EUNSUPPORTED, "hopf_union: parts must be diagonal FP32 handles");
     if (parts[i]->n != parts[0]->n || (same_h && parts[i]->h_kind != parts[0]->h_kind))
       return fail(HOPF_EINVAL, "hopf_union: parts must share n and h_kind");
-    if (need_l2 && parts[i]->h_kind != HOPF_H_L2)
-      return fail(HOPF_EINVAL, "hopf_union_closest: parts must use H = l2");
+    if (need_l2 && (parts[i]->h_kind != HOPF_H_L2 || parts[i]->j_kind != 0))
+      return fail(HOPF_EINVAL, "hopf_union_closest: parts must use H = l2 and a quadratic J");
   }
   return HOPF_OK;
 }
@@ -367,6 +473,8 @@ hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, cons
                           float* g_t, float* g_A, cudaStream_t stream) {
   set_error("");
   if (!h || batch < 0) return fail(HOPF_EINVAL, "hopf_backward: bad argument");
+  if (g_A && h->j_kind != 0)
+    return fail(HOPF_EUNSUPPORTED, "hopf_backward: g_A needs initial data with a matrix A");
   if (batch == 0) {
     if (g_A) {
       size_t m = h->a_kind == HOPF_A_DENSE ? (size_t)h->n * h->n : (size_t)h->n;

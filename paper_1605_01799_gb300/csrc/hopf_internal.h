@@ -14,6 +14,9 @@ struct hopf_handle_s {
   int a_kind = 0, h_kind = 0, precision = 0, stop_rule = 0, max_iter = 0;
   double c0 = 0, lambda = 1, tol = 0;
   int device = 0, num_sms = 0;
+  // initial data on the diagonal path: 0 quadratic (diagonal A), or
+  // HOPF_J_L1SQ / HOPF_J_LINFSQ (A unused)
+  int j_kind = 0;
   // SMs one cooperative dense launch may occupy (0: all).  A ragged batch sets
   // it to its per-stream share so that the dense solvers running side by side
   // on different streams fit on the GPU together.
@@ -25,6 +28,11 @@ struct hopf_handle_s {
   float* d_cf = nullptr;       // [n_pad] centre as float (zeros when none)
   float* d_wf = nullptr;       // [n_pad] weights as float (padding 1)
   float* d_af = nullptr;       // diagonal A as float [n_pad]
+  // H = sqrt(<p, M p>): M = P diag(l) P^T, l stored as the weights d_w / d_wf
+  double* d_P = nullptr;       // [n][n] row-major, column k the k-th eigenvector
+  double* d_PT = nullptr;      // P^T
+  float* d_Pf = nullptr;       // FP32 copies
+  float* d_PTf = nullptr;
   // dense derived operands, padded to n_pad x n_pad, row-major
   double* d_M64 = nullptr;     // (A + lambda I)^{-1}, FP64
   float* d_M32 = nullptr;      // FP32 copy of M

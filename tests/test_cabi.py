@@ -45,7 +45,7 @@ def test_version(hg):
 
 def _desc(hg, **kw):
     A = kw.pop("A", np.ones(4))
-    d = dict(n=4, a_kind=0, A=A.ctypes.data, centre=None, c0=0.5, h_kind=0, w=None, lam=1.0, tol=1e-10,
+    d = dict(n=4, a_kind=0, A=None if A is None else A.ctypes.data, centre=None, c0=0.5, h_kind=0, w=None, lam=1.0, tol=1e-10,
              max_iter=10, precision=1, stop_rule=0)
     d.update(kw)
     return hg.hopf_desc(**d), A
@@ -82,6 +82,59 @@ def test_unsupported_combinations(hg):
     assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
     d, keep = _desc(hg, A=A, a_kind=1, precision=1, stop_rule=0)
     assert hg.lib().hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+
+
+def test_new_kinds_argument_checks(hg):
+    """l_inf and sqrt(sum w p^2) Hamiltonians and the norm initial data:
+    weights required and positive for sqrt(sum w p^2), l_inf and
+    sqrt(sum w p^2) refused on the dense path, a norm J needs no A but still a
+    valid n."""
+    L = hg.lib()
+    h = ctypes.c_void_p()
+    d, keep = _desc(hg, h_kind=hg.H_DNORM)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+    w = np.array([1.0, 2.0, -1.0, 1.0])
+    d, keep = _desc(hg, h_kind=hg.H_DNORM, w=w.ctypes.data)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+    A = np.eye(4)
+    for hk in (hg.H_LINF, hg.H_DNORM):
+        wv = np.ones(4)
+        d, keep = _desc(hg, A=A, a_kind=hg.A_DENSE, h_kind=hk, w=wv.ctypes.data, precision=hg.P_MIXED,
+                        stop_rule=hg.STOP_UREL)
+        assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+    for jk in (hg.J_L1SQ, hg.J_LINFSQ):
+        d, keep = _desc(hg, a_kind=jk, A=None, n=0)
+        assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+        d, keep = _desc(hg, a_kind=jk, A=None, n=9000)
+        assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+    assert not h.value
+
+
+def test_anorm_argument_checks(hg):
+    """H = sqrt(<p, M p>): M required, symmetric, positive definite (the
+    host eigendecomposition finds a non-positive eigenvalue), n <= 512, and
+    the diagonal path only.  All refused before any device work."""
+    L = hg.lib()
+    h = ctypes.c_void_p()
+    d, keep = _desc(hg, h_kind=hg.H_ANORM)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+    M = np.eye(4)
+    M[0, 1] = 0.5
+    d, keep = _desc(hg, h_kind=hg.H_ANORM, w=M.ctypes.data)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EINVAL
+    M = np.ones((4, 4)) + np.diag([1.0, 1.0, 1.0, -3.9])  # eigenvalue below 0
+    assert np.linalg.eigvalsh(M).min() < 0
+    d, keep = _desc(hg, h_kind=hg.H_ANORM, w=M.ctypes.data)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_ENOTSPD
+    big = np.eye(600)
+    a = np.ones(600)
+    d, keep = _desc(hg, A=a, n=600, h_kind=hg.H_ANORM, w=big.ctypes.data)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+    I4 = np.eye(4)
+    d, keep = _desc(hg, A=np.eye(4), a_kind=hg.A_DENSE, h_kind=hg.H_ANORM, w=I4.ctypes.data,
+                    precision=hg.P_MIXED, stop_rule=hg.STOP_UREL)
+    assert L.hopf_create(ctypes.byref(d), ctypes.byref(h), None) == hg.HOPF_EUNSUPPORTED
+    assert not h.value
 
 
 def test_null_arguments(hg):
@@ -125,3 +178,17 @@ def test_control_and_maxH_reject_bad_arguments(hg):
     assert L.hopf_eval_control(None, 4, None, None, None, None, None, None, None, None, None, None, 0,
                                None) == hg.HOPF_EINVAL
     assert L.hopf_maxH_eval(None, 0, 4, None, None, None, None, None, None, None, None, 0, None) == hg.HOPF_EINVAL
+
+
+def test_figure_grid_and_level_lines():
+    """Host side of the 2-D slices: the paper's grid x_i = -20 + 40 k / 99 in
+    the first two coordinates (the rest 0), and level lines where phi crosses a
+    multiple of the step."""
+    from paper_1605_01799_gb300 import figures as F
+    X = F.grid_points()
+    assert X.shape == (10000, 8) and (X[:, 2:] == 0).all()
+    assert X[0, 0] == -20.0 and X[-1, 0] == 20.0 and abs(X[1, 1] - (-20.0 + 40.0 / 99)) < 1e-12
+    assert (X[:100, 0] == -20.0).all()  # x2 runs fastest
+    phi = np.add.outer(np.arange(10.0), np.zeros(4))  # phi = row index
+    img = F.to_pgm(phi, 5.0)
+    assert (img[4] == 0).all() and (img[3] != 0).all()  # 4 -> 5 crosses a multiple of 5

@@ -1,0 +1,323 @@
+"""The l_inf, sqrt(sum w p^2) and sqrt(<p, M p>) Hamiltonians (Sections
+4.2-4.3) and the
+initial data 1/2|x-c|_1^2 and 1/2|x-c|_inf^2 (Section 4.4) on the GPU
+against the FP64 oracle, at each group shape of the diagonal path (thread,
+warp with 2 and 8 values per lane, CTA), both stop rules, FP64 and FP32.
+
+Bars.
+- FP64 against the oracle run with the same rule and tolerance: the two run
+  the same split Bregman map; they differ only in the rounding of the root
+  finds (Newton on the GPU, sorted breakpoints in the oracle), and the map
+  is non-expansive in u, so on queries whose iteration counts agree the
+  iterates agree to (iterations x 1e-16 x |u|): phi to 1e-10 relative and
+  the gradient to 1e-8 (floor 1).
+- FP32 against the converged oracle: phi to 2e-6 relative (FP32 state, FP64
+  objective) plus three times the error that the same stop rule leaves in
+  the FP64 oracle (the relative u-step rule at 1e-12 stops slowly converging
+  kinds up to ~2e-5 away from the limit; the GPU shares that, it is the rule's
+  error and not the arithmetic's).  For sqrt(<p, M p>) with a norm J the
+  FP32 part grows to 2e-6 n / 32: the two FP32 rotations per iteration put
+  ~n eps_32 of noise on every coordinate of d, and J* of a norm J is not
+  differentiable where the maximiser has zero or tied coordinates, so phi at
+  d moves at first order in that noise.  With J = 1/2|.|_1^2
+  the conjugate 1/2|p|_inf^2 is not strictly convex, the maximiser p need not
+  be unique and split Bregman converges slowly along the flat directions,
+  so there the gradient is checked for validity (the GPU's own objective at
+  its p, which is the phi it reports, attains the oracle's maximum) and for
+  agreement only where the problem is strictly concave (quadratic J or
+  J = 1/2|.|_inf^2 with the l2 or sqrt(sum w p^2) Hamiltonian: 2e-5)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1605_01799_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _cuda(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+J_NAMES = {0: "quad", 2: "l1sq", 3: "linfsq"}
+
+
+def _case(jk, hk, n, B, seed):
+    a = wl.uniform(seed, n, 0.5, 2.0) if jk == 0 else None
+    w = wl.uniform(seed + 1, n, 0.5, 1.5) if hk in (1, 4) else None
+    if hk == 5:  # M = Q diag(s) Q^T, s log-uniform in [0.3, 3]
+        w = wl.spd_matrix(seed + 1, seed + 5, n, 0.3, 3.0)[0]
+    c = wl.normal(seed + 2, n, 1.0)
+    x = wl.normal(seed + 3, B * n, 2.0).reshape(B, n)
+    t = wl.uniform(seed + 4, B, 0.0, 3.0)
+    t[0] = 0.0  # phi(x, 0) = J(x)
+    return a, w, c, x, t
+
+
+def _handle(hg, jk, hk, a, w, c, n, **kw):
+    return hg.Hopf(a, hk, w=w, centre=c, j_kind=jk, n=n, **kw)
+
+
+def _oracle(orc, jk, hk, a, w, c, n, **kw):
+    return orc.Problem(a, hk, w=w, centre=c, j_kind=jk if jk else None, n=n, **kw)
+
+
+KINDS = [(0, 3), (0, 4), (2, 0), (2, 1), (2, 2), (2, 3), (2, 4), (3, 0), (3, 1), (3, 2), (3, 3), (3, 4),
+         (0, 5), (2, 5), (3, 5)]
+
+
+def _skip_anorm(hk, n):
+    if hk == 5 and n > 512:
+        pytest.skip("sqrt(<p, M p>) is implemented for n <= 512")
+
+
+@pytest.mark.parametrize("n", [5, 40, 200, 700])
+@pytest.mark.parametrize("jk,hk", KINDS)
+@pytest.mark.parametrize("rule", [0, 1])
+def test_fp64_same_iterates(hg, orc, jk, hk, n, rule):
+    import torch
+    if jk == 2 and n >= 200:
+        pytest.skip("1/2|x|_1^2 at n >= 200 runs 10^4-10^5 iterations per query in the oracle")
+    _skip_anorm(hk, n)
+    B = 24 if n >= 700 else 64
+    a, w, c, x, t = _case(jk, hk, n, B, 31000 + 7 * n + 100 * jk + 10 * hk + rule)
+    tol, mi = (1e-10, 20000) if rule == 0 else (1e-16, 20000)
+    h = _handle(hg, jk, hk, a, w, c, n, lam=1.0, tol=tol, max_iter=mi, precision=hg.P_FP64, stop_rule=rule)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    ref = _oracle(orc, jk, hk, a, w, c, n, lam=1.0, tol=tol, max_iter=mi, stop_rule=rule).eval(x, t)
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    same = it == ref["iters"]
+    # with 1/2|x|_1^2 the residuals fall slowly for thousands of iterations, so
+    # rounding moves the iteration at which they cross the tolerance
+    assert same.mean() >= (0.5 if jk == 2 else 0.9), (same.mean(), it[:8], ref["iters"][:8])
+    ep = np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+    eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+    assert ep[same].max() <= 1e-10, ep[same].max()
+    assert eg[same].max() <= 1e-8, eg[same].max()
+    # a query that stopped one iteration apart is one tiny step away
+    assert ep.max() <= 1e-7, ep.max()
+    st = out["status"].cpu().numpy()
+    assert np.array_equal(st == hg.Q_OK, ref["converged"] != 0) or (st == hg.Q_OK).mean() >= 0.9
+    dt = out["dphidt"].cpu().numpy()
+    assert np.allclose(dt[same], ref["dphidt"][same], rtol=1e-8, atol=1e-8)
+    assert np.allclose(dt, ref["dphidt"], rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("n", [1, 5, 16, 17, 40, 64, 200, 257, 700])
+@pytest.mark.parametrize("jk,hk", KINDS)
+def test_fp32_against_converged_oracle(hg, orc, jk, hk, n):
+    import torch
+    if jk == 2 and n >= 64:
+        pytest.skip("1/2|x|_1^2 at n >= 64: the converged oracle needs 10^5 iterations per query")
+    _skip_anorm(hk, n)
+    B = 24 if n >= 257 else 64
+    a, w, c, x, t = _case(jk, hk, n, B, 37000 + 7 * n + 100 * jk + 10 * hk)
+    x32, t32 = x.astype(np.float32), t.astype(np.float32)
+    h = _handle(hg, jk, hk, a, w, c, n, lam=1.0, tol=1e-12, max_iter=20000, precision=hg.P_FP32,
+                stop_rule=hg.STOP_UREL)
+    out = h.eval(_cuda(x32), _cuda(t32))
+    torch.cuda.synchronize()
+    P = _oracle(orc, jk, hk, a, w, c, n, lam=1.0, tol=1e-28, max_iter=200000, stop_rule=orc.STOP_UREL)
+    ref = P.eval(x32.astype(np.float64), t32.astype(np.float64))
+    rule = _oracle(orc, jk, hk, a, w, c, n, lam=1.0, tol=1e-12, max_iter=20000, stop_rule=orc.STOP_UREL).eval(
+        x32.astype(np.float64), t32.astype(np.float64))
+    phi = out["phi"].cpu().numpy()
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    fp32 = 2e-6 * (max(1.0, n / 32) if (hk == 5 and jk != 0) else 1.0)
+    bar = fp32 * np.maximum(1, np.abs(ref["phi"])) + 3 * np.abs(rule["phi"] - ref["phi"])
+    assert (np.abs(phi - ref["phi"]) <= bar).all(), np.max(np.abs(phi - ref["phi"]) / bar)
+    # the reported phi is the objective at the reported p: evaluate it in FP64
+    # from the GPU's p with the oracle's J* and H
+    yv = x32.astype(np.float64) - P.c
+    if jk == 0:
+        js = 0.5 * (a * g * g).sum(1)
+    elif jk == 2:
+        js = 0.5 * np.abs(g).max(1) ** 2
+    else:
+        js = 0.5 * np.abs(g).sum(1) ** 2
+    Hg = np.array([P.H(gi) for gi in g])
+    own = (yv * g).sum(1) - js - P.c0 - t32.astype(np.float64) * Hg
+    # (the GPU forms y = x - c and reads A, w in FP32: 1e-6 relative)
+    assert (np.abs(own - phi) <= 1e-6 * np.maximum(1.0, np.abs(phi))).all()
+    strict = jk == 0 or (jk == 3 and hk in (2, 4, 5))
+    if strict:
+        # the stop rule's own gradient error (FP64 oracle, same rule) is added
+        # as for phi: 1/2|x|_inf^2 with the l2-type Hamiltonians converges
+        # slowly although its maximiser is unique
+        gn = np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+        eg = np.linalg.norm(g - ref["grad"], axis=1) / gn
+        er = np.linalg.norm(rule["grad"] - ref["grad"], axis=1) / gn
+        assert (eg <= 2e-5 + 3 * er).all(), np.max(eg / (2e-5 + 3 * er))
+    assert (out["status"].cpu().numpy() != hg.Q_NONFINITE).all()
+
+
+@pytest.mark.parametrize("lam", [0.5, 2.5])
+@pytest.mark.parametrize("jk,hk", [(2, 3), (3, 4), (0, 3), (3, 1), (0, 5)])
+def test_lambda_scaling(hg, orc, jk, hk, lam):
+    """lambda != 1 (the Moreau scale of the norm initial data's v-update and
+    tau = t / lambda in the d-update): FP64 against the oracle, same rule."""
+    import torch
+    n, B = 12, 64
+    a, w, c, x, t = _case(jk, hk, n, B, 41000 + 100 * jk + 10 * hk + int(lam * 10))
+    h = _handle(hg, jk, hk, a, w, c, n, lam=lam, tol=1e-16, max_iter=20000, precision=hg.P_FP64,
+                stop_rule=hg.STOP_UREL)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    ref = _oracle(orc, jk, hk, a, w, c, n, lam=lam, tol=1e-16, max_iter=20000, stop_rule=orc.STOP_UREL).eval(x, t)
+    same = out["iters"].cpu().numpy() == ref["iters"]
+    assert same.mean() >= (0.5 if jk == 2 else 0.9)
+    ep = np.abs(out["phi"].cpu().numpy() - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+    assert ep[same].max() <= 1e-10 and ep.max() <= 1e-7
+
+
+def test_maxH_over_the_new_hamiltonians(hg, orc):
+    """The maximum over Hamiltonians (Section 2.2) with parts l1, l2, l_inf and
+    sqrt(sum w p^2) sharing a quadratic J: phi, argmax and the gradient of the
+    maximising part against the oracle."""
+    import torch
+    n, B = 48, 200
+    a = wl.uniform(43000, n, 0.5, 2.0)
+    c = wl.normal(43001, n, 1.0)
+    wd = wl.uniform(43002, n, 0.03, 0.15)
+    x = wl.normal(43003, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(43004, B, 0.0, 3.0).astype(np.float32)
+    kinds = [(0, None), (2, None), (3, None), (4, wd)]
+    parts = [hg.Hopf(a, hk, w=wv, centre=c, tol=1e-12, max_iter=3000, precision=hg.P_FP32, stop_rule=hg.STOP_UREL)
+             for hk, wv in kinds]
+    out = hg.maxH_eval(parts, _cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    oparts = [orc.Problem(a, hk, w=wv, centre=c, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL)
+              for hk, wv in kinds]
+    ref = orc.maxH_eval(oparts, x.astype(np.float64), t.astype(np.float64))
+    phi = out["phi"].cpu().numpy()
+    ep = np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+    assert ep.max() <= 1e-6
+    am = out["argmax"].cpu().numpy()
+    # argmax agrees wherever the two largest parts are clearly apart
+    each = np.stack([p.eval(x.astype(np.float64), t.astype(np.float64))["phi"] for p in oparts], 1)
+    srt = np.sort(each, 1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-5 * np.maximum(1, np.abs(srt[:, -1]))
+    assert (am[clear] == ref["argmax"][clear]).all()
+    assert len(set(ref["argmax"].tolist())) >= 2  # more than one Hamiltonian wins somewhere
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    eg = np.linalg.norm(g - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
+    assert eg[clear].max() <= 2e-5
+
+
+def test_union_of_norm_initial_data(hg, orc):
+    """Union of the sets {1/2|x - c_i|_inf^2 <= c0} (Section 2.2, min over
+    parts) with H = l_inf: phi and argmin against the oracle."""
+    import torch
+    n, K, B = 24, 5, 160
+    x = wl.normal(44000, B * n, 3.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(44001, B, 0.0, 2.0).astype(np.float32)
+    cs = [wl.normal(44010 + i, n, 2.0) for i in range(K)]
+    parts = [hg.Hopf(None, hg.H_LINF, centre=cs[i], c0=0.5, tol=1e-12, max_iter=5000, precision=hg.P_FP32,
+                     stop_rule=hg.STOP_UREL, j_kind=hg.J_LINFSQ, n=n) for i in range(K)]
+    out = hg.union_eval(parts, _cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    oparts = [orc.Problem(None, orc.H_LINF, centre=cs[i], c0=0.5, tol=1e-28, max_iter=50000,
+                          stop_rule=orc.STOP_UREL, j_kind=orc.J_LINFSQ, n=n) for i in range(K)]
+    ref = orc.union_eval(oparts, x.astype(np.float64), t.astype(np.float64))
+    rparts = [orc.Problem(None, orc.H_LINF, centre=cs[i], c0=0.5, tol=1e-12, max_iter=5000,
+                          stop_rule=orc.STOP_UREL, j_kind=orc.J_LINFSQ, n=n) for i in range(K)]
+    rule = orc.union_eval(rparts, x.astype(np.float64), t.astype(np.float64))
+    phi = out["phi"].cpu().numpy()
+    bar = 2e-6 * np.maximum(1, np.abs(ref["phi"])) + 3 * np.abs(rule["phi"] - ref["phi"])
+    assert (np.abs(phi - ref["phi"]) <= bar).all()
+    each = np.stack([p.eval(x.astype(np.float64), t.astype(np.float64))["phi"] for p in oparts], 1)
+    srt = np.sort(each, 1)
+    clear = srt[:, 1] - srt[:, 0] > 1e-5 * np.maximum(1, np.abs(srt[:, 0]))
+    assert (out["argmin"].cpu().numpy()[clear] == ref["argmin"][clear]).all()
+
+
+@pytest.mark.parametrize("hk", [3, 4, 5])
+def test_control_and_backward_for_the_new_hamiltonians(hg, orc, hk):
+    """Control beta = b / tau in dH(p) and its terminal point against the
+    oracle's (y - A p) / t; backward g_t = -g H(v*) for l_inf and
+    sqrt(sum w p^2)."""
+    import torch
+    n, B = 40, 128
+    a = wl.uniform(45000 + hk, n, 0.5, 2.0)
+    w = wl.uniform(45010 + hk, n, 0.5, 1.5) if hk == 4 else None
+    if hk == 5:
+        w = wl.spd_matrix(45010, 45015, n, 0.3, 3.0)[0]
+    c = wl.normal(45020 + hk, n, 0.5)
+    x = wl.normal(45030 + hk, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(45040 + hk, B, 0.1, 3.0).astype(np.float32)
+    h = hg.Hopf(a, hk, w=w, centre=c, tol=1e-12, max_iter=3000, precision=hg.P_FP32, stop_rule=hg.STOP_UREL)
+    out = h.eval_control(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    g = out["grad"].cpu().numpy().astype(np.float64)
+    beta = out["beta"].cpu().numpy().astype(np.float64)
+    P = orc.Problem(a, hk, w=w, centre=c, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL)
+    ref = P.eval(x.astype(np.float64), t.astype(np.float64))
+    rc = orc.control(P, x.astype(np.float64), t.astype(np.float64), ref["grad"])
+    tau = t.astype(np.float64)
+    bar = 5e-5 / np.minimum(tau, 1.0)
+    assert (np.abs(beta - rc["beta"]).max(1) <= bar).all()
+    # beta in dH(p): <beta, p> = H(p) and H*(beta) <= 1 (the dual-ball test)
+    Hp = np.array([P.H(gi) for gi in g])
+    assert np.allclose((beta * g).sum(1), Hp, rtol=1e-4, atol=1e-4)
+    if hk == 3:
+        assert (np.abs(beta).sum(1) <= 1 + 1e-4).all()
+    elif hk == 4:
+        assert ((beta * beta / w).sum(1) <= 1 + 2e-4).all()
+    else:
+        assert (np.einsum("qi,ij,qj->q", beta, np.linalg.inv(w), beta) <= 1 + 2e-4).all()
+    gphi = wl.normal(45050 + hk, B, 1.0).astype(np.float32)
+    gx, gt, _ = h.backward(_cuda(gphi), out["grad"], want_A=False)
+    torch.cuda.synchronize()
+    ob = orc.backward(n, orc.A_DIAG, hk, w, gphi.astype(np.float64), g, t.astype(np.float64), want_A=False)
+    assert np.allclose(gt.cpu().numpy(), ob["g_t"], rtol=1e-5, atol=1e-5)
+    assert np.allclose(gx.cpu().numpy(), ob["g_x"], rtol=1e-6, atol=1e-6)
+
+
+def test_ragged_batch_with_the_new_kinds(hg, orc):
+    """A ragged batch mixing quadratic and norm initial data and the new
+    Hamiltonians: bit-identical to each instance evaluated alone."""
+    import torch
+    descs, xs, ts, counts = [], [], [], []
+    specs = [(0, 3, 30, 17), (3, 4, 100, 40), (2, 2, 8, 9), (3, 0, 300, 33), (0, 4, 5, 0), (2, 3, 20, 70),
+             (0, 5, 12, 21), (3, 5, 48, 5)]
+    for i, (jk, hk, n, B) in enumerate(specs):
+        a, w, c, x, t = _case(jk, hk, n, max(B, 1), 46000 + 10 * i)
+        x, t = x[:B], t[:B]
+        descs.append({"A": a, "j_kind": jk, "n": n, "h_kind": hk, "w": w, "centre": c, "tol": 1e-12,
+                      "max_iter": 5000, "precision": hg.P_FP32, "stop_rule": hg.STOP_UREL})
+        xs.append(x.astype(np.float32).reshape(-1))
+        ts.append(t.astype(np.float32))
+        counts.append(B)
+    b = hg.HopfBatch(descs)
+    X = _cuda(np.concatenate(xs))
+    T = _cuda(np.concatenate(ts))
+    out = b.eval(counts, X, T)
+    torch.cuda.synchronize()
+    phi = out["phi"].cpu().numpy()
+    grad = out["grad"].cpu().numpy()
+    q = e = 0
+    for d, x, t, B in zip(descs, xs, ts, counts):
+        n = d["n"]
+        if B:
+            h = hg.Hopf(d["A"], d["h_kind"], w=d["w"], centre=d["centre"], tol=d["tol"], max_iter=d["max_iter"],
+                        precision=d["precision"], stop_rule=d["stop_rule"], j_kind=d["j_kind"], n=n)
+            one = h.eval(_cuda(x.reshape(B, n)), _cuda(t))
+            torch.cuda.synchronize()
+            assert np.array_equal(one["phi"].cpu().numpy(), phi[q:q + B])
+            assert np.array_equal(one["grad"].cpu().numpy().reshape(-1), grad[e:e + B * n])
+        q += B
+        e += B * n
+    b.close()
