@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh", "paper"])
+    p.add_argument("--paper-only", default="",
+                   help="--workload paper: only these configurations, J:H:n[,J:H:n...] "
+                        "(J in l2sq, linfsq, l1sq, diagD; H in l1, l2, linf, D, A)")
     return p.parse_args()
 
 
@@ -796,10 +799,13 @@ def run_paper(args):
     import paper_1605_01799_gb300 as hg
     ws, rank, local, dev = init_device()
     table, total_evals, total_ms, clocks = [], 0, 0.0, None
+    only = {tuple(c.split(":")) for c in args.paper_only.split(",") if c}
     for ji, (j, hname) in enumerate(PAPER_S_PER_EVAL):
         ref = PAPER_S_PER_EVAL[(j, hname)]
         B = PAPER_BATCH[j]
         for n in (4, 8, 12, 16):
+            if only and (j, hname, str(n)) not in only:
+                continue
             a, jk = paper_setup(j, n)
             hk, w = paper_hamiltonian(hname, n)
             h = hg.Hopf(a, hk, w=w, c0=0.0, tol=1e-8, max_iter=PAPER_MAX_ITER, precision=hg.P_FP64,

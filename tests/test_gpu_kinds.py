@@ -321,3 +321,57 @@ def test_ragged_batch_with_the_new_kinds(hg, orc):
         q += B
         e += B * n
     b.close()
+
+
+@pytest.mark.parametrize("jk,hk", [(2, 0), (2, 3), (3, 2), (3, 4)])
+def test_control_with_norm_initial_data(hg, jk, hk):
+    """Control and terminal point for J = 1/2|x-c|_1^2 and 1/2|x-c|_inf^2,
+    checked by the two conditions that define them (Section 2): beta lies in
+    dH(p), and the terminal point x_T = x - t beta is the Hopf-Lax minimiser,
+    i.e. p lies in dJ(x_T) (with y = x_T - c: p = |y|_1 sign(y) off the zeros
+    of y and |p_i| <= |y|_1 on them for 1/2|.|_1^2; p supported where |y_i| =
+    |y|_inf, with sign(p_i) = sign(y_i) and |p|_1 = |y|_inf, for
+    1/2|.|_inf^2).  FP32: 2e-3 relative slack on the set-valued tests."""
+    import torch
+    n, B = 12, 96
+    a, w, c, x, t = _case(jk, hk, n, B, 47000 + 10 * jk + hk)
+    t = np.maximum(t, 0.2)
+    x32, t32 = x.astype(np.float32), t.astype(np.float32)
+    h = _handle(hg, jk, hk, a, w, c, n, lam=1.0, tol=1e-14, max_iter=20000, precision=hg.P_FP32,
+                stop_rule=hg.STOP_UREL)
+    out = h.eval_control(_cuda(x32), _cuda(t32))
+    torch.cuda.synchronize()
+    p = out["grad"].cpu().numpy().astype(np.float64)
+    beta = out["beta"].cpu().numpy().astype(np.float64)
+    xT = out["x_final"].cpu().numpy().astype(np.float64)
+    assert np.allclose(xT, x32 - t32[:, None] * beta, atol=1e-5)
+    # beta in dH(p)
+    if hk == 0:
+        Hp = np.abs(p).sum(1)
+        assert (np.abs(beta).max(1) <= 1 + 2e-3).all()
+    elif hk == 2:
+        Hp = np.linalg.norm(p, axis=1)
+        assert (np.linalg.norm(beta, axis=1) <= 1 + 2e-3).all()
+    elif hk == 3:
+        Hp = np.abs(p).max(1)
+        assert (np.abs(beta).sum(1) <= 1 + 2e-3).all()
+    else:
+        Hp = np.sqrt((w * p * p).sum(1))
+        assert ((beta * beta / w).sum(1) <= 1 + 2e-3).all()
+    assert np.allclose((beta * p).sum(1), Hp, rtol=2e-3, atol=2e-3)
+    # p in dJ(x_T)
+    y = xT - c
+    scale = np.maximum(1.0, np.abs(y).max(1))
+    for q in range(B):
+        yq, pq = y[q], p[q]
+        if jk == 2:
+            l1 = np.abs(yq).sum()
+            off = np.abs(yq) > 2e-3 * scale[q]
+            assert np.allclose(pq[off], l1 * np.sign(yq[off]), rtol=2e-3, atol=2e-3 * scale[q]), q
+            assert (np.abs(pq[~off]) <= l1 * (1 + 2e-3) + 2e-3).all(), q
+        else:
+            li = np.abs(yq).max()
+            top = np.abs(yq) >= li - 2e-3 * scale[q]
+            assert (np.abs(pq[~top]) <= 2e-3 * scale[q]).all(), q
+            assert (pq[top] * np.sign(yq[top]) >= -2e-3 * scale[q]).all(), q
+            assert abs(np.abs(pq).sum() - li) <= 2e-3 * scale[q], q
