@@ -861,7 +861,8 @@ def run_paper(args):
                 "roofline": {"bound": "fp64 alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                              "traffic": None,
                              "note": "one thread per query with the state in registers; FP64 throughput is not in "
-                                     "the measured peaks"},
+                                     "the measured peaks; ncu puts the FP64 pipe at 82% active on the l2sq:A:16 "
+                                     "configuration (profiles/k_diag_eval_fp64_anorm_n16_b1e6.md)"},
                 "cpu_baseline": cpu, "e2e": None, "clocks": clocks, "gpu_launches": len(table) * args.steps}
         print(json.dumps(line), flush=True)
     if ws > 1:
