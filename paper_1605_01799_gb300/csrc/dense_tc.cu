@@ -501,6 +501,23 @@ __device__ __forceinline__ void transpose_reduce16(float v[16], int lane) {
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
+// The same for V doubles: lane l ends with the warp total of value l & (V - 1).
+template <int V>
+__device__ __forceinline__ void transpose_reduce_d(double v[V], int lane) {
+#pragma unroll
+  for (int o = V / 2; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const double send = up ? v[i] : v[i + o];
+      const double keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int o = V; o < 32; o <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+}
+
 // Per-slot data of an item's column: t / lambda, query, prox scale and state.
 // Phases A and P take decision k here from the partial sums of iteration
 // k - 1 (every row tile of the column alike):  0 inactive, 1 active,
@@ -843,7 +860,13 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
       tmem_ld16(lanebase + 256 + j0, d2);
       tmem_ld16(lanebase + 384 + j0, d3);
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
+      for (int h = 0; h < 2; ++h) {
+      // the FP64 objective terms of 8 columns, summed over the warp's 32 rows
+      // by one transpose-reduction (9 FP64 adds per lane for 8 columns)
+      double f0v[8], f1v[8];
+#pragma unroll
+      for (int jh = 0; jh < 8; ++jh) {
+        const int jj = 8 * h + jh;
         const int j = j0 + jj;
         // A p = D1 + 2^-11 D2 + 2^-22 D3
         const float ap = acc[16 * g + jj] + (d2[jj] + d3[jj] * (1.f / kLoScale)) * (1.f / kLoScale);
@@ -869,12 +892,15 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
             }
           }
         }
-        f0 = warp_sum(f0);
-        f1 = warp_sum(f1);
-        if (lane == 0) {
-          S.redd[qd][j][0] = f0;
-          S.redd[qd][j][1] = f1;
-        }
+        f0v[jh] = f0;
+        f1v[jh] = f1;
+      }
+      transpose_reduce_d<8>(f0v, lane);
+      transpose_reduce_d<8>(f1v, lane);
+      if (lane < 8) {
+        S.redd[qd][j0 + 8 * h + lane][0] = f0v[0];
+        S.redd[qd][j0 + 8 * h + lane][1] = f1v[0];
+      }
       }
     }
     tc_fence_before();
@@ -983,23 +1009,52 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
 // query (query-indexed p1 and p2 planes of buffer set 0, the third term in the
 // g plane), from the retired u.
 __device__ __noinline__ void prep_final_operand(const TcArgs& a) {
-  const int64_t total = a.B_pad * a.np;
+  // four consecutive rows of one query per piece (np is a multiple of 128),
+  // two pieces per thread in flight
+  const int per_q = a.np / 4;
+  const int64_t total = a.B_pad * per_q;
   const int64_t stride = (int64_t)gridDim.x * NEPI;
-  for (int64_t i = (int64_t)blockIdx.x * NEPI + (threadIdx.x - 64); i < total; i += stride) {
-    const int64_t q = i / a.np;
-    const int row = (int)(i % a.np);
-    float pn = 0.f;
-    if (q < a.B) {
-      const float uu = a.ufin[i];
-      pn = a.h_kind == H_L2 ? a.sfin[q] * uu : shrink1(uu, a.tau[q] * a.w[row]);
+  for (int64_t i0 = (int64_t)blockIdx.x * NEPI + (threadIdx.x - 64); i0 < total; i0 += 2 * stride) {
+    float4 uv[2];
+    int64_t q[2];
+    int row[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int64_t i4 = i0 + b * stride;
+      q[b] = i4 / per_q;
+      row[b] = (int)(i4 - q[b] * per_q) * 4;
+      uv[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i4 < total && q[b] < a.B) uv[b] = *reinterpret_cast<const float4*>(a.ufin + i4 * 4);
     }
-    const __half h1 = __float2half_rn(pn);
-    const float r1 = pn - __half2float(h1);  // exact
-    const __half h2 = __float2half_rn(r1 * kLoScale);
-    const float r2 = r1 - __half2float(h2) * (1.f / kLoScale);  // exact
-    a.p1[0][i] = __half_as_ushort(h1);
-    a.p2[0][i] = __half_as_ushort(h2);
-    a.g[i] = __half_as_ushort(__float2half_rn(r2 * kLo2Scale));
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int64_t i4 = i0 + b * stride;
+      if (i4 >= total) break;
+      const bool live = q[b] < a.B;
+      const float tq = live ? (a.h_kind == H_L2 ? a.sfin[q[b]] : a.tau[q[b]]) : 0.f;
+      const float4 w4 = *reinterpret_cast<const float4*>(a.w + row[b]);
+      const float u4[4] = {uv[b].x, uv[b].y, uv[b].z, uv[b].w};
+      const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+      unsigned short h1[4], h2[4], h3[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float pn = 0.f;
+        if (live) pn = a.h_kind == H_L2 ? tq * u4[e] : shrink1(u4[e], tq * wv[e]);
+        const __half x1 = __float2half_rn(pn);
+        const float r1 = pn - __half2float(x1);  // exact
+        const __half x2 = __float2half_rn(r1 * kLoScale);
+        const float r2 = r1 - __half2float(x2) * (1.f / kLoScale);  // exact
+        h1[e] = __half_as_ushort(x1);
+        h2[e] = __half_as_ushort(x2);
+        h3[e] = __half_as_ushort(__float2half_rn(r2 * kLo2Scale));
+      }
+      const uint2 o1 = make_uint2(h1[0] | ((unsigned)h1[1] << 16), h1[2] | ((unsigned)h1[3] << 16));
+      const uint2 o2 = make_uint2(h2[0] | ((unsigned)h2[1] << 16), h2[2] | ((unsigned)h2[3] << 16));
+      const uint2 o3 = make_uint2(h3[0] | ((unsigned)h3[1] << 16), h3[2] | ((unsigned)h3[3] << 16));
+      *reinterpret_cast<uint2*>(a.p1[0] + i4 * 4) = o1;
+      *reinterpret_cast<uint2*>(a.p2[0] + i4 * 4) = o2;
+      *reinterpret_cast<uint2*>(a.g + i4 * 4) = o3;
+    }
   }
 }
 
@@ -1088,11 +1143,15 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     if (a.form != FORM_MIXED) continue;
     run(PH_B, k);
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
-    // every CTA takes the same decision from the same count
+    // every CTA takes the same decision from the same count: compact when it
+    // frees an eighth of the column tiles in use and shortens each phase by
+    // at least one round of items over the grid
     const int need = (n_active + BN - 1) / BN;
+    const int g = (int)gridDim.x;
+    const bool fewer_rounds = (need * a.rt + g - 1) / g < (cx.ct_on * a.rt + g - 1) / g;
     // (the packing offsets of the column tiles live in shared memory)
     if (a.compact && cx.ct_on <= (int)(sizeof(S.base) / sizeof(S.base[0])) &&
-        need + (cx.ct_on + 7) / 8 <= cx.ct_on) {
+        need + (cx.ct_on + 7) / 8 <= cx.ct_on && fewer_rounds) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
       if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
