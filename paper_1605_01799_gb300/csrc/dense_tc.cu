@@ -242,7 +242,7 @@ struct Smem {
   int qact[BN];
   int qid[BN];
   int base[1024];  // compaction: first new slot of each column tile
-  float red[4][BN][2];
+  float red[2][4][BN][2];  // by item parity: an item's row sums are read after the next item's first barrier
   double redd[4][BN][2];
 };
 
@@ -598,6 +598,22 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   float pf_tau = 0.f, pf_sc = 1.f;
   int pf_act = 0, pf_qid = 0;
   if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
+  // phases B and P: an item's row sums go to the partial-sum array after the
+  // next item's first barrier (or after the loop), which saves a barrier
+  int ipar = 0, prev_par = 0, prev_r = 0, prev_c = -1;
+  bool prev_on = false;
+  auto flush_part = [&]() {
+    if (prev_c >= 0 && prev_on) {
+      const int64_t q = (int64_t)prev_c * BN + et;
+      const float s0 = S.red[prev_par][0][et][0] + S.red[prev_par][1][et][0] + S.red[prev_par][2][et][0] +
+                       S.red[prev_par][3][et][0];
+      const float s1 = S.red[prev_par][0][et][1] + S.red[prev_par][1][et][1] + S.red[prev_par][2][et][1] +
+                       S.red[prev_par][3][et][1];
+      const int par = k & 1;
+      a.part[cb][((int64_t)(par * 2 + 0) * a.rt + prev_r) * a.B_pad + q] = s0;
+      a.part[cb][((int64_t)(par * 2 + 1) * a.rt + prev_r) * a.B_pad + q] = s1;
+    }
+  };
   while (it < items) {
     const int r = it % a.rt, c = it / a.rt;
     int it_next = it + gridDim.x;
@@ -608,6 +624,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     epi_sync();  // previous item's readers of the shared query data are done
     const bool record = ph != PH_B && r == 0;  // row tile 0 records decision k
     if (et < BN) {
+      if constexpr (ph != PH_A) flush_part();
       S.qtau[et] = pf_tau;
       S.qscale[et] = pf_sc;
       S.qact[et] = pf_act;
@@ -752,8 +769,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         transpose_reduce16(d1, lane);
         transpose_reduce16(uu, lane);
         if (lane < 16) {
-          S.red[qd][j0 + lane][0] = d1[0];
-          S.red[qd][j0 + lane][1] = uu[0];
+          S.red[ipar][qd][j0 + lane][0] = d1[0];
+          S.red[ipar][qd][j0 + lane][1] = uu[0];
         }
       } else if constexpr (ph == PH_P) {
         float* U = a.u[cb] + col0;
@@ -777,8 +794,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         transpose_reduce16(d1, lane);
         transpose_reduce16(uu, lane);
         if (lane < 16) {
-          S.red[qd][j0 + lane][0] = d1[0];
-          S.red[qd][j0 + lane][1] = uu[0];
+          S.red[ipar][qd][j0 + lane][0] = d1[0];
+          S.red[ipar][qd][j0 + lane][1] = uu[0];
         }
       }
     }
@@ -788,19 +805,19 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
     ++st.ue[buf];
     if constexpr (ph != PH_A) {
-      epi_sync();
-      if (et < BN && S.qact[et] == 1) {
-        const int64_t q = (int64_t)c * BN + et;
-        const float s0 = S.red[0][et][0] + S.red[1][et][0] + S.red[2][et][0] + S.red[3][et][0];
-        const float s1 = S.red[0][et][1] + S.red[1][et][1] + S.red[2][et][1] + S.red[3][et][1];
-        const int par = k & 1;
-        a.part[cb][((int64_t)(par * 2 + 0) * a.rt + r) * a.B_pad + q] = s0;
-        a.part[cb][((int64_t)(par * 2 + 1) * a.rt + r) * a.B_pad + q] = s1;
-      }
+      prev_on = et < BN && S.qact[et] == 1;
+      prev_c = c;
+      prev_r = r;
+      prev_par = ipar;
+      ipar ^= 1;
     }
     // the next item's slot data (and decision), from lines asked for above
     if (et < BN && it_next < items) slot_data(a, x, ph, (int64_t)(it_next / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
     it = it_next;
+  }
+  if constexpr (ph != PH_A) {
+    epi_sync();
+    if (et < BN) flush_part();
   }
 }
 
@@ -947,10 +964,10 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
       const int64_t sl = (int64_t)c * BN + et;
       const bool act = a.qact[cb][par][sl] == 1;
       const unsigned m = __ballot_sync(0xffffffffu, act);
-      if ((et & 31) == 0) S.red[et >> 5][1][0] = __int_as_float(__popc(m));
+      if ((et & 31) == 0) S.red[0][et >> 5][1][0] = __int_as_float(__popc(m));
       epi_sync_half();
       int rank = __popc(m & ((1u << (et & 31)) - 1u));
-      for (int wv = 0; wv < (et >> 5); ++wv) rank += __float_as_int(S.red[wv][1][0]);
+      for (int wv = 0; wv < (et >> 5); ++wv) rank += __float_as_int(S.red[0][wv][1][0]);
       S.qact[et] = act ? S.base[c] + rank : -1;  // destination slot
       if (act) {
         const int d = S.base[c] + rank;
