@@ -1144,7 +1144,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
 
   // Iteration k: phase A (decision k in its epilogue, then g), barrier,
   // phase B (u, p and the partial sums), barrier, and a compaction when it
-  // frees at least an eighth of the column tiles in use.  The BF16 form has
+  // frees a quarter of the column tiles in use.  The BF16 form has
   // the single phase P.
   bool ok = true;
   for (int k = 1; ok; ++k) {
@@ -1161,14 +1161,15 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     run(PH_B, k);
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
     // every CTA takes the same decision from the same count: compact when it
-    // frees an eighth of the column tiles in use and shortens each phase by
-    // at least one round of items over the grid
+    // frees a quarter of the column tiles in use and shortens each phase by
+    // at least one round of items over the grid (a sixteenth, an eighth, a
+    // third and a half were each measured slower)
     const int need = (n_active + BN - 1) / BN;
     const int g = (int)gridDim.x;
     const bool fewer_rounds = (need * a.rt + g - 1) / g < (cx.ct_on * a.rt + g - 1) / g;
     // (the packing offsets of the column tiles live in shared memory)
     if (a.compact && cx.ct_on <= (int)(sizeof(S.base) / sizeof(S.base[0])) &&
-        need + (cx.ct_on + 7) / 8 <= cx.ct_on && fewer_rounds) {
+        need + (cx.ct_on + 3) / 4 <= cx.ct_on && fewer_rounds) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
       if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
