@@ -49,9 +49,6 @@ def _cuda(a):
     return torch.tensor(np.ascontiguousarray(a), device="cuda")
 
 
-J_NAMES = {0: "quad", 2: "l1sq", 3: "linfsq"}
-
-
 def _case(jk, hk, n, B, seed):
     a = wl.uniform(seed, n, 0.5, 2.0) if jk == 0 else None
     w = wl.uniform(seed + 1, n, 0.5, 1.5) if hk in (1, 4) else None
