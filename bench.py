@@ -70,6 +70,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, ws):
+    """Element-wise maximum over the ranks of a list of floats (the job's
+    time is its slowest rank's).  The reduction tensor lives where the
+    process group's backend wants it: the GPU for NCCL, the host for gloo."""
+    values = [float(v) for v in values]
+    if ws <= 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.tolist()
+
+
+def whole_job_rate(units_per_rank, ws, ms):
+    """Units all ranks processed per second, from the slowest rank's ms."""
+    return ws * units_per_rank / (ms * 1e-3)
+
+
 def workload(n, batch, rank):
     import workloads as wl
     A, Q, s = wl.spd_matrix(2001, 2002, n)
@@ -259,10 +279,7 @@ def run_ragged(args):
         clk.terminate()
         clk.wait()
     ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = tt.item()
+    ms, = max_over_ranks([ms], ws)
     clocks = read_clocks(clk_path, local)
 
     e2e = None
@@ -287,8 +304,8 @@ def run_ragged(args):
         f1.record()
         torch.cuda.synchronize()
         barrier()
-        ems = f0.elapsed_time(f1) / steps_e2e
-        e2e = {"value": ws * Q / (ems * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+        ems, = max_over_ranks([f0.elapsed_time(f1) / steps_e2e], ws)
+        e2e = {"value": whole_job_rate(Q, ws, ems), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
                "d2h_bytes_per_step": int(Q * 8 + x.size * 4 + Q * 4), "ms_per_step": ems}
 
     # work-weighted roofline: dense instances on the tensor pipe (4 n x n MMA
@@ -375,10 +392,7 @@ def time_steps(fn, steps, ws, local):
         clk.terminate()
         clk.wait()
     ms = e0.elapsed_time(e1) / steps
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = tt.item()
+    ms, = max_over_ranks([ms], ws)
     return ms, read_clocks(clk_path, local)
 
 
@@ -941,10 +955,7 @@ def main():
         clk.wait()
     ms = e0.elapsed_time(e1) / args.steps
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_k]))
-    if ws > 1:
-        tt = torch.tensor([ms, kern_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms, kern_ms = tt.tolist()
+    ms, kern_ms = max_over_ranks([ms, kern_ms], ws)
     clocks = read_clocks(clk_path, local)
     value = ws * B / (ms * 1e-3)
 
@@ -972,11 +983,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ems = f0.elapsed_time(f1) / steps_e2e
-        if ws > 1:
-            tt = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ems = tt.item()
-        e2e = {"value": ws * B / (ems * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
+        ems, = max_over_ranks([ems], ws)
+        e2e = {"value": whole_job_rate(B, ws, ems), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
                "d2h_bytes_per_step": int(phih.numel() * 8 + gradh.numel() * 4 + dth.numel() * 4),
                "ms_per_step": ems}
 

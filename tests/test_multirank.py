@@ -1,0 +1,91 @@
+"""The multi-rank path of bench.py on the host: two gloo ranks on 127.0.0.1.
+
+With N GPUs the benchmark runs one process per GPU; each rank evaluates its
+own shard of the query stream (weak scaling, no collective on the data
+path), the job's time is the slowest rank's, and the throughput counts the
+queries of all ranks.  No GPU is involved here: the ranks exchange their
+times over gloo, and the shards are checked against a single-process draw
+of the same stream."""
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    A, w, x, t = bench.workload(16, 8, rank)
+    # a rank's own "time": the slowest rank's must come back on every rank
+    mx = bench.max_over_ranks([10.0 + 3.0 * rank, 5.0 - rank], ws)
+    rate = bench.whole_job_rate(8, ws, mx[0])
+    np.savez(os.path.join(out_dir, "rank%d.npz" % rank), x=x, t=t, mx=np.array(mx), rate=rate)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_reduce(tmp_path):
+    import torch.multiprocessing as mp
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, str(tmp_path))) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    sys.path.insert(0, ROOT)
+    import bench
+    _, _, x_all, t_all = bench.workload(16, 16, 0)  # one process drawing both shards
+    for r in range(ws):
+        d = np.load(tmp_path / ("rank%d.npz" % r))
+        # the shards partition one query stream, in rank order
+        assert np.array_equal(d["x"], x_all[8 * r:8 * (r + 1)])
+        assert np.array_equal(d["t"], t_all[8 * r:8 * (r + 1)])
+        # element-wise maximum over the ranks, the same on every rank
+        assert list(d["mx"]) == [13.0, 5.0]
+        assert float(d["rate"]) == pytest.approx(2 * 8 / 13.0e-3)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """bench.py --impl reference under two ranks: rank 0 times the oracle and
+    prints one JSON line; rank 1 exits 0 without work."""
+    outs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r), MASTER_ADDR="127.0.0.1")
+        p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                            "--steps", "1", "--warmup", "1", "--n", "64", "--cpu-sample", "16"],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+        assert p.returncode == 0, p.stderr[-2000:]
+        outs.append([l for l in p.stdout.splitlines() if l.startswith("{")])
+    assert len(outs[0]) == 1 and outs[1] == []
+    import json
+    line = json.loads(outs[0][0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_generator_offsets_slice_one_stream():
+    """The seeded generators return slices of one stream for any offset, odd
+    ones included (normals come in Box-Muller pairs)."""
+    sys.path.insert(0, ROOT)
+    import workloads as wl
+    full_n, full_u = wl.normal(7, 1001), wl.uniform(7, 1001)
+    for off, cnt in [(0, 10), (1, 7), (2, 9), (13, 100), (500, 499), (1000, 1)]:
+        assert np.array_equal(wl.normal(7, cnt, offset=off), full_n[off:off + cnt])
+        assert np.array_equal(wl.uniform(7, cnt, offset=off), full_u[off:off + cnt])

@@ -41,15 +41,21 @@ def log_uniform(seed, count, lo, hi, offset=0):
 
 
 def normal(seed, count, std=1.0, offset=0):
-    """Box-Muller: pairs (u1, u2) -> sqrt(-2 ln(1-u1)) (cos, sin)(2 pi u2)."""
-    m = (count + 1) // 2
-    u = uniform(seed, 2 * m, offset=2 * offset)
+    """Box-Muller: pairs (u1, u2) -> sqrt(-2 ln(1-u1)) (cos, sin)(2 pi u2).
+    Normal i of the stream is the cos (i even) or sin (i odd) of pair i // 2,
+    whose uniforms are numbers 2 (i // 2) and 2 (i // 2) + 1 of the uniform
+    stream, so a call with an offset returns a slice of the same stream."""
+    if count <= 0:
+        return np.zeros(0)
+    p0, p1 = offset // 2, (offset + count - 1) // 2
+    u = uniform(seed, 2 * (p1 - p0 + 1), offset=2 * p0)
     r = np.sqrt(-2.0 * np.log1p(-u[0::2]))
     th = 2.0 * np.pi * u[1::2]
-    z = np.empty(2 * m)
+    z = np.empty(2 * (p1 - p0 + 1))
     z[0::2] = r * np.cos(th)
     z[1::2] = r * np.sin(th)
-    return std * z[:count]
+    s = offset - 2 * p0
+    return std * z[s:s + count]
 
 
 def haar_orthogonal(seed, n):
