@@ -34,7 +34,7 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 
   s[14] = 2 * B_pad * 4;                 // qact (by decision parity)
   s[15] = 2 * (B_pad / 128) * 4;         // tile_act (tensor-core solver: last decision with active slots, and its count)
   s[16] = tc ? B_pad * np * 4 : 0;       // y_b
-  s[17] = tc ? B_pad * np * 4 : 0;       // u_b
+  s[17] = B_pad * np * 4;                // u_b (FP32 solver: u of odd iterations)
   s[18] = tc ? B_pad * np * 2 : 0;       // ph_b
   s[19] = tc ? B_pad * np * 2 : 0;       // pl_b
   s[20] = B_pad * 4;                     // scale_b
@@ -79,7 +79,7 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
   d->qact = (int*)(p + off[14]);
   d->tile_act = (int*)(p + off[15]);
   d->y_b = tc ? (float*)(p + off[16]) : nullptr;
-  d->u_b = tc ? (float*)(p + off[17]) : nullptr;
+  d->u_b = (float*)(p + off[17]);
   d->ph_b = tc ? (uint16_t*)(p + off[18]) : nullptr;
   d->pl_b = tc ? (uint16_t*)(p + off[19]) : nullptr;
   d->scale_b = (float*)(p + off[20]);

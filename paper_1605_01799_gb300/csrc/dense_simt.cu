@@ -10,7 +10,10 @@
 // One persistent cooperative launch runs all iterations.  Work item =
 // (128-row tile of n, 128-query column tile).  The B-operand loader forms r
 // from u and y on the fly; the epilogue updates u and writes per-(row tile,
-// query) partial sums of |u^k - u^{k-1}|^2 and |u^k|^2.  A grid barrier ends
+// query) partial sums of |u^k - u^{k-1}|^2 and |u^k|^2.  u^k lives in buffer
+// k & 1: an item's GEMM reads u^{k-1} over all rows of its column while the
+// epilogues of the column's other row tiles write u^k, so the two may not
+// share storage.  A grid barrier ends
 // each iteration; the next iteration decides each query's convergence from the
 // partials (every CTA reaches the same decision from the same data) and skips
 // column tiles with no active query.  After the last iteration one more GEMM
@@ -40,6 +43,7 @@ struct SimtArgs {
   const float* x;   // [B][n] the caller's queries (terminal point)
   float* beta;      // optional: control in dH(grad phi) [B][n]
   float* xfin;      // optional: terminal point x - t beta [B][n]
+  float* U[2];      // u^k in U[k & 1] (U[0] holds u^0 = y)
 };
 
 // Per-query data of the current column tile, decided at the start of an item.
@@ -47,6 +51,7 @@ struct TileQ {
   float tau[BN];
   float scale[BN];  // l2: shrink_2 scale of u^{k-1}
   int act[BN];      // 1 = update this query in this iteration
+  int ub[BN];       // final pass: the buffer of the query's last iterate
   int first;        // iteration 1: p^0 = y
 };
 
@@ -114,7 +119,8 @@ __device__ __forceinline__ int block_sum_int(int v, int* red) {
 // mode 1: final (rhs = p).
 template <int MODE>
 __device__ void gemm_tile(const SimtArgs& a, const float* __restrict__ Mat, int r, int c, const TileQ& tq,
-                          float (*As)[BK][BM + PADS], float (*Bs)[BK][BN + PADS], float acc[8][8]) {
+                          const float* __restrict__ Uin, float (*As)[BK][BM + PADS], float (*Bs)[BK][BN + PADS],
+                          float acc[8][8]) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const DenseWs& W = a.ws;
   const int np = a.np;
@@ -137,7 +143,9 @@ __device__ void gemm_tile(const SimtArgs& a, const float* __restrict__ Mat, int 
       const int f = tid + h * NT, j = f >> 2, c4 = f & 3;
       const int64_t q = (int64_t)c * BN + j;
       const int64_t off = q * np + k0 + c4 * 4;
-      const float4 u4 = *reinterpret_cast<const float4*>(W.u + off);
+      // step: u^{k-1} of every query; final: each query's last iterate
+      const float* Uq = MODE == 0 ? Uin : a.U[tq.ub[j]];
+      const float4 u4 = *reinterpret_cast<const float4*>(Uq + off);
       float4 o;
       if (MODE == 0) {
         const float4 y4 = *reinterpret_cast<const float4*>(W.y + off);
@@ -229,7 +237,9 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
       cnt = block_sum_int(cnt, red);
       if (r == 0 && tid == 0 && cnt > 0) atomicAdd(W.bar + 2 + (k % 3), (unsigned)cnt);
       if (cnt == 0 || k > a.max_iter) continue;
-      gemm_tile<0>(a, a.M, r, c, tq, As, Bs, acc);
+      const float* Uold = a.U[(k - 1) & 1];
+      float* Unew = a.U[k & 1];
+      gemm_tile<0>(a, a.M, r, c, tq, Uold, As, Bs, acc);
       // epilogue: u^k = v^k + u^{k-1} - p^{k-1}; partials of |du|^2, |u|^2
       float pdu[8], pnu[8];
 #pragma unroll
@@ -242,8 +252,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int row0 = r * BM + hh * 64 + ty * 4;
-          float4* up = reinterpret_cast<float4*>(W.u + q * a.np + row0);
-          const float4 u4 = *up;
+          const float4 u4 = *reinterpret_cast<const float4*>(Uold + q * a.np + row0);
           const float4 w4 = *reinterpret_cast<const float4*>(a.w + row0);
           const float uo[4] = {u4.x, u4.y, u4.z, u4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
           float un[4];
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
             pdu[jj] += du * du;
             pnu[jj] += un[e] * un[e];
           }
-          if (act) *up = make_float4(un[0], un[1], un[2], un[3]);
+          if (act) *reinterpret_cast<float4*>(Unew + q * a.np + row0) = make_float4(un[0], un[1], un[2], un[3]);
         }
       }
       // reduce the partials over the 16 row groups (ty) of the tile
@@ -302,13 +311,14 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
       if (kl >= 1)
         for (int rr = 0; rr < a.rt; ++rr) nu2 += W.part[((int64_t)((kl & 1) * 2 + 1) * a.rt + rr) * W.B_pad + q];
       tq.scale[j] = kl >= 1 ? shrink2_scale(sqrtf(nu2), tq.tau[j]) : 1.f;
+      tq.ub[j] = kl & 1;
     }
     tq.first = 0;
     __syncthreads();
     int any = 0;
     for (int j = 0; j < BN; ++j) any |= tq.act[j];
     if (!any) continue;
-    gemm_tile<1>(a, a.A, r, c, tq, As, Bs, acc);
+    gemm_tile<1>(a, a.A, r, c, tq, nullptr, As, Bs, acc);
     double f0[8], f1[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int row0 = r * BM + hh * 64 + ty * 4;
-        const float4 u4 = *reinterpret_cast<const float4*>(W.u + q * a.np + row0);
+        const float4 u4 = *reinterpret_cast<const float4*>(a.U[tq.ub[j]] + q * a.np + row0);
         const float4 y4 = *reinterpret_cast<const float4*>(W.y + q * a.np + row0);
         const float4 w4 = *reinterpret_cast<const float4*>(a.w + row0);
         const float uo[4] = {u4.x, u4.y, u4.z, u4.w}, yv[4] = {y4.x, y4.y, y4.z, y4.w};
@@ -391,6 +401,8 @@ hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const flo
   a.x = x;
   a.beta = beta;
   a.xfin = xfin;
+  a.U[0] = w.u;
+  a.U[1] = w.u_b;
   int per_sm = 0;
   HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_simt, NT, 0));
   if (per_sm < 1) return fail(HOPF_ECUDA, "dense FP32 solver: kernel does not fit on an SM");

@@ -105,7 +105,7 @@ struct DenseWs {
   // queries converge; a second buffer set receives the packed slots, and a
   // converged query's u and l2 scale are retired to query-indexed arrays
   float* y_b = nullptr;      // [B_pad][n_pad]
-  float* u_b = nullptr;      // [B_pad][n_pad]
+  float* u_b = nullptr;      // [B_pad][n_pad] (FP32 solver: u^k of odd k; u^k of even k is in u)
   uint16_t* ph_b = nullptr;  // [B_pad][n_pad]
   uint16_t* pl_b = nullptr;  // [B_pad][n_pad]
   float* scale_b = nullptr;  // [B_pad]

@@ -105,6 +105,36 @@ def test_dense_iteration_counts(hg, orc):
     assert np.abs(it - same["iters"]).max() <= 10
 
 
+@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+def test_dense_iterates_across_row_tiles(hg, orc, precision):
+    """n = 384 (three row tiles per query): an item's product reads u^{k-1}
+    over all rows while the other row tiles' epilogues write u^k, so the two
+    must not share storage.  Two evaluations agree bit for bit, and the
+    iteration counts follow the oracle's under the same rule."""
+    import torch
+    n, B = 384, 1024
+    A, Q, s = wl.spd_matrix(11700, 11701, n)
+    w = wl.uniform(11702, n, 0.5, 1.5)
+    x = wl.normal(11703, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(11704, B, 0.1, 3.0).astype(np.float32)
+    tol = 1e-12
+    h = hg.Hopf(A, 1, w=w, tol=tol, max_iter=3000, precision=getattr(hg, "P_" + precision))
+    xd, td = _cuda(x), _cuda(t)
+    o1 = h.eval(xd, td)
+    torch.cuda.synchronize()
+    snap = {k: v.clone() for k, v in o1.items()}
+    o2 = h.eval(xd, td)
+    torch.cuda.synchronize()
+    for k in ("phi", "grad", "iters"):
+        assert torch.equal(snap[k], o2[k]), k
+    if precision == "FP32":
+        same = orc.Problem(A, 1, w=w, tol=tol, max_iter=3000, stop_rule=orc.STOP_UREL).eval(
+            x.astype(np.float64), t.astype(np.float64))
+        it = o2["iters"].cpu().numpy()
+        assert np.median(np.abs(it - same["iters"])) <= 1
+        assert np.abs(it - same["iters"]).max() <= 10
+
+
 def test_dense_t_zero_and_not_converged(hg, orc):
     """t = 0 gives phi = J(x) (eq. 1.1b); a tiny max_iter reports
     NOT_CONVERGED with iters = max_iter."""
