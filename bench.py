@@ -530,7 +530,9 @@ def run_grad(args):
     pk = peaks()
     tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
     f_fwd = float(np.sum(2.0 * n * n * (4.0 * iters + 3.0)))
-    f_bwd = 2.0 * n * n * B  # g_A = -1/2 V^T diag(g) V on FP32 CUDA cores
+    # g_A = -1/2 V^T diag(g) V is symmetric: a SYRK's n (n + 1) / 2 distinct
+    # entries of 2B flop each (FP32 CUDA cores)
+    f_bwd = float(n) * (n + 1) * B
     t_roof = f_fwd / (tc_peak * 1e12) + f_bwd / (ALU_PEAK * 1e12)
     frac = t_roof / (ms * 1e-3)
     roof = {"bound": "tensor+alu (work-weighted)", "achieved": frac, "peak": 1.0,

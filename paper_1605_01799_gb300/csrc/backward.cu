@@ -66,19 +66,31 @@ __global__ void k_bwd_diagA(const float* __restrict__ g, const float* __restrict
 // rows of V (contiguous along the output index), so no transpose is needed.
 constexpr int BM = 128, BK = 16, NT = 256, PADS = 4;
 
+// g_A is symmetric, so only the tiles (bi, bj) with bi <= bj are computed and
+// an off-diagonal tile is written twice (as itself and transposed): T (T + 1) / 2
+// blocks for T = ceil(n / 128) tile rows.  The next k-tile of the batch is
+// loaded into registers while the current one is multiplied.
 __global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ g, const float* __restrict__ V, int n,
                                                       int64_t B, float* __restrict__ gA) {
-  __shared__ __align__(16) float As[BK][BM + PADS];
-  __shared__ __align__(16) float Bs[BK][BM + PADS];
+  __shared__ __align__(16) float As[2][BK][BM + PADS];
+  __shared__ __align__(16) float Bs[2][BK][BM + PADS];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BM;
+  const int T = (n + BM - 1) / BM;
+  int bi = 0, rem = blockIdx.x;
+  while (rem >= T - bi) {
+    rem -= T - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  const int i0 = bi * BM, j0 = bj * BM;
   float acc[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-  for (int64_t q0 = 0; q0 < B; q0 += BK) {
-    // each thread loads 8 elements of each operand tile (16 rows of the batch x 128)
+  // each thread stages 8 elements of each operand tile (16 batch rows x 128)
+  float ra[8], rb[8];
+  auto load = [&](int64_t q0) {
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
       const int f = tid + h * NT, kk = f >> 7, col = f & 127;
@@ -86,16 +98,31 @@ __global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ 
       const bool okq = q < B;
       const float gq = okq ? g[q] : 0.f;
       const int ia = i0 + col, jb = j0 + col;
-      As[kk][col] = (okq && ia < n) ? V[q * n + ia] * gq : 0.f;
-      Bs[kk][col] = (okq && jb < n) ? V[q * n + jb] : 0.f;
+      ra[h] = (okq && ia < n) ? V[q * n + ia] * gq : 0.f;
+      rb[h] = (okq && jb < n) ? V[q * n + jb] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int f = tid + h * NT, kk = f >> 7, col = f & 127;
+      As[buf][kk][col] = ra[h];
+      Bs[buf][kk][col] = rb[h];
+    }
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int cur = 0;
+  for (int64_t q0 = 0; q0 < B; q0 += BK) {
+    const bool more = q0 + BK < B;
+    if (more) load(q0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -103,7 +130,11 @@ __global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ 
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
     }
-    __syncthreads();
+    if (more) {
+      store(cur ^ 1);  // the other buffer: its last readers finished before the previous barrier
+      __syncthreads();
+      cur ^= 1;
+    }
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -112,7 +143,11 @@ __global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ 
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int j = j0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
-      if (j < n) gA[(int64_t)i * n + j] = -0.5f * acc[a][b];
+      if (j < n) {
+        const float v = -0.5f * acc[a][b];
+        gA[(int64_t)i * n + j] = v;
+        if (bi != bj) gA[(int64_t)j * n + i] = v;
+      }
     }
   }
 }
@@ -131,8 +166,8 @@ hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const flo
     if (h->a_kind == HOPF_A_DIAG) {
       k_bwd_diagA<<<(n + 255) / 256, 256, 0, stream>>>(g_phi, vstar, n, batch, g_A);
     } else {
-      dim3 grd((n + BM - 1) / BM, (n + BM - 1) / BM);
-      k_bwd_denseA<<<grd, NT, 0, stream>>>(g_phi, vstar, n, batch, g_A);
+      const int T = (n + BM - 1) / BM;
+      k_bwd_denseA<<<(unsigned)(T * (T + 1) / 2), NT, 0, stream>>>(g_phi, vstar, n, batch, g_A);
     }
     HOPF_CUDA(cudaGetLastError());
   }
