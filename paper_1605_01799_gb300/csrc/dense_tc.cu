@@ -72,7 +72,7 @@ constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 // ufin, sfin, fpart, the final-pass operand planes.
 struct TcArgs {
   CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mP1b, mP2b, mG, mP3;  // mP3: the g plane read as the third split of p
-  CUtensorMap mU[2], mY[2];  // FP32 state planes, for L2 prefetch of the epilogue's tiles
+  CUtensorMap mU[2];  // the FP32 u planes, for L2 prefetch of the epilogue's tiles
   float* y[2];
   float* u[2];
   uint16_t* p1[2];
@@ -317,12 +317,9 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, x, ph, c)) continue;
-    // the epilogue of this item reads u (and y) of its tile one to two items
-    // from now: start the DRAM reads now
-    if (ph != PH_F) {
-      tma_prefetch_l2(&a.mU[x.cb], r * BM, c * BN);
-      if (ph != PH_B) tma_prefetch_l2(&a.mY[x.cb], r * BM, c * BN);
-    }
+    // the epilogue of this item reads u of its tile one to two items from
+    // now: start the DRAM reads now (a prefetch of y as well measured slower)
+    if (ph != PH_F) tma_prefetch_l2(&a.mU[x.cb], r * BM, c * BN);
     for (int kb = 0; kb < nk; kb += kstep) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
         const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
@@ -1311,9 +1308,7 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
             encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
             encode(&a.mP1b, w.ph_b, w.B_pad, np, false) && encode(&a.mP2b, w.pl_b, w.B_pad, np, false) &&
             encode(&a.mG, w.g, w.B_pad, np, true) && encode_f32(&a.mU[0], w.u, w.B_pad, np) &&
-            encode_f32(&a.mY[0], w.y, w.B_pad, np) &&
-            encode_f32(&a.mU[1], form == FORM_MIXED ? w.u_b : w.u, w.B_pad, np) &&
-            encode_f32(&a.mY[1], form == FORM_MIXED ? w.y_b : w.y, w.B_pad, np);
+            encode_f32(&a.mU[1], form == FORM_MIXED ? w.u_b : w.u, w.B_pad, np);
   if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
   a.y[0] = w.y;
   a.y[1] = w.y_b;

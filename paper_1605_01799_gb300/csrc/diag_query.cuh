@@ -213,7 +213,7 @@ struct Query {
         T r1 = T(0);
 #pragma unroll
         for (int j = 0; j < VPT; ++j) {
-          const T du = z[j] - (d[j] + b[j]);  // u^{k-1} = d^{k-1} + b^{k-1}
+          const T du = vn[j] - d[j];  // u^k - u^{k-1} = (v^k + b^{k-1}) - (d^{k-1} + b^{k-1})
           r1 += du * du;
         }
         Group<G, T>::sum2(r1, zz);
@@ -224,7 +224,7 @@ struct Query {
           T dn;
           if constexpr (L2) dn = s2 * z[j];            // eq. 3.4(b)
           else dn = shrink1(z[j], thr[j]);
-          b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
+          b[j] = z[j] - dn;  // eq. 3.4(c): b^{k-1} + v^k - d^k = u^k - d^k
           d[j] = dn;
         }
         if (k >= 2 && r1 <= P.tol * (zz > T(1) ? zz : T(1))) {
@@ -243,7 +243,7 @@ struct Query {
           r1 += (vn[j] - v[j]) * (vn[j] - v[j]);
           r2 += (dn - d[j]) * (dn - d[j]);
           r3 += (dn - vn[j]) * (dn - vn[j]);
-          b[j] = b[j] + vn[j] - dn;  // eq. 3.4(c)
+          b[j] = z[j] - dn;  // eq. 3.4(c): b^{k-1} + v^k - d^k = u^k - d^k
           d[j] = dn;
           v[j] = vn[j];
         }
@@ -483,11 +483,11 @@ struct Query {
             r2 += (dn[j] - d[j]) * (dn[j] - d[j]);
             r3 += (dn[j] - vn[j]) * (dn[j] - vn[j]);
           } else {
-            const T du = z[j] - (d[j] + b[j]);  // u^k - u^{k-1}
+            const T du = vn[j] - d[j];  // u^k - u^{k-1} = (v^k + b^{k-1}) - (d^{k-1} + b^{k-1})
             r1 += du * du;
             r2 += z[j] * z[j];
           }
-          b[j] = b[j] + vn[j] - dn[j];  // eq. 3.4(c)
+          b[j] = z[j] - dn[j];  // eq. 3.4(c): b^{k-1} + v^k - d^k = u^k - d^k
           d[j] = dn[j];
           v[j] = vn[j];
         }
