@@ -167,7 +167,8 @@ hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const d
  * trajectory is beta = grad H(grad_x phi); for a 1-homogeneous H the terminal
  * point is the Hopf-Lax minimiser x - t beta).  Same call as hopf_eval, plus
  *   beta    [batch][n] float: the control.  At the fixed point the optimality
- *           condition of eq. 3.3 gives lambda b = y - A p, so the library
+ *           condition of eq. 3.3 gives lambda b = y - A p (for the norm
+ *           initial data, y - lambda b lies in dJ*(p)), so the library
  *           returns beta = b / (t / lambda) = (u - prox(u)) / (t / lambda),
  *           which lies in the subdifferential dH(p) (equal to grad H(p)
  *           where H is differentiable); 0 when t = 0.  Device, required.
