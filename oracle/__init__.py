@@ -85,6 +85,7 @@ def lib():
         _lib.orc_union_closest.restype = ctypes.c_int
         _lib.orc_maxH_eval.restype = ctypes.c_int
         _lib.orc_control.restype = None
+        _lib.orc_backward_params.restype = None
         _lib.orc_prox.restype = None
         _lib.orc_factor.restype = ctypes.c_int
         _lib.orc_num_threads.restype = ctypes.c_int
@@ -199,6 +200,23 @@ def backward(n, a_kind, h_kind, w, g_phi, vstar, t, want_A=True):
     lib().orc_backward(n, a_kind, h_kind, _p(w), ctypes.c_int64(B), _p(g_phi), _p(vstar), _p(t),
                        _p(g_x), _p(g_t), _p(g_A))
     return {"g_x": g_x, "g_t": g_t, "g_A": g_A}
+
+
+def backward_params(n, h_kind, w, g_phi, vstar, t):
+    """Gradients of sum_q g_q phi_q with respect to the centre c, the constant
+    c0 and the weights w (weighted l1, sqrt(sum w p^2)), by the envelope
+    theorem at the minimisers vstar."""
+    vstar = np.ascontiguousarray(vstar, dtype=np.float64).reshape(-1, n)
+    B = vstar.shape[0]
+    g_phi = np.ascontiguousarray(g_phi, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    g_c = np.empty(n)
+    g_c0 = ctypes.c_double(0.0)
+    g_w = np.empty(n) if int(h_kind) in (H_WL1, H_DNORM) else None
+    lib().orc_backward_params(n, int(h_kind), _p(w), ctypes.c_int64(B), _p(g_phi), _p(vstar), _p(t), _p(g_c),
+                              ctypes.byref(g_c0), _p(g_w))
+    return {"g_c": g_c, "g_c0": g_c0.value, "g_w": g_w}
 
 
 def control(problem, x, t, grad):

@@ -661,6 +661,37 @@ void orc_backward(int32_t n, int32_t a_kind, int32_t h_kind, const double *w, in
     (void)t;
 }
 
+/* Gradients with respect to the other parameters of the problem, by the
+ * same envelope argument on eq. 3.3 (phi = <x - c, p> - J*_0(p) - c0 - t H(p)
+ * at the minimiser p):
+ *   d phi / d c    = -p            (J depends on x - c),
+ *   d phi / d c0   = -1,
+ *   d phi / d w_i  = -t |p_i|                 (H = sum_i w_i |p_i|),
+ *                  = -t p_i^2 / (2 H(p))      (H = sqrt(sum_i w_i p_i^2), 0 at p = 0).
+ * With upstream weights g_q, summed over the batch: g_c (n), g_c0 (1) and
+ * g_w (n, weighted kinds only; may be NULL). */
+void orc_backward_params(int32_t n, int32_t h_kind, const double *w, int64_t batch, const double *g_phi,
+                         const double *vstar, const double *t, double *g_c, double *g_c0, double *g_w)
+{
+    for (int i = 0; i < n; ++i) {
+        g_c[i] = 0.0;
+        if (g_w) g_w[i] = 0.0;
+    }
+    *g_c0 = 0.0;
+    for (int64_t q = 0; q < batch; ++q) {
+        const double *v = vstar + q * n;
+        *g_c0 -= g_phi[q];
+        for (int i = 0; i < n; ++i) g_c[i] -= g_phi[q] * v[i];
+        if (g_w && h_kind == ORC_H_WL1) {
+            for (int i = 0; i < n; ++i) g_w[i] -= g_phi[q] * t[q] * fabs(v[i]);
+        } else if (g_w && h_kind == ORC_H_DNORM) {
+            const double H = orc_H(h_kind, n, w, v);
+            if (H > 0.0)
+                for (int i = 0; i < n; ++i) g_w[i] -= g_phi[q] * t[q] * v[i] * v[i] / (2.0 * H);
+        }
+    }
+}
+
 /* ---- optimal control and terminal point (Section 2, the control remark and
  *      the Hopf-Lax discussion at the end of Section 2.2) ------------------- */
 

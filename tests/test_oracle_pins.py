@@ -669,3 +669,40 @@ def test_l1sq_beta_fixed_point_including_ties(orc):
         assert abs(b - rhs) <= 1e-13 * max(1, abs(b)), (trial, b, rhs)
         if trial % 2:
             assert abs(b - m) <= 1e-13 * max(1, m)
+
+
+# ---- P14: gradients with respect to c, c0 and w (envelope theorem) ---------
+
+@pytest.mark.parametrize("hk", ["wl1", "dnorm", "l2"])
+def test_parameter_gradients_against_finite_differences(orc, hk):
+    """d/dc, d/dc0 and d/dw of sum_q g_q phi_q against central differences of
+    the oracle's own converged phi (FP64, h = 1e-5): a dropped t, a wrong
+    sign or a missing 1/(2H) fails."""
+    n, B = 5, 4
+    a = wl.uniform(9401, n, 0.5, 2.0)
+    c = wl.normal(9402, n, 1.0)
+    w = wl.uniform(9403, n, 0.5, 1.5)
+    x = wl.normal(9404, B * n, 2.0).reshape(B, n)
+    t = wl.uniform(9405, B, 0.3, 2.0)
+    g = wl.normal(9406, B, 1.0)
+    kind = {"wl1": orc.H_WL1, "dnorm": orc.H_DNORM, "l2": orc.H_L2}[hk]
+    ww = w if hk != "l2" else None
+    kw = dict(tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+
+    def L(cc=c, c0=0.5, wv=ww):
+        return float(g @ orc.Problem(a, kind, w=wv, centre=cc, c0=c0, **kw).eval(x, t)["phi"])
+
+    r = orc.Problem(a, kind, w=ww, centre=c, c0=0.5, **kw).eval(x, t)
+    bp = orc.backward_params(n, kind, ww, g, r["grad"], t)
+    h = 1e-5
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd = (L(cc=c + e) - L(cc=c - e)) / (2 * h)
+        assert abs(fd - bp["g_c"][i]) <= 1e-6 * max(1, abs(fd)), ("c", i, fd, bp["g_c"][i])
+        if hk != "l2":
+            fdw = (L(wv=w + e) - L(wv=w - e)) / (2 * h)
+            assert abs(fdw - bp["g_w"][i]) <= 1e-6 * max(1, abs(fdw)), ("w", i, fdw, bp["g_w"][i])
+    fd0 = (L(c0=0.5 + h) - L(c0=0.5 - h)) / (2 * h)
+    assert abs(fd0 - bp["g_c0"]) <= 1e-8
+    assert bp["g_w"] is None if hk == "l2" else bp["g_w"] is not None
