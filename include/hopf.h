@@ -249,6 +249,23 @@ hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int6
 hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
                           float* g_t, float* g_A, cudaStream_t stream);
 
+/* Gradients of L = sum_q g_phi[q] phi_q with respect to the problem's other
+ * parameters, by the same envelope argument (phi = <x - c, p> - J*_0(p) - c0
+ * - t H(p) at the minimiser p = vstar):
+ *   g_c  [n] float   dL/dc    = -sum_q g_phi[q] vstar[q]                (may be NULL)
+ *   g_c0 [1] float   dL/dc0   = -sum_q g_phi[q]                         (may be NULL)
+ *   g_w  [n] float   dL/dw_i  = -sum_q g_phi[q] t[q] |vstar[q][i]|      (HOPF_H_WL1)
+ *                             = -sum_q g_phi[q] t[q] vstar[q][i]^2 / (2 H_q)
+ *                               with H_q = -dphidt[q] (HOPF_H_DNORM; 0 where H_q = 0)
+ *                    (may be NULL; requested for another h_kind: HOPF_EUNSUPPORTED)
+ * t [batch] is needed for g_w, dphidt [batch] (the forward's output) for g_w
+ * with HOPF_H_DNORM.  All device pointers, float sums accumulated in FP64 in a
+ * fixed order (the result does not depend on the launch).  batch = 0 writes
+ * zeros. */
+hopf_status hopf_backward_params(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar,
+                                 const float* t, const float* dphidt, float* g_c, float* g_c0, float* g_w,
+                                 cudaStream_t stream);
+
 /* ---- ragged batches -----------------------------------------------------
  * Many independent instances (each with its own A, H, n and number of
  * queries) evaluated together.  Queries share no state (Section 1; Section

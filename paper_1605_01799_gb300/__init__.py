@@ -29,7 +29,7 @@ Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
 
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
-           "hopf_backward",
+           "hopf_backward", "hopf_backward_params",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
            "hopf_last_error", "hopf_version"]
@@ -72,6 +72,7 @@ def lib():
             "hopf_union_closest_noalloc": ([_vp, _i32, _i64, _vp, _f32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
                                            ctypes.c_int),
             "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "hopf_backward_params": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_set_compaction": ([_vp, _i32], ctypes.c_int),
             "hopf_batch_create": ([ctypes.POINTER(hopf_desc), _i32, ctypes.POINTER(_vp), _vp], ctypes.c_int),
@@ -234,6 +235,21 @@ class Hopf:
         _check(lib().hopf_backward(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
                                    _stream(stream)))
         return gx, gt, gA
+
+    def backward_params(self, g_phi, vstar, t=None, dphidt=None, want_c=True, want_c0=True, want_w=False,
+                        stream=None):
+        """dL/dc [n], dL/dc0 [1] and dL/dw [n] of L = sum_q g_phi[q] phi_q
+        (envelope theorem; dL/dw for the weighted Hamiltonians, which needs t,
+        and dphidt for sqrt(sum w p^2))."""
+        import torch
+        B = vstar.shape[0]
+        dev = vstar.device
+        gc = torch.empty(self.n, dtype=torch.float32, device=dev) if want_c else None
+        gc0 = torch.empty(1, dtype=torch.float32, device=dev) if want_c0 else None
+        gw = torch.empty(self.n, dtype=torch.float32, device=dev) if want_w else None
+        _check(lib().hopf_backward_params(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(t), _ptr(dphidt),
+                                          _ptr(gc), _ptr(gc0), _ptr(gw), _stream(stream)))
+        return gc, gc0, gw
 
 
 class HopfBatch:

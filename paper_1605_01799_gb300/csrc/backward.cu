@@ -152,7 +152,59 @@ __global__ void __launch_bounds__(NT, 2) k_bwd_denseA(const float* __restrict__ 
   }
 }
 
+// Column sums over the batch for the parameter gradients: thread i owns
+// column i and walks the batch in order (FP64 sums, deterministic).
+__global__ void k_bwd_params(const float* __restrict__ g, const float* __restrict__ V, const float* __restrict__ t,
+                             const float* __restrict__ dphidt, int n, int64_t B, int h_kind,
+                             float* __restrict__ g_c, float* __restrict__ g_w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sc = 0.0, sw = 0.0;
+  for (int64_t q = 0; q < B; ++q) {
+    const double v = V[q * n + i], gq = g[q];
+    sc -= gq * v;
+    if (g_w) {
+      if (h_kind == H_WL1) {
+        sw -= gq * (double)t[q] * fabs(v);
+      } else {  // H_DNORM: H_q = -dphidt[q]
+        const double H = -(double)dphidt[q];
+        if (H > 0.0) sw -= gq * (double)t[q] * v * v / (2.0 * H);
+      }
+    }
+  }
+  if (g_c) g_c[i] = (float)sc;
+  if (g_w) g_w[i] = (float)sw;
+}
+
+// dL/dc0 = -sum_q g_q: one block, a fixed reduction order.
+__global__ void k_bwd_c0(const float* __restrict__ g, int64_t B, float* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < B; q += blockDim.x) s -= g[q];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (float)red[0];
+}
+
 }  // namespace
+
+hopf_status backward_params(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, const float* t,
+                            const float* dphidt, float* g_c, float* g_c0, float* g_w, cudaStream_t stream) {
+  const int n = h->n;
+  if (g_c || g_w) {
+    k_bwd_params<<<(n + 127) / 128, 128, 0, stream>>>(g_phi, vstar, t, dphidt, n, batch, h->h_kind, g_c, g_w);
+    HOPF_CUDA(cudaGetLastError());
+  }
+  if (g_c0) {
+    k_bwd_c0<<<1, 256, 0, stream>>>(g_phi, batch, g_c0);
+    HOPF_CUDA(cudaGetLastError());
+  }
+  return HOPF_OK;
+}
 
 hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,
                      float* g_A, cudaStream_t stream) {

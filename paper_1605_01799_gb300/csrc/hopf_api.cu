@@ -469,6 +469,26 @@ hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int6
   return union_closest_noalloc(parts, K, batch, x, s_tol, max_newton, dist, closest, argmin, newton, qstatus, stream);
 }
 
+hopf_status hopf_backward_params(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar,
+                                 const float* t, const float* dphidt, float* g_c, float* g_c0, float* g_w,
+                                 cudaStream_t stream) {
+  set_error("");
+  if (!h || batch < 0) return fail(HOPF_EINVAL, "hopf_backward_params: bad argument");
+  if (g_w && h->h_kind != HOPF_H_WL1 && h->h_kind != HOPF_H_DNORM)
+    return fail(HOPF_EUNSUPPORTED, "hopf_backward_params: g_w needs weights (HOPF_H_WL1 or HOPF_H_DNORM)");
+  if (batch == 0) {
+    if (g_c) HOPF_CUDA(cudaMemsetAsync(g_c, 0, sizeof(float) * h->n, stream));
+    if (g_w) HOPF_CUDA(cudaMemsetAsync(g_w, 0, sizeof(float) * h->n, stream));
+    if (g_c0) HOPF_CUDA(cudaMemsetAsync(g_c0, 0, sizeof(float), stream));
+    return HOPF_OK;
+  }
+  if (!g_phi || ((g_c || g_w) && !vstar)) return fail(HOPF_EINVAL, "hopf_backward_params: null g_phi or vstar");
+  if (g_w && !t) return fail(HOPF_EINVAL, "hopf_backward_params: g_w needs t");
+  if (g_w && h->h_kind == HOPF_H_DNORM && !dphidt)
+    return fail(HOPF_EINVAL, "hopf_backward_params: g_w for sqrt(sum w p^2) needs dphidt");
+  return backward_params(h, batch, g_phi, vstar, t, dphidt, g_c, g_c0, g_w, stream);
+}
+
 hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
                           float* g_t, float* g_A, cudaStream_t stream) {
   set_error("");

@@ -131,6 +131,8 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
 // ---- backward (backward.cu) ----
 hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,
                      float* g_A, cudaStream_t stream);
+hopf_status backward_params(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, const float* t,
+                            const float* dphidt, float* g_c, float* g_c0, float* g_w, cudaStream_t stream);
 
 int sm_count(int device);
 

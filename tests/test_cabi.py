@@ -192,3 +192,8 @@ def test_figure_grid_and_level_lines():
     phi = np.add.outer(np.arange(10.0), np.zeros(4))  # phi = row index
     img = F.to_pgm(phi, 5.0)
     assert (img[4] == 0).all() and (img[3] != 0).all()  # 4 -> 5 crosses a multiple of 5
+
+
+def test_backward_params_null_handle(hg):
+    L = hg.lib()
+    assert L.hopf_backward_params(None, 4, None, None, None, None, None, None, None, None) == hg.HOPF_EINVAL

@@ -99,3 +99,39 @@ def test_backward_fd_on_sampled_queries(hg, orc):
             fd = (phi_of(A + E) - phi_of(A - E)) / 2e-6
             expect = gA[i, j] * (1 if i == j else 2)
             assert abs(fd - expect) <= 2e-5 * max(1, abs(fd)), (q, i, j, fd, expect)
+
+
+@pytest.mark.parametrize("dense,hk", [(False, 1), (False, 4), (True, 1), (False, 2)])
+def test_parameter_gradients_match_oracle(hg, orc, dense, hk):
+    """dL/dc, dL/dc0 and dL/dw (weighted l1, sqrt(sum w p^2)) from the GPU's
+    minimisers against the oracle's formulas at the same minimisers (FP64
+    sums on both sides; the GPU's are FP32-rounded), and g_w refused for an
+    unweighted Hamiltonian."""
+    import torch
+    n, B = (128, 200) if dense else (40, 300)
+    seed = 12500 + 10 * hk + (100 if dense else 0)
+    A = wl.spd_matrix(seed, seed + 1, n)[0] if dense else wl.uniform(seed, n, 0.5, 2.0)
+    w = wl.uniform(seed + 2, n, 0.5, 1.5) if hk in (1, 4) else None
+    c = wl.normal(seed + 3, n, 1.0)
+    x = wl.normal(seed + 4, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(seed + 5, B, 0.1, 3.0).astype(np.float32)
+    g = wl.normal(seed + 6, B, 1.0).astype(np.float32)
+    h = hg.Hopf(A, hk, w=w, centre=c, tol=1e-13 if dense else 1e-12, max_iter=3000,
+                precision=hg.P_MIXED if dense else hg.P_FP32)
+    out = h.eval(_cuda(x), _cuda(t))
+    td = _cuda(t)
+    want_w = hk in (1, 4)
+    gc, gc0, gw = h.backward_params(_cuda(g), out["grad"], t=td, dphidt=out["dphidt"], want_w=want_w)
+    torch.cuda.synchronize()
+    v = out["grad"].cpu().numpy().astype(np.float64)
+    ref = orc.backward_params(n, hk, w, g.astype(np.float64), v, t.astype(np.float64))
+    scale = np.abs(ref["g_c"]).max()
+    assert np.abs(gc.cpu().numpy() - ref["g_c"]).max() <= 1e-5 * max(1.0, scale)
+    assert abs(float(gc0.cpu()) - ref["g_c0"]) <= 1e-5 * max(1.0, abs(ref["g_c0"]))
+    if want_w:
+        # (the GPU's H for sqrt(sum w p^2) is the forward's dphidt, FP32)
+        sw = np.abs(ref["g_w"]).max()
+        assert np.abs(gw.cpu().numpy() - ref["g_w"]).max() <= 2e-5 * max(1.0, sw)
+    else:
+        with pytest.raises(hg.HopfError):
+            h.backward_params(_cuda(g), out["grad"], t=td, want_w=True)
