@@ -50,7 +50,7 @@ typedef struct hopf_handle_s* hopf_handle;
 
 typedef enum {
   HOPF_OK = 0,
-  HOPF_EINVAL = 1,        /* bad argument (null pointer, size, t < 0, ...) */
+  HOPF_EINVAL = 1,        /* bad argument (null pointer, size, ...) */
   HOPF_ENOMEM = 2,        /* device allocation failed in hopf_create */
   HOPF_ECUDA = 3,         /* a CUDA runtime or driver call failed */
   HOPF_ENOTSPD = 4,       /* A + lambda I (or M of HOPF_H_ANORM) is not SPD */
@@ -94,8 +94,10 @@ enum { HOPF_P_FP64 = 0, HOPF_P_FP32 = 1, HOPF_P_BF16 = 2, HOPF_P_MIXED = 5 };
 enum { HOPF_STOP_PAPER = 0, HOPF_STOP_UREL = 1 };
 
 /* Per-query status bytes.  ABORTED: a bounded device-side wait of the dense
- * solver gave up (it never hangs); every query of that call carries it. */
-enum { HOPF_Q_OK = 0, HOPF_Q_NOT_CONVERGED = 1, HOPF_Q_NONFINITE = 2, HOPF_Q_ABORTED = 3 };
+ * solver gave up (it never hangs); every query of that call carries it.
+ * BAD_INPUT: the query's t is negative or NaN (t lives on the device, so the
+ * call cannot refuse it); its outputs carry no meaning. */
+enum { HOPF_Q_OK = 0, HOPF_Q_NOT_CONVERGED = 1, HOPF_Q_NONFINITE = 2, HOPF_Q_ABORTED = 3, HOPF_Q_BAD_INPUT = 4 };
 
 /* Problem description for hopf_create (host memory, copied).
  *   n          dimension, 1 <= n <= 8192 (diagonal) or 4096 (dense)
@@ -151,7 +153,8 @@ hopf_status hopf_workspace_size(hopf_handle h, int64_t batch, size_t* bytes);
  *   dphidt  [batch] float: -H(grad), device, may be NULL
  *   iters   [batch] int32: split Bregman iterations, device, may be NULL
  *   qstatus [batch] uint8: HOPF_Q_*, device, may be NULL
- * t must be >= 0; t = 0 gives phi = J(x) (eq. 1.1b).  The split Bregman start
+ * t must be >= 0 (a query with t < 0 or NaN reports HOPF_Q_BAD_INPUT); t = 0
+ * gives phi = J(x) (eq. 1.1b).  The split Bregman start
  * is v^0 = d^0 = x - c, b^0 = 0 (Section 3.1). */
 hopf_status hopf_eval(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
                       float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace, size_t ws_bytes,

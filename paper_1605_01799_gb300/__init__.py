@@ -25,7 +25,7 @@ J_QUAD, J_L1SQ, J_LINFSQ = 0, 2, 3
 H_L1, H_WL1, H_L2, H_LINF, H_DNORM, H_ANORM = 0, 1, 2, 3, 4, 5  # H_ANORM: w = M (n x n)
 P_FP64, P_FP32, P_BF16, P_MIXED = 0, 1, 2, 5
 STOP_PAPER, STOP_UREL = 0, 1
-Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED = 0, 1, 2, 3
+Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED, Q_BAD_INPUT = 0, 1, 2, 3, 4
 
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",

@@ -15,7 +15,7 @@ namespace hopf {
 enum : int { H_L1 = 0, H_WL1 = 1, H_L2 = 2, H_LINF = 3, H_DNORM = 4, H_ANORM = 5 };
 enum : int { J_QUAD = 0, J_L1SQ = 2, J_LINFSQ = 3 };
 enum : int { STOP_PAPER = 0, STOP_UREL = 1 };
-enum : uint8_t { Q_OK = 0, Q_NOT_CONVERGED = 1, Q_NONFINITE = 2, Q_ABORTED = 3 };
+enum : uint8_t { Q_OK = 0, Q_NOT_CONVERGED = 1, Q_NONFINITE = 2, Q_ABORTED = 3, Q_BAD_INPUT = 4 };
 
 // Error words a kernel can leave in its device error flag (never a trap).
 enum : int { ERR_NONE = 0, ERR_BARRIER_TIMEOUT = 1, ERR_MBAR_TIMEOUT = 2, ERR_NOT_SPD = 3, ERR_TMEM = 4 };

@@ -147,6 +147,7 @@ __global__ void k_dense_finalize(const double* __restrict__ fpart, const int* __
   if (qstatus) {
     uint8_t st = qdone[q] == 1 ? Q_OK : Q_NOT_CONVERGED;
     if (!isfinite(p)) st = Q_NONFINITE;
+    if (!(tq[q] >= 0.f)) st = Q_BAD_INPUT;  // t < 0 or NaN
     if (*err != ERR_NONE) st = Q_ABORTED;
     qstatus[q] = st;
   }

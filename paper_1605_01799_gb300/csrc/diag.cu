@@ -50,7 +50,8 @@ __device__ void emit(const DiagEvalArgs<T>& A, Query<T, G, VPT>& Q, int64_t q, T
     A.phi[q] = phi;
     if (A.dphidt) A.dphidt[q] = (T)(-H);
     if (A.iters) A.iters[q] = k;
-    if (A.qstatus) A.qstatus[q] = !finite ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED);
+    if (A.qstatus)
+      A.qstatus[q] = !(tq >= T(0)) ? Q_BAD_INPUT : (!finite ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED));
   }
 }
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(block_of<G>()) k_union_pick(UnionArgs U) {
     U.phi[q] = bv;
     U.argmin[q] = best;
     if (U.iters) U.iters[q] = U.it_parts[q * U.K + best];
-    if (U.qstatus) U.qstatus[q] = U.st_parts[q * U.K + best];
+    if (U.qstatus) U.qstatus[q] = !(U.t[q] >= 0.f) ? Q_BAD_INPUT : U.st_parts[q * U.K + best];
   }
 }
 

@@ -152,3 +152,40 @@ def test_paper_tables_protocol_fp64(hg, orc, j, h_kind, n):
     g = out["grad"].cpu().numpy()
     assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"])))[same].max() <= 1e-10
     assert np.abs(g - ref["grad"])[same].max() <= 1e-8
+
+
+@pytest.mark.parametrize("path", ["diag", "dense", "union"])
+def test_negative_or_nan_time_is_flagged(hg, path):
+    """A query whose t is negative or NaN reports HOPF_Q_BAD_INPUT; the
+    other queries of the call are unaffected (bit-identical to a call
+    without the bad ones)."""
+    import torch
+    n, B = 64, 40
+    x = wl.normal(15001, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(15002, B, 0.1, 2.0).astype(np.float32)
+    bad = t.copy()
+    bad[3], bad[17] = -0.5, np.nan
+    a = wl.uniform(15003, n, 0.5, 2.0)
+    if path == "dense":
+        A = wl.spd_matrix(15004, 15005, n)[0]
+        h = hg.Hopf(A, hg.H_L1, tol=1e-13, max_iter=3000, precision=hg.P_MIXED)
+        run = lambda tt: h.eval(_cuda(x), _cuda(tt))
+    elif path == "diag":
+        h = hg.Hopf(a, hg.H_L2, tol=1e-12, max_iter=3000, precision=hg.P_FP32)
+        run = lambda tt: h.eval(_cuda(x), _cuda(tt))
+    else:
+        parts = [hg.Hopf(a, hg.H_L2, centre=wl.normal(15006 + i, n, 1.0), tol=1e-12, max_iter=3000,
+                         precision=hg.P_FP32) for i in range(3)]
+        run = lambda tt: hg.union_eval(parts, _cuda(x), _cuda(tt))
+    good = run(t)
+    torch.cuda.synchronize()
+    g_phi, g_st = good["phi"].cpu().numpy(), good["status"].cpu().numpy()
+    out = run(bad)
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    assert st[3] == hg.Q_BAD_INPUT and st[17] == hg.Q_BAD_INPUT
+    keep = np.ones(B, bool)
+    keep[[3, 17]] = False
+    assert (st[keep] == g_st[keep]).all()
+    if path != "dense":  # one query per group: the others' iterates are untouched
+        assert np.array_equal(out["phi"].cpu().numpy()[keep], g_phi[keep])
