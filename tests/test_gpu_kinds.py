@@ -372,3 +372,28 @@ def test_control_with_norm_initial_data(hg, jk, hk):
             assert (np.abs(pq[~top]) <= 2e-3 * scale[q]).all(), q
             assert (pq[top] * np.sign(yq[top]) >= -2e-3 * scale[q]).all(), q
             assert abs(np.abs(pq).sum() - li) <= 2e-3 * scale[q], q
+
+
+def test_golden_norm_kinds_on_the_gpu(hg):
+    """FP64 GPU evaluations of the hand-checkable Hopf-Lax closed forms in
+    tests/golden/section4_norm_kinds.txt."""
+    import os
+    import torch
+    path = os.path.join(os.path.dirname(__file__), "golden", "section4_norm_kinds.txt")
+    spec = {0: (np.ones, hg.H_LINF, hg.J_QUAD), 1: (None, hg.H_L1, hg.J_LINFSQ), 2: (None, hg.H_LINF, hg.J_L1SQ)}
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        v = [float(s) for s in line.split()]
+        kind, n = int(v[0]), int(v[1])
+        x = np.array(v[2:2 + n])
+        t, phi = v[2 + n], v[3 + n]
+        g = np.array(v[4 + n:4 + 2 * n])
+        mk, hk, jk = spec[kind]
+        h = hg.Hopf(mk(n) if mk else None, hk, c0=0.0, tol=1e-28, max_iter=200000, precision=hg.P_FP64,
+                    stop_rule=hg.STOP_UREL, j_kind=jk, n=n)
+        out = h.eval(_cuda(x[None]), _cuda(np.array([t])))
+        torch.cuda.synchronize()
+        assert abs(float(out["phi"][0]) - phi) <= 1e-9 * max(1, abs(phi)), (kind, x)
+        assert np.abs(out["grad"].cpu().numpy()[0] - g).max() <= 1e-6, (kind, x)
+        h.close()

@@ -706,3 +706,32 @@ def test_parameter_gradients_against_finite_differences(orc, hk):
     fd0 = (L(c0=0.5 + h) - L(c0=0.5 - h)) / (2 * h)
     assert abs(fd0 - bp["g_c0"]) <= 1e-8
     assert bp["g_w"] is None if hk == "l2" else bp["g_w"] is not None
+
+
+def _norm_golden():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "section4_norm_kinds.txt")):
+        if line.startswith("#"):
+            continue
+        v = [float(s) for s in line.split()]
+        kind, n = int(v[0]), int(v[1])
+        x = np.array(v[2:2 + n])
+        t, phi = v[2 + n], v[3 + n]
+        g = np.array(v[4 + n:4 + 2 * n])
+        rows.append((kind, x, t, phi, g))
+    return rows
+
+
+def test_golden_norm_kinds(orc):
+    """The oracle against hand-checkable Hopf-Lax closed forms of the norm
+    kinds (tests/golden/section4_norm_kinds.txt, written by make_golden.py from
+    the closed forms, not from the oracle)."""
+    spec = {0: (np.ones, orc.H_LINF, None), 1: (None, orc.H_L1, orc.J_LINFSQ), 2: (None, orc.H_LINF, orc.J_L1SQ)}
+    for kind, x, t, phi, g in _norm_golden():
+        n = len(x)
+        mk, hk, jk = spec[kind]
+        P = orc.Problem(mk(n) if mk else None, hk, c0=0.0, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL,
+                        j_kind=jk, n=n)
+        r = P.eval(x[None], [t])
+        assert abs(r["phi"][0] - phi) <= 1e-9 * max(1, abs(phi)), (kind, x, r["phi"][0], phi)
+        assert np.abs(r["grad"][0] - g).max() <= 1e-6, (kind, x, r["grad"][0], g)
