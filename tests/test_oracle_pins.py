@@ -735,3 +735,40 @@ def test_golden_norm_kinds(orc):
         r = P.eval(x[None], [t])
         assert abs(r["phi"][0] - phi) <= 1e-9 * max(1, abs(phi)), (kind, x, r["phi"][0], phi)
         assert np.abs(r["grad"][0] - g).max() <= 1e-6, (kind, x, r["grad"][0], g)
+
+
+@pytest.mark.parametrize("h", ["linf", "dnorm", "anorm"])
+def test_control_for_the_section4_hamiltonians(orc, h):
+    """The control of P9 for l_inf, sqrt(sum w p^2) and sqrt(<p, M p>):
+    <beta, p> = H(p), beta in the dual unit ball (|beta|_1 <= 1,
+    sum beta^2 / w <= 1, <beta, M^-1 beta> <= 1), and x - t beta attains phi
+    (Hopf-Lax)."""
+    n, B = 8, 16
+    rng = np.random.default_rng(71)
+    a = wl.uniform(9501, n, 0.5, 2.0)
+    c = wl.normal(9502, n, 0.5)
+    x = wl.normal(9503, B * n, 2.0).reshape(B, n)
+    t = wl.uniform(9504, B, 0.2, 2.0)
+    if h == "linf":
+        kind, w = orc.H_LINF, None
+        dual = lambda b: np.abs(b).sum()
+    elif h == "dnorm":
+        kind, w = orc.H_DNORM, wl.uniform(9505, n, 0.5, 1.5)
+        dual = lambda b: np.sqrt((b * b / w).sum())
+    else:
+        Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+        w = (Q * rng.uniform(0.3, 3.0, n)) @ Q.T
+        Minv = np.linalg.inv(w)
+        kind = orc.H_ANORM
+        dual = lambda b: np.sqrt(b @ Minv @ b)
+    P = orc.Problem(a, kind, w=w, centre=c, tol=1e-30, max_iter=200000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    ctl = orc.control(P, x, t, r["grad"])
+    for q in range(B):
+        p, beta = r["grad"][q], ctl["beta"][q]
+        Hp = P.H(p)
+        assert abs(beta @ p - Hp) <= 1e-7 * max(1.0, Hp)
+        assert dual(beta) <= 1 + 1e-7
+        z = ctl["x_T"][q] - c
+        J = 0.5 * (z * z / a).sum() - 0.5
+        assert abs(J - r["phi"][q]) <= 1e-7 * max(1.0, abs(r["phi"][q]))
