@@ -234,15 +234,16 @@ struct Smem {
   uint64_t cfull[2], cempty[2];  // final pass: hand-off of the D1 chunks
   uint32_t tmem_base;
   int abort;
-  int epi_abort;  // snapshot of abort read by all epilogue warps after a barrier
-  int first;
-  int cnt[4];  // active slots per warp of the decision (row tile 0)
-  alignas(16) float qtau[BN];
-  alignas(16) float qscale[BN];
-  int qact[BN];
-  int qid[BN];
+  // [2]: by item parity in the per-iteration epilogues (slot 0 in the final
+  // pass and the compaction)
+  int epi_abort[2];  // snapshot of abort read by all epilogue warps after a barrier
+  int cnt[2][4];     // active slots per warp of the decision (row tile 0)
+  alignas(16) float qtau[2][BN];
+  alignas(16) float qscale[2][BN];
+  int qact[2][BN];
+  int qid[2][BN];
   int base[1024];  // compaction: first new slot of each column tile
-  float red[2][4][BN][2];  // by item parity: an item's row sums are read after the next item's first barrier
+  float red[2][4][BN][2];  // by item parity: an item's row sums are read after the next item's barrier
   double redd[4][BN][2];
 };
 
@@ -473,10 +474,9 @@ struct EpiState {
 __device__ void epi_stage_final(const TcArgs& a, Smem& S, int c, int et) {
   if (et >= BN) return;
   const int64_t q = (int64_t)c * BN + et;
-  S.qtau[et] = a.tau[q];
-  S.qscale[et] = a.sfin[q];
-  S.qact[et] = q < a.B;
-  if (et == 0) S.first = 0;
+  S.qtau[0][et] = a.tau[q];
+  S.qscale[0][et] = a.sfin[q];
+  S.qact[0][et] = q < a.B;
 }
 
 // Transpose-reduce over 16 columns: lane L holds v[0..15] (one value per
@@ -595,9 +595,12 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   float pf_tau = 0.f, pf_sc = 1.f;
   int pf_act = 0, pf_qid = 0;
   if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
-  // phases B and P: an item's row sums go to the partial-sum array after the
-  // next item's first barrier (or after the loop), which saves a barrier
-  int ipar = 0, prev_par = 0, prev_r = 0, prev_c = -1;
+  // One named barrier per item: the shared query data and row sums are
+  // double-buffered by item parity ib.  A warp that writes item i + 1's has
+  // passed item i's barrier, so every warp has finished reading item i - 1's.
+  // Phases B and P: an item's row sums go to the partial-sum array after the
+  // next item's barrier (or after the loop).
+  int ib = 0, prev_par = 0, prev_r = 0, prev_c = -1;
   bool prev_on = false;
   auto flush_part = [&]() {
     if (prev_c >= 0 && prev_on) {
@@ -618,14 +621,12 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     const uint32_t buf = st.nb;
     st.nb ^= 1;
     const uint32_t use = st.uf[buf]++;
-    epi_sync();  // previous item's readers of the shared query data are done
     const bool record = ph != PH_B && r == 0;  // row tile 0 records decision k
     if (et < BN) {
-      if constexpr (ph != PH_A) flush_part();
-      S.qtau[et] = pf_tau;
-      S.qscale[et] = pf_sc;
-      S.qact[et] = pf_act;
-      S.qid[et] = pf_qid;
+      S.qtau[ib][et] = pf_tau;
+      S.qscale[ib][et] = pf_sc;
+      S.qact[ib][et] = pf_act;
+      S.qid[ib][et] = pf_qid;
       if (record) {
         const int64_t sl = (int64_t)c * BN + et;
         a.qact[cb][x.par][sl] = pf_act >= 2 ? 2 : pf_act;
@@ -635,20 +636,20 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
           a.sfin[pf_qid] = pf_sc;
         }
         const int cnt = __reduce_add_sync(0xffffffffu, pf_act == 1 ? 1 : 0);
-        if ((et & 31) == 0) S.cnt[et >> 5] = cnt;
+        if ((et & 31) == 0) S.cnt[ib][et >> 5] = cnt;
       }
       // one lane in 32 asks for each 128-byte line of the next item's slot data
       if (it_next < items && (et & 31) == 0)
         slot_prefetch(a, x, ph, (int64_t)(it_next / a.rt) * BN + et);
     }
-    if (et == 0) {
-      S.first = k == 1;
-      S.epi_abort = S.abort;
-    }
+    if (et == 0) S.epi_abort[ib] = S.abort;
     epi_sync();
-    if (S.epi_abort) return;  // the same decision in all epilogue warps
+    if (S.epi_abort[ib]) return;  // the same decision in all epilogue warps
+    if constexpr (ph != PH_A) {
+      if (et < BN) flush_part();
+    }
     if (record && et == 0) {
-      const int tot = S.cnt[0] + S.cnt[1] + S.cnt[2] + S.cnt[3];
+      const int tot = S.cnt[ib][0] + S.cnt[ib][1] + S.cnt[ib][2] + S.cnt[ib][3];
       if (tot) {
         a.tile_cnt[c] = tot;
         a.tile_k[c] = k;
@@ -658,7 +659,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     const int row = r * BM + rloc;
     const float wr = a.w[row];
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
-    const bool first = S.first;
+    const bool first = k == 1;
     // The state a chunk reads from global memory does not depend on this
     // item's products: the first chunk's loads go out before the wait for
     // the accumulator, each later chunk's when its predecessor is done.
@@ -667,7 +668,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     float uu[16], yy[16];
     uint32_t am = 0, rm = 0;
     auto load = [&](int j0) {
-      const int qa = lane < 16 ? S.qact[j0 + (lane & 15)] : 0;
+      const int qa = lane < 16 ? S.qact[ib][j0 + (lane & 15)] : 0;
       am = __ballot_sync(0xffffffffu, qa == 1);
       rm = ph == PH_B ? 0u : __ballot_sync(0xffffffffu, qa >= 2);
       const int64_t col0 = ((int64_t)c * BN + j0) * np + row;
@@ -700,7 +701,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         // a stopping slot leaves its u^{k-1} row segment in the final array
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj)
-          if (rm >> jj & 1u) a.ufin[(int64_t)S.qid[j0 + jj] * np + row] = uu[jj];
+          if (rm >> jj & 1u) a.ufin[(int64_t)S.qid[ib][j0 + jj] * np + row] = uu[jj];
       }
       if constexpr (ph == PH_A) {
         // b = u - prox(u) in place of u, column by column (the branches are
@@ -712,7 +713,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         } else if (hk == H_L2) {
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
-            const float4 s4 = *reinterpret_cast<const float4*>(&S.qscale[j0 + 4 * q4]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&S.qscale[ib][j0 + 4 * q4]);
             const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -723,7 +724,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         } else {
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
-            const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[j0 + 4 * q4]);
+            const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[ib][j0 + 4 * q4]);
             const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) uu[4 * q4 + e] -= shrink1(uu[4 * q4 + e], tv[e] * wr);
@@ -744,7 +745,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         const bool l2 = hk == H_L2;
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[j0 + 4 * q4]);
+          const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[ib][j0 + 4 * q4]);
           const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -766,8 +767,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         transpose_reduce16(d1, lane);
         transpose_reduce16(uu, lane);
         if (lane < 16) {
-          S.red[ipar][qd][j0 + lane][0] = d1[0];
-          S.red[ipar][qd][j0 + lane][1] = uu[0];
+          S.red[ib][qd][j0 + lane][0] = d1[0];
+          S.red[ib][qd][j0 + lane][1] = uu[0];
         }
       } else if constexpr (ph == PH_P) {
         float* U = a.u[cb] + col0;
@@ -777,8 +778,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
           float du = 0.f, un = 0.f;
           if (am >> jj & 1u) {
             const int j = j0 + jj;
-            const float tau = S.qtau[j];
-            const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, S.qscale[j], hk);
+            const float tau = S.qtau[ib][j];
+            const float p = first ? yy[jj] : prox1(uu[jj], wr, tau, S.qscale[ib][j], hk);
             un = d1[jj] + uu[jj] - p;
             du = un - uu[jj];
             const float pn = prox1(un, wr, tau, 1.f, hk);
@@ -791,8 +792,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         transpose_reduce16(d1, lane);
         transpose_reduce16(uu, lane);
         if (lane < 16) {
-          S.red[ipar][qd][j0 + lane][0] = d1[0];
-          S.red[ipar][qd][j0 + lane][1] = uu[0];
+          S.red[ib][qd][j0 + lane][0] = d1[0];
+          S.red[ib][qd][j0 + lane][1] = uu[0];
         }
       }
     }
@@ -802,15 +803,15 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
     ++st.ue[buf];
     if constexpr (ph != PH_A) {
-      prev_on = et < BN && S.qact[et] == 1;
+      prev_on = et < BN && S.qact[ib][et] == 1;
       prev_c = c;
       prev_r = r;
-      prev_par = ipar;
-      ipar ^= 1;
+      prev_par = ib;
     }
     // the next item's slot data (and decision), from lines asked for above
     if (et < BN && it_next < items) slot_data(a, x, ph, (int64_t)(it_next / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
     it = it_next;
+    ib ^= 1;
   }
   if constexpr (ph != PH_A) {
     epi_sync();
@@ -833,9 +834,9 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     if (!tile_on(a, x, PH_F, c)) continue;
     epi_sync();
     epi_stage_final(a, S, c, et);
-    if (et == 0) S.epi_abort = S.abort;
+    if (et == 0) S.epi_abort[0] = S.abort;
     epi_sync();
-    if (S.epi_abort) return;
+    if (S.epi_abort[0]) return;
     const uint32_t lanebase = S.tmem_base + ((uint32_t)(qd * 32) << 16);
     // promote each 128-wide K chunk of D1 into FP32 registers (round to nearest)
     float acc[CPW];
@@ -885,12 +886,12 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
         // A p = D1 + 2^-11 D2 + 2^-22 D3
         const float ap = acc[16 * g + jj] + (d2[jj] + d3[jj] * (1.f / kLoScale)) * (1.f / kLoScale);
         double f0 = 0.0, f1 = 0.0;
-        if (S.qact[j]) {
+        if (S.qact[0][j]) {
           const int64_t q = (int64_t)c * BN + j;
           const int64_t off = q * np + row;
           const float uu = a.ufin[off];
           const float yy = row < a.n ? a.x[q * a.n + row] - a.cf[row] : 0.f;  // y = x - c, as at the start
-          const float p = prox1(uu, wr, S.qtau[j], S.qscale[j], hk);
+          const float p = prox1(uu, wr, S.qtau[0][j], S.qscale[0][j], hk);
           const double pd = p;
           f0 = (double)yy * pd - 0.5 * pd * (double)ap;
           f1 = hk == H_L2 ? pd * pd : (double)wr * fabs(pd);
@@ -899,7 +900,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
             if (a.beta) {
               // control (y - A p) / t = (u - p) / tau at the fixed point, an
               // element of dH(p) by the prox (u - prox(u) in tau dH)
-              const float tau = S.qtau[j];
+              const float tau = S.qtau[0][j];
               const float bt = tau > 0.f ? (uu - p) / tau : 0.f;
               a.beta[q * a.n + row] = bt;
               if (a.xfin) a.xfin[q * a.n + row] = a.x[q * a.n + row] - tau * a.lam * bt;
@@ -965,7 +966,7 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
       epi_sync_half();
       int rank = __popc(m & ((1u << (et & 31)) - 1u));
       for (int wv = 0; wv < (et >> 5); ++wv) rank += __float_as_int(S.red[0][wv][1][0]);
-      S.qact[et] = act ? S.base[c] + rank : -1;  // destination slot
+      S.qact[0][et] = act ? S.base[c] + rank : -1;  // destination slot
       if (act) {
         const int d = S.base[c] + rank;
         a.sq[nb][d] = a.sq[cb][sl];
@@ -990,7 +991,7 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
         dst[b] = -1;
         if (e >= total) continue;
         const int j = e / per_row, i = (e - j * per_row) * 4;
-        const int d = S.qact[j];
+        const int d = S.qact[0][j];
         if (d < 0) continue;
         const int64_t so = ((int64_t)c * BN + j) * np + i;
         dst[b] = (int64_t)d * np + i;
