@@ -175,9 +175,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "dense_wl1_n%d" % args.n, "n": args.n, "batch_per_step": per_step,
-                       "note": "FP64 C oracle (plain loops, OpenMP over queries) on a bounded sample per step; "
-                        "the factorisation of A + lambda I is timed apart and excluded"},
+            "config": {"workload": "dense_wl1_n%d_b%d" % (args.n, args.batch), "n": args.n,
+                       "batch_per_gpu": args.batch, "sample_per_step": per_step, "tol_urel": TOL,
+                       "max_iter": MAX_ITER,
+                       "note": "FP64 C oracle (plain loops, OpenMP over queries) on a bounded sample of the "
+                               "workload's queries per step; the factorisation of A + lambda I is timed apart "
+                               "and excluded"},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": threads, "kind": "oracle",
                              "sample": "%d queries of the n=%d workload per step" % (per_step, args.n)},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -78,6 +78,8 @@ def test_reference_arm_prints_on_rank_zero_only():
     line = json.loads(outs[0][0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+    # the same workload name as the GPU arm's line at these sizes
+    assert line["config"]["workload"] == "dense_wl1_n64_b65536"
 
 
 def test_generator_offsets_slice_one_stream():
