@@ -19,6 +19,8 @@ the Hamiltonian min_i H_i, the new proxes against numerical minimisation of
 their definitions, closed forms through Hopf-Lax projections for J = 1/2|x|^2
 with H = l_inf and sqrt(sum w p^2), and brute-force Hopf objectives at n = 2
 for the non-quadratic initial data (with lambda != 1).  Parity unpinned: iteration counts (the paper prints none).
+``tests/test_oracle_mutants.py`` plants plausible mistakes one at a time in a
+scratch copy of the C source and checks that the pins named for each fail.
 """
 import ctypes
 import os

@@ -1,0 +1,112 @@
+"""Planted mistakes in the oracle: each pin set must catch its mutant.
+
+The oracle is trusted because independent pins (closed forms, KKT and
+duality certificates, brute-force Hopf-Lax minimisation, finite differences)
+agree with it.  This file checks that the pins would notice a plausible
+mistake: each case copies the oracle, the tests and the input generators to a
+scratch directory, plants one mistake in the copy of ``hopf_oracle.c`` (a
+dropped term, a wrong sign, scale or index, a transposed operand, a swapped
+min and max), rebuilds it there and runs the named pins, which must fail.
+The copy in the repository is never touched, and nothing here runs on a GPU.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, text in hopf_oracle.c, planted replacement, pins that must fail (-k))
+MUTANTS = [
+    # split Bregman, eq. 3.4(a)-(c)
+    ("vupdate_drops_lambda", "tmp[i] = y[i] + lam * (d[i] - b[i]);", "tmp[i] = y[i] + (d[i] - b[i]);",
+     "test_paper_example_l1_ellipsoid"),
+    ("tau_is_t", "const double lam = p->lambda, tau = t / p->lambda;", "const double lam = p->lambda, tau = t;",
+     "test_paper_example_l1_ellipsoid"),
+    ("bregman_sign", "b[i] = b[i] + v[i] - dn[i];", "b[i] = b[i] - v[i] + dn[i];",
+     "test_workload1_closed_form"),
+    ("gradient_is_v", "for (int i = 0; i < n; ++i) grad[i] = d[i];", "for (int i = 0; i < n; ++i) grad[i] = v[i];",
+     "test_dense_wl1_kkt_certificate"),
+    # the factorisation of A + lambda I and its solve
+    ("factor_drops_lambda", "double s = A[(int64_t)i * n + j] + (i == j ? lambda : 0.0);",
+     "double s = A[(int64_t)i * n + j];", "test_dense_wl1_kkt_certificate"),
+    ("backsolve_transposed", "for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * v[k];",
+     "for (int k = i + 1; k < n; ++k) s -= L[(int64_t)i * n + k] * v[k];", "test_dense_wl1_kkt_certificate"),
+    # the objective of eq. 3.3 and the outputs
+    ("c0_sign", "return s - 0.5 * quad_A(p, v) - p->c0", "return s - 0.5 * quad_A(p, v) + p->c0",
+     "test_paper_example_sphere"),
+    ("centre_dropped", "s += (x[i] - (p->c ? p->c[i] : 0.0)) * v[i];", "s += x[i] * v[i];",
+     "test_weighted_l1_with_centre"),
+    ("dphidt_sign", "res->dphidt = -orc_H(p->h_kind, n, p->w, d);", "res->dphidt = orc_H(p->h_kind, n, p->w, d);",
+     "test_time_derivative_and_gradient_fd"),
+    # the proxes (Sections 1, 4.2-4.4)
+    ("weights_ignored", "double a = tau * (h_kind == ORC_H_WL1 && w ? w[i] : 1.0);", "double a = tau;",
+     "test_weighted_l1_with_centre"),
+    ("shrink2_half_tau", "double m = nz - tau > 0.0 ? nz - tau : 0.0;",
+     "double m = nz - 0.5 * tau > 0.0 ? nz - 0.5 * tau : 0.0;", "test_paper_example_sphere"),
+    ("linf_H_is_l1", "for (int i = 0; i < n; ++i) s = fabs(q[i]) > s ? fabs(q[i]) : s;\n        return s;\n    }\n    if (h_kind == ORC_H_DNORM)",
+     "for (int i = 0; i < n; ++i) s += fabs(q[i]);\n        return s;\n    }\n    if (h_kind == ORC_H_DNORM)",
+     "test_l2sq_initial_data_closed_forms_new_H"),
+    ("l1ball_mu_off_by_one", "const double mu = (S - radius) / k;", "const double mu = (S - radius) / (k + 1);",
+     "test_new_prox_against_their_definition"),
+    ("ellipsoid_prox_is_projection", "out[i] = z[i] * mu / (s2[i] + mu);", "out[i] = z[i] * s2[i] / (s2[i] + mu);",
+     "test_new_prox_against_their_definition"),
+    ("ellipsoid_radius_not_squared", "s2[i] = tau * tau * w[i];", "s2[i] = tau * w[i];",
+     "test_new_prox_against_their_definition"),
+    ("anorm_rotation_transposed", "for (int i = 0; i < n; ++i) s += P[(int64_t)i * n + k] * z[i];",
+     "for (int i = 0; i < n; ++i) s += P[(int64_t)k * n + i] * z[i];", "test_anorm_prox_against_its_definition"),
+    ("l1sq_beta_drops_alpha", "const double beta = alpha * S / (1.0 + alpha * k);",
+     "const double beta = alpha * S / (1.0 + k);", "test_l1sq_beta_fixed_point_including_ties"),
+    ("breakpoints_ascending", "return x < y ? 1 : (x > y ? -1 : 0);", "return x < y ? -1 : (x > y ? 1 : 0);",
+     "test_l1sq_beta_fixed_point_including_ties"),
+    # the non-quadratic initial data of Section 4.4
+    ("jstar_moreau_swap", "p->a_kind == ORC_J_LINFSQ ? alpha : 1.0 / alpha, tmp);",
+     "p->a_kind == ORC_J_LINFSQ ? 1.0 / alpha : alpha, tmp);", "test_nonquadratic_initial_data_bruteforce_n2"),
+    ("jstar_linf_not_squared", "for (int i = 0; i < p->n; ++i) s = fabs(v[i]) > s ? fabs(v[i]) : s;\n        return s * s;",
+     "for (int i = 0; i < p->n; ++i) s = fabs(v[i]) > s ? fabs(v[i]) : s;\n        return s;",
+     "test_nonquadratic_initial_data_bruteforce_n2"),
+    # unions, the maximum over Hamiltonians, the level-set distance (Sections 2.2, 3.2)
+    ("union_takes_max", "double best = INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L[i], x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi < best) {",
+     "double best = -INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L[i], x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi > best) {",
+     "test_union_min_rule"),
+    ("maxH_takes_min", "double best = -INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L, x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi > best) {",
+     "double best = INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L, x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi < best) {",
+     "test_max_over_hamiltonians_solves_the_min_hamiltonian_pde"),
+    ("newton_step_scaled", "double ds = r.phi / gn;", "double ds = r.phi / gn / gn;",
+     "test_closest_point_against_ellipsoid_projection"),
+    ("projection_sign", "for (int i = 0; i < n; ++i) proj[i] = y[i] - s * g[i] / gn;",
+     "for (int i = 0; i < n; ++i) proj[i] = y[i] + s * g[i] / gn;", "test_closest_point_against_ellipsoid_projection"),
+    # gradients with respect to the data, and the control
+    ("gA_drops_half", "g_A[(int64_t)i * n + j] -= 0.5 * g_phi[q] * v[i] * v[j];",
+     "g_A[(int64_t)i * n + j] -= g_phi[q] * v[i] * v[j];", "test_backward_envelope_fd"),
+    ("gw_dnorm_drops_half", "g_w[i] -= g_phi[q] * t[q] * v[i] * v[i] / (2.0 * H);",
+     "g_w[i] -= g_phi[q] * t[q] * v[i] * v[i] / H;", "test_parameter_gradients_against_finite_differences"),
+    ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
+     "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
+]
+
+
+def _scratch_copy(dst):
+    ign = shutil.ignore_patterns("_build", "__pycache__")
+    for d in ("oracle", "tests", "workloads"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d), ignore=ign)
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins):
+    _scratch_copy(str(tmp_path))
+    src = os.path.join(str(tmp_path), "oracle", "hopf_oracle.c")
+    text = open(src).read()
+    assert text.count(old) == 1, "the mutated text must occur exactly once in hopf_oracle.c"
+    open(src, "w").write(text.replace(old, new))
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q", "-p",
+                        "no:cacheprovider", "-k", pins], cwd=str(tmp_path), env=env, capture_output=True,
+                       text=True, timeout=600)
+    # exit code 1: tests ran and at least one failed (2-5 would be an
+    # interruption, an internal error, a usage error or no test selected)
+    assert r.returncode == 1, "%s: pins %r did not fail (exit %d)\n%s" % (name, pins, r.returncode,
+                                                                             r.stdout[-1500:])
+    assert " failed" in r.stdout.splitlines()[-1]
