@@ -29,6 +29,8 @@ MUTANTS = [
      "test_workload1_closed_form"),
     ("gradient_is_v", "for (int i = 0; i < n; ++i) grad[i] = d[i];", "for (int i = 0; i < n; ++i) grad[i] = v[i];",
      "test_dense_wl1_kkt_certificate"),
+    ("diag_solve_drops_lambda", "v[i] = r[i] / (p->A[i] + p->lambda);", "v[i] = r[i] / p->A[i];",
+     "test_workload1_closed_form"),
     # the factorisation of A + lambda I and its solve
     ("factor_drops_lambda", "double s = A[(int64_t)i * n + j] + (i == j ? lambda : 0.0);",
      "double s = A[(int64_t)i * n + j];", "test_dense_wl1_kkt_certificate"),
@@ -39,11 +41,14 @@ MUTANTS = [
      "test_paper_example_sphere"),
     ("centre_dropped", "s += (x[i] - (p->c ? p->c[i] : 0.0)) * v[i];", "s += x[i] * v[i];",
      "test_weighted_l1_with_centre"),
+    ("jstar_diag_unweighted", "s += p->A[i] * v[i] * v[i];", "s += v[i] * v[i];", "test_workload1_closed_form"),
     ("dphidt_sign", "res->dphidt = -orc_H(p->h_kind, n, p->w, d);", "res->dphidt = orc_H(p->h_kind, n, p->w, d);",
      "test_time_derivative_and_gradient_fd"),
     # the proxes (Sections 1, 4.2-4.4)
     ("weights_ignored", "double a = tau * (h_kind == ORC_H_WL1 && w ? w[i] : 1.0);", "double a = tau;",
      "test_weighted_l1_with_centre"),
+    ("dnorm_H_not_rooted", "s += w[i] * q[i] * q[i];\n        return sqrt(s);", "s += w[i] * q[i] * q[i];\n        return s;",
+     "test_l2sq_initial_data_closed_forms_new_H"),
     ("shrink2_half_tau", "double m = nz - tau > 0.0 ? nz - tau : 0.0;",
      "double m = nz - 0.5 * tau > 0.0 ? nz - 0.5 * tau : 0.0;", "test_paper_example_sphere"),
     ("linf_H_is_l1", "for (int i = 0; i < n; ++i) s = fabs(q[i]) > s ? fabs(q[i]) : s;\n        return s;\n    }\n    if (h_kind == ORC_H_DNORM)",
@@ -76,6 +81,8 @@ MUTANTS = [
      "test_max_over_hamiltonians_solves_the_min_hamiltonian_pde"),
     ("newton_step_scaled", "double ds = r.phi / gn;", "double ds = r.phi / gn / gn;",
      "test_closest_point_against_ellipsoid_projection"),
+    ("closest_takes_farthest", "if (sb < best) {", "if (sb > best) {",
+     "test_closest_point_against_ellipsoid_projection"),
     ("projection_sign", "for (int i = 0; i < n; ++i) proj[i] = y[i] - s * g[i] / gn;",
      "for (int i = 0; i < n; ++i) proj[i] = y[i] + s * g[i] / gn;", "test_closest_point_against_ellipsoid_projection"),
     # gradients with respect to the data, and the control
@@ -83,6 +90,9 @@ MUTANTS = [
      "g_A[(int64_t)i * n + j] -= g_phi[q] * v[i] * v[j];", "test_backward_envelope_fd"),
     ("gw_dnorm_drops_half", "g_w[i] -= g_phi[q] * t[q] * v[i] * v[i] / (2.0 * H);",
      "g_w[i] -= g_phi[q] * t[q] * v[i] * v[i] / H;", "test_parameter_gradients_against_finite_differences"),
+    ("gc0_sign", "*g_c0 -= g_phi[q];", "*g_c0 += g_phi[q];", "test_parameter_gradients_against_finite_differences"),
+    ("control_drops_centre", "(xi - (p->c ? p->c[i] : 0.0) - ap) / t[q]", "(xi - ap) / t[q]",
+     "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
     ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
 ]
