@@ -197,3 +197,32 @@ def test_figure_grid_and_level_lines():
 def test_backward_params_null_handle(hg):
     L = hg.lib()
     assert L.hopf_backward_params(None, 4, None, None, None, None, None, None, None, None) == hg.HOPF_EINVAL
+
+
+def test_header_is_plain_c_and_links(hg, tmp_path):
+    """The boundary is usable from C: a C99 program that includes hopf.h and
+    takes the address of every declared entry point compiles with gcc and
+    links against the library (C linkage, no C++ types in the signatures)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not on PATH")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    names = declared_functions()
+    src = tmp_path / "use_hopf.c"
+    src.write_text('#include "hopf.h"\n#include <stdio.h>\ntypedef void (*fn)(void);\n'
+                   "static const fn entry[] = {\n" + ",\n".join("    (fn)%s" % n for n in names) + "\n};\n"
+                   "int main(void) {\n"
+                   "    printf(\"%d entry points\\n\", (int)(sizeof(entry) / sizeof(entry[0])));\n"
+                   "    return 0;\n}\n")
+    lib = hg.LIB_PATH
+    exe = tmp_path / "use_hopf"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                        "-I" + cuda_inc, str(src), lib, "-Wl,--allow-shlib-undefined", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    env = dict(os.environ, LD_LIBRARY_PATH=os.pathsep.join(
+        [os.path.dirname(lib), os.environ.get("LD_LIBRARY_PATH", "")]))
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "%d entry points" % len(names), (r.stdout, r.stderr)
