@@ -187,5 +187,35 @@ def test_negative_or_nan_time_is_flagged(hg, path):
     keep = np.ones(B, bool)
     keep[[3, 17]] = False
     assert (st[keep] == g_st[keep]).all()
-    if path != "dense":  # one query per group: the others' iterates are untouched
-        assert np.array_equal(out["phi"].cpu().numpy()[keep], g_phi[keep])
+    # queries are independent (dense: a query is one column of every product,
+    # and packing moves columns without changing their arithmetic)
+    assert np.array_equal(out["phi"].cpu().numpy()[keep], g_phi[keep])
+
+
+@pytest.mark.parametrize("path", ["diag", "dense"])
+def test_nonfinite_query_leaves_the_others_untouched(hg, path):
+    """A query with a NaN or an infinite coordinate reports
+    HOPF_Q_NONFINITE (or runs out of iterations) and every other query of
+    the call is bit-identical to a call without it."""
+    import torch
+    n, B = 64, 40
+    x = wl.normal(15101, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(15102, B, 0.1, 2.0).astype(np.float32)
+    bad = x.copy()
+    bad[5, 7], bad[21, 0] = np.nan, np.inf
+    if path == "dense":
+        A = wl.spd_matrix(15104, 15105, n)[0]
+        h = hg.Hopf(A, hg.H_WL1, w=wl.uniform(15106, n, 0.5, 1.5), tol=1e-13, max_iter=300, precision=hg.P_MIXED)
+    else:
+        h = hg.Hopf(wl.uniform(15103, n, 0.5, 2.0), hg.H_L2, tol=1e-12, max_iter=300, precision=hg.P_FP32)
+    good = h.eval(_cuda(x), _cuda(t))
+    out = h.eval(_cuda(bad), _cuda(t))
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    for q in (5, 21):
+        assert st[q] in (hg.Q_NONFINITE, hg.Q_NOT_CONVERGED), (q, st[q])
+        assert not np.isfinite(out["phi"].cpu().numpy()[q]) or st[q] == hg.Q_NOT_CONVERGED
+    keep = np.ones(B, bool)
+    keep[[5, 21]] = False
+    for key in ("phi", "grad", "iters", "status"):
+        assert np.array_equal(out[key].cpu().numpy()[keep], good[key].cpu().numpy()[keep]), key
