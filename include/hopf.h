@@ -96,7 +96,11 @@ enum { HOPF_STOP_PAPER = 0, HOPF_STOP_UREL = 1 };
 /* Per-query status bytes.  ABORTED: a bounded device-side wait of the dense
  * solver gave up (it never hangs); every query of that call carries it.
  * BAD_INPUT: the query's t is negative or NaN (t lives on the device, so the
- * call cannot refuse it); its outputs carry no meaning. */
+ * call cannot refuse it); its outputs carry no meaning.
+ * NONFINITE: phi came out NaN or infinite (e.g. a NaN or infinite coordinate
+ * of x); such a query's residual never passes the stop test, so it runs to
+ * max_iter.  Queries are independent: a bad query leaves every other query's
+ * outputs bit-identical. */
 enum { HOPF_Q_OK = 0, HOPF_Q_NOT_CONVERGED = 1, HOPF_Q_NONFINITE = 2, HOPF_Q_ABORTED = 3, HOPF_Q_BAD_INPUT = 4 };
 
 /* Problem description for hopf_create (host memory, copied).
