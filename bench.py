@@ -311,30 +311,35 @@ def run_ragged(args):
         e2e = {"value": whole_job_rate(Q, ws, ems), "unit": "evals/s", "h2d_bytes_per_step": int(x.nbytes + t.nbytes),
                "d2h_bytes_per_step": int(Q * 8 + x.size * 4 + Q * 4), "ms_per_step": ems}
 
-    # work-weighted roofline: dense instances on the tensor pipe (4 n x n MMA
-    # passes per iteration plus 3 for setup and the final pass, MIXED form),
-    # diagonal ones on the FP32 pipe (about 10 flop per coordinate-iteration)
+    # work-weighted roofline: dense instances on the tensor pipe (the
+    # algorithmic 2 n^2 (K + 2) flop per query; the MIXED form executes about
+    # four times that), diagonal ones on the FP32 pipe (about 10 flop per
+    # coordinate-iteration)
     pk = peaks()
     tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
     alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12
     qoff = np.concatenate([[0], np.cumsum(counts)])
-    tc_flops, alu_flops, launches = 0.0, 0.0, 0
+    tc_flops, tc_exec, alu_flops, launches = 0.0, 0.0, 0.0, 0
     for i, e in enumerate(descs):
         K = iters[qoff[i]:qoff[i + 1]]
         n = inst[i]["n"]
         if counts[i] == 0:
             continue
         if e["dense"]:
-            tc_flops += float(np.sum(2.0 * n * n * (4.0 * K + 3.0)))
+            f_alg, f_exe = dense_work(n, K, "mixed")
+            tc_flops += f_alg
+            tc_exec += f_exe
             launches += 4
         else:
             alu_flops += float(np.sum(10.0 * n * K))
             launches += 1
     t_roof = tc_flops / (tc_peak * 1e12) + alu_flops / (alu_peak * 1e12)
+    t_exec = tc_exec / (tc_peak * 1e12) + alu_flops / (alu_peak * 1e12)
     frac = t_roof / (ms * 1e-3)
     roof = {"bound": "tensor+alu (work-weighted)", "achieved": frac, "peak": 1.0,
             "unit": "fraction of the work-weighted roofline time", "frac": frac, "traffic": None,
             "roofline_ms": 1e3 * t_roof, "tensor_flops": tc_flops, "alu_flops": alu_flops,
+            "tensor_flops_executed": tc_exec, "frac_executed": t_exec / (ms * 1e-3),
             "peak_source": "tensor: MEASURED_PEAKS.json bf16_tflops_sustained (measured) %.1f TFLOP/s; "
                            "alu: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived) %.1f TFLOP/s" % (tc_peak, alu_peak)}
 
@@ -401,6 +406,28 @@ def time_steps(fn, steps, ws, local):
 
 ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 lanes x 2 flop (FMA) x max SM clock, TFLOP/s
 ALU_SRC = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived) %.1f TFLOP/s" % ALU_PEAK
+
+
+def dense_work(n, iters, form):
+    """(algorithmic, executed) flop of a dense solve over queries with the
+    given iteration counts.  Algorithmic: the method's one n x n product per
+    iteration plus the set-up and final products, 2 n^2 (K_q + 2) per query,
+    whatever the form.  Executed: the products the form issues -- "mixed":
+    four n x n MMA passes per iteration (three for A p in the two-term FP16
+    split, one for M g) plus three for the operand set-up and the final pass;
+    "bf16": one per iteration plus three; "fp32": one per iteration plus the
+    final A p pass."""
+    K = np.asarray(iters, dtype=np.float64)
+    alg = float(np.sum(2.0 * n * n * (K + 2.0)))
+    if form == "mixed":
+        exe = float(np.sum(2.0 * n * n * (4.0 * K + 3.0)))
+    elif form == "bf16":
+        exe = float(np.sum(2.0 * n * n * (K + 3.0)))
+    else:
+        exe = float(np.sum(2.0 * n * n * (K + 1.0)))
+    return alg, exe
+
+
 UNION_FLOP_PER_COORD = 12.0  # one split Bregman step of the diagonal l2 solve, per coordinate
 
 
@@ -532,7 +559,7 @@ def run_grad(args):
     iters = st["o"]["iters"].cpu().numpy().astype(np.float64)
     pk = peaks()
     tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
-    f_fwd = float(np.sum(2.0 * n * n * (4.0 * iters + 3.0)))
+    f_fwd, f_fwd_exec = dense_work(n, iters, "mixed")
     # g_A = -1/2 V^T diag(g) V is symmetric: a SYRK's n (n + 1) / 2 distinct
     # entries of 2B flop each (FP32 CUDA cores)
     f_bwd = float(n) * (n + 1) * B
@@ -541,6 +568,8 @@ def run_grad(args):
     roof = {"bound": "tensor+alu (work-weighted)", "achieved": frac, "peak": 1.0,
             "unit": "fraction of the work-weighted roofline time", "frac": frac, "traffic": None,
             "roofline_ms": 1e3 * t_roof, "forward_tensor_flops": f_fwd, "backward_alu_flops": f_bwd,
+            "forward_tensor_flops_executed": f_fwd_exec,
+            "frac_executed": (f_fwd_exec / (tc_peak * 1e12) + f_bwd / (ALU_PEAK * 1e12)) / (ms * 1e-3),
             "backward_ms": ms_b, "backward_alu_frac": f_bwd / (ms_b * 1e-3) / 1e12 / ALU_PEAK,
             "peak_source": "tensor: MEASURED_PEAKS.json bf16_tflops_sustained (measured) %.1f TFLOP/s; alu: %s"
                            % (tc_peak, ALU_SRC)}
@@ -607,10 +636,12 @@ def run_control(args):
     iters = st["o"]["iters"].cpu().numpy().astype(np.float64)
     pk = peaks()
     peak = pk.get("bf16_tflops_sustained", 1700.0)
-    flops = float(np.sum(2.0 * n * n * (4.0 * iters + 3.0)))
+    flops, f_exec = dense_work(n, iters, "mixed")
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    executed = f_exec / (kern_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
+            "executed_flops_per_launch": f_exec, "executed": executed, "executed_frac": executed / peak,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
     e2e = None
     if not args.no_e2e:
@@ -997,18 +1028,17 @@ def main():
     pk = peaks()
     K = iters.astype(np.float64)
     if prec == hg.P_FP32:
-        # one n x n FP32 product per iteration plus the final A p pass
-        flops = float(np.sum(2.0 * n * n * (K + 1)))
+        flops, f_exec = dense_work(n, K, "fp32")
         peak = 152 * 128 * 2 * 2.070e9 / 1e12  # FFMA lanes x 2 flop x max SM clock
         roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
         dtype = "f32"
     else:
-        terms = 4.0 if prec == hg.P_MIXED else 1.0  # MMA passes of n x n per iteration
-        flops = float(np.sum(2.0 * n * n * (terms * K + 3)))
+        flops, f_exec = dense_work(n, K, "mixed" if prec == hg.P_MIXED else "bf16")
         peak = pk.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
         dtype = "bf16+f16 (fp32 accumulate)" if prec == hg.P_MIXED else "bf16 (fp32 accumulate)"
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    executed = f_exec / (kern_ms * 1e-3) / 1e12
     traffic = None
     mt = MEASURED_TRAFFIC.get(args.variant)
     if mt and mt["n"] == n and mt["batch"] == B:
@@ -1017,7 +1047,9 @@ def main():
         if hashlib.sha256(src).hexdigest().startswith(mt["sha256_prefix"]):
             traffic = mt["bytes"]
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops})
+                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops,
+                 "algorithmic_flops_per_query": "2 n^2 (K_q + 2)",
+                 "executed_flops_per_launch": f_exec, "executed": executed, "executed_frac": executed / peak})
 
     cpu = None
     accuracy = None

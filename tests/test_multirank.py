@@ -91,3 +91,17 @@ def test_generator_offsets_slice_one_stream():
     for off, cnt in [(0, 10), (1, 7), (2, 9), (13, 100), (500, 499), (1000, 1)]:
         assert np.array_equal(wl.normal(7, cnt, offset=off), full_n[off:off + cnt])
         assert np.array_equal(wl.uniform(7, cnt, offset=off), full_u[off:off + cnt])
+
+
+def test_dense_work_counts():
+    """The roofline's algorithmic work is the method's one n x n product per
+    iteration plus the set-up and final products, 2 n^2 (K + 2) per query,
+    for every form; the executed work is the form's own product count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, K = 1024, np.array([44, 75, 120])
+    alg, exe = bench.dense_work(n, K, "mixed")
+    assert alg == 2.0 * n * n * (K + 2).sum()
+    assert exe == 2.0 * n * n * (4 * K + 3).sum()
+    assert bench.dense_work(n, K, "bf16") == (alg, 2.0 * n * n * (K + 3).sum())
+    assert bench.dense_work(n, K, "fp32") == (alg, 2.0 * n * n * (K + 1).sum())
