@@ -7,6 +7,8 @@
   every initial data and every Hamiltonian.  Every step of split Bregman
   keeps the state at exactly zero there (shrink of 0, the prox of a norm at 0
   and the l2 shrink's guard at |z| = 0), so the bar is exact.
+- Identical parts tie in the union, the maximum over Hamiltonians and the
+  distance: the first index wins, with the single part's value.
 """
 import numpy as np
 import pytest
@@ -107,3 +109,28 @@ def test_query_at_the_centre(hg):
         assert (out["dphidt"] == 0).all(), label
         assert (out["status"] == hg.Q_OK).all(), (label, out["status"])
         h.close()
+
+
+@pytest.mark.parametrize("n", [6, 40])
+def test_ties_go_to_the_smallest_index(hg, n):
+    """Identical parts tie everywhere: the union (Section 2.2), the maximum
+    over Hamiltonians and the distance (Section 3.2) report index 0 and the
+    single part's value."""
+    import torch
+    import workloads as wl
+    B = 50
+    a = wl.uniform(7701, n, 0.5, 2.0)
+    c = wl.normal(7702, n, 1.0)
+    x = torch.tensor(wl.normal(7703, B * n, 3.0).reshape(B, n).astype(np.float32), device="cuda")
+    t = torch.tensor(wl.uniform(7704, B, 0.0, 2.0).astype(np.float32), device="cuda")
+    h = hg.Hopf(a, hg.H_L2, centre=c, tol=1e-12, max_iter=3000, precision=hg.P_FP32)
+    one = hg.union_eval([h], x, t)
+    three = hg.union_eval([h, h, h], x, t)
+    mx = hg.maxH_eval([h, h], x, t)
+    d1 = hg.union_closest([h], x)
+    d2 = hg.union_closest([h, h], x)
+    torch.cuda.synchronize()
+    assert (three["argmin"] == 0).all() and torch.equal(three["phi"], one["phi"])
+    assert (mx["argmax"] == 0).all() and torch.equal(mx["phi"], one["phi"])
+    assert (d2["argmin"] == 0).all() and torch.equal(d2["dist"], d1["dist"])
+    h.close()

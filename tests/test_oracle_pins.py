@@ -772,3 +772,24 @@ def test_control_for_the_section4_hamiltonians(orc, h):
         z = ctl["x_T"][q] - c
         J = 0.5 * (z * z / a).sum() - 0.5
         assert abs(J - r["phi"][q]) <= 1e-7 * max(1.0, abs(r["phi"][q]))
+
+
+def test_ties_go_to_the_smallest_index(orc):
+    """With identical parts every part attains the minimum (union, Section
+    2.2), the maximum (maximum over Hamiltonians) and the distance (Section
+    3.2): the index reported is the first, 0, and the value is the single
+    part's."""
+    n = 6
+    a = wl.uniform(7601, n, 0.5, 2.0)
+    c = wl.normal(7602, n, 1.0)
+    x = wl.normal(7603, 12 * n, 3.0).reshape(12, n)
+    t = wl.uniform(7604, 12, 0.0, 2.0)
+    one = orc.Problem(a, orc.H_L2, centre=c, tol=1e-14, max_iter=5000, stop_rule=orc.STOP_UREL)
+    ref = one.eval(x, t)
+    r = orc.union_eval([one, one, one], x, t)
+    assert (r["argmin"] == 0).all() and np.array_equal(r["phi"], ref["phi"])
+    r = orc.maxH_eval([one, one], x, t)
+    assert (r["argmax"] == 0).all() and np.array_equal(r["phi"], ref["phi"])
+    r = orc.union_closest([one, one], x)
+    d1 = orc.union_closest([one], x)
+    assert (r["argmin"] == 0).all() and np.array_equal(r["dist"], d1["dist"])
