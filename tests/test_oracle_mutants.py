@@ -79,6 +79,11 @@ MUTANTS = [
     ("maxH_takes_min", "double best = -INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L, x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi > best) {",
      "double best = INFINITY;\n            int bi = -1, it = 0;\n            for (int i = 0; i < K; ++i) {\n                orc_result r;\n                orc_solve(&parts[i], L, x + q * n, t[q], g, &r, work, NULL);\n                it += r.iters;\n                if (r.phi < best) {",
      "test_max_over_hamiltonians_solves_the_min_hamiltonian_pde"),
+    ("union_ties_to_last", "it += r.iters;\n                if (r.phi < best) {", "it += r.iters;\n                if (r.phi <= best) {",
+     "test_ties_go_to_the_smallest_index"),
+    ("maxH_ties_to_last", "it += r.iters;\n                if (r.phi > best) {", "it += r.iters;\n                if (r.phi >= best) {",
+     "test_ties_go_to_the_smallest_index"),
+    ("closest_ties_to_last", "if (sb < best) {", "if (sb <= best) {", "test_ties_go_to_the_smallest_index"),
     ("newton_step_scaled", "double ds = r.phi / gn;", "double ds = r.phi / gn / gn;",
      "test_closest_point_against_ellipsoid_projection"),
     ("closest_takes_farthest", "if (sb < best) {", "if (sb > best) {",
