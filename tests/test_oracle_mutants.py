@@ -98,6 +98,15 @@ MUTANTS = [
     ("gc0_sign", "*g_c0 -= g_phi[q];", "*g_c0 += g_phi[q];", "test_parameter_gradients_against_finite_differences"),
     ("control_drops_centre", "(xi - (p->c ? p->c[i] : 0.0) - ap) / t[q]", "(xi - ap) / t[q]",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
+    ("warm_start_stops_at_k1", "(k >= 2 && ru <= p->tol)", "(ru <= p->tol)", "test_closest_point_against_ellipsoid_projection"),
+    ("ellipsoid_newton_loose", "if (fabs(dmu) <= 1e-15 * (mu > 1.0 ? mu : 1.0)) break;",
+     "if (fabs(dmu) <= 1e-3 * (mu > 1.0 ? mu : 1.0)) break;", "test_l2sq_initial_data_closed_forms_new_H"),
+    ("gt_sign", "g_t[q] = -g_phi[q] * orc_H(h_kind, n, w, v);", "g_t[q] = g_phi[q] * orc_H(h_kind, n, w, v);",
+     "test_backward_envelope_fd"),
+    ("gA_diag_drops_half", "for (int i = 0; i < n; ++i) g_A[i] -= 0.5 * g_phi[q] * v[i] * v[i];",
+     "for (int i = 0; i < n; ++i) g_A[i] -= g_phi[q] * v[i] * v[i];", "test_backward_diagonal_A_fd"),
+    ("gw_wl1_signed", "g_w[i] -= g_phi[q] * t[q] * fabs(v[i]);", "g_w[i] -= g_phi[q] * t[q] * v[i];",
+     "test_parameter_gradients_against_finite_differences"),
     ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
 ]

@@ -302,6 +302,34 @@ def test_backward_envelope_fd(orc):
     assert abs(b["g_t"][0] + np.abs(v).sum()) <= 1e-12
 
 
+def test_backward_diagonal_A_fd(orc):
+    """Diagonal A with H = l1 decouples (Section 1): phi = sum_i
+    shrink_1(x_i, t)^2 / (2 a_i) - c0.  The oracle's diagonal g_A (with an
+    upstream weight g) matches central differences of that closed form in
+    each a_i, and g_x, g_t match g v and -g H(v)."""
+    n = 7
+    a = wl.uniform(7611, n, 0.5, 2.0)
+    x = wl.normal(7612, n, 2.0)
+    t, g = 0.6, 1.7
+    P = orc.Problem(a, orc.H_L1, tol=1e-30, max_iter=50000, stop_rule=orc.STOP_UREL)
+    v = P.eval(x[None], [t])["grad"][0]
+    b = orc.backward(n, orc.A_DIAG, orc.H_L1, None, [g], v[None], [t])
+    s = np.sign(x) * np.maximum(np.abs(x) - t, 0.0)
+    assert (np.abs(s) > 0).sum() >= 2 and (s == 0).sum() >= 1  # both kinds of coordinate
+
+    def phi(av):
+        return (s * s / (2 * av)).sum() - 0.5
+
+    h = 1e-6
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd = g * (phi(a + e) - phi(a - e)) / (2 * h)
+        assert abs(b["g_A"][i] - fd) <= 1e-7 * max(1, abs(fd)), (i, b["g_A"][i], fd)
+    assert np.allclose(b["g_x"][0], g * v, rtol=1e-12, atol=1e-14)
+    assert abs(b["g_t"][0] + g * np.abs(v).sum()) <= 1e-12
+
+
 def test_golden_section1_example(orc):
     """A fixed worked instance of the Section 1 example (values written by
     tests/golden/make_golden.py from the closed form, not from the oracle)."""
