@@ -107,6 +107,14 @@ MUTANTS = [
      "for (int i = 0; i < n; ++i) g_A[i] -= g_phi[q] * v[i] * v[i];", "test_backward_diagonal_A_fd"),
     ("gw_wl1_signed", "g_w[i] -= g_phi[q] * t[q] * fabs(v[i]);", "g_w[i] -= g_phi[q] * t[q] * v[i];",
      "test_parameter_gradients_against_finite_differences"),
+    ("union_grad_of_last_part", "                    bi = i;\n                    memcpy(grad + q * n, g, sizeof(double) * (size_t)n);\n                }\n            }\n            phi[q] = best;\n            argmin[q] = bi;",
+     "                    bi = i;\n                }\n                memcpy(grad + q * n, g, sizeof(double) * (size_t)n);\n            }\n            phi[q] = best;\n            argmin[q] = bi;",
+     "test_union_min_rule"),
+    ("maxH_grad_of_last_part", "                    bi = i;\n                    memcpy(grad + q * n, g, sizeof(double) * (size_t)n);\n                }\n            }\n            phi[q] = best;\n            argmax[q] = bi;",
+     "                    bi = i;\n                }\n                memcpy(grad + q * n, g, sizeof(double) * (size_t)n);\n            }\n            phi[q] = best;\n            argmax[q] = bi;",
+     "test_max_over_hamiltonians_solves_the_min_hamiltonian_pde"),
+    ("control_diag_drops_A", "if (p->a_kind == ORC_A_DIAG) ap = p->A[i] * g[i];", "if (p->a_kind == ORC_A_DIAG) ap = g[i];",
+     "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
     ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
 ]

@@ -228,18 +228,23 @@ def _union_parts(orc, K, n, seed, tol=1e-28):
 
 def test_union_min_rule(orc):
     """phi = min_i phi_i (Section 2.2) with each phi_i from the secular
-    equation; at t = 0 it is min_i J_i(x)."""
+    equation, and its gradient the minimising part's; at t = 0 it is
+    min_i J_i(x)."""
     K, n = 4, 10
     semi, cen, parts = _union_parts(orc, K, n, 7401)
     x = wl.normal(7404, 20 * n, 5.0).reshape(20, n)
     t = wl.uniform(7405, 20, 0.0, 2.0)
     t[:3] = 0.0
     r = orc.union_eval(parts, x, t)
+    assert len(set(r["argmin"][3:].tolist())) >= 2  # the minimum moves between parts
     for q in range(20):
-        vals = [pins.diag_l2_secular(x[q] - cen[k], t[q], semi[k] ** 2)[0] for k in range(K)]
+        sol = [pins.diag_l2_secular(x[q] - cen[k], t[q], semi[k] ** 2) for k in range(K)]
+        vals = [v for v, _ in sol]
         k = int(np.argmin(vals))
         assert r["argmin"][q] == k
         assert abs(r["phi"][q] - vals[k]) <= 1e-9 * max(1, abs(vals[k]))
+        gk = sol[k][1]
+        assert np.linalg.norm(r["grad"][q] - gk) <= 1e-7 * max(1, np.linalg.norm(gk)), q
         if t[q] == 0:
             J = min(0.5 * (((x[q] - cen[j]) / semi[j]) ** 2).sum() - 0.5 for j in range(K))
             assert abs(r["phi"][q] - J) <= 1e-11 * max(1, abs(J))
