@@ -115,6 +115,14 @@ MUTANTS = [
      "test_max_over_hamiltonians_solves_the_min_hamiltonian_pde"),
     ("control_diag_drops_A", "if (p->a_kind == ORC_A_DIAG) ap = p->A[i] * g[i];", "if (p->a_kind == ORC_A_DIAG) ap = g[i];",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
+    ("shrink2_not_normalised", "out[i] = z[i] / nz * m;", "out[i] = z[i] * m;", "test_paper_example_sphere"),
+    ("gx_drops_weight", "g_x[q * n + i] = g_phi[q] * v[i];", "g_x[q * n + i] = v[i];", "test_backward_diagonal_A_fd"),
+    ("gc_sign", "g_c[i] -= g_phi[q] * v[i];", "g_c[i] += g_phi[q] * v[i];",
+     "test_parameter_gradients_against_finite_differences"),
+    ("jstar_l1_not_squared", "for (int i = 0; i < p->n; ++i) s += fabs(v[i]);\n        return s * s;",
+     "for (int i = 0; i < p->n; ++i) s += fabs(v[i]);\n        return s;", "test_nonquadratic_initial_data_bruteforce_n2"),
+    ("H_weights_ignored", "s += (h_kind == ORC_H_WL1 && w ? w[i] : 1.0) * fabs(q[i]);", "s += fabs(q[i]);",
+     "test_weighted_l1_with_centre"),
     ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
 ]
