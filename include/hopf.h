@@ -79,12 +79,21 @@ enum { HOPF_H_L1 = 0, HOPF_H_WL1 = 1, HOPF_H_L2 = 2, HOPF_H_LINF = 3, HOPF_H_DNO
  *          v = (A + lambda I)^{-1} r as an FP32 CUDA-core GEMM per iteration.
  *   BF16   dense: the same form with M = (A + lambda I)^{-1} and r in BF16 on
  *          the tensor cores (tcgen05), FP32 accumulation.  Fast, ~1e-2 error.
+ *   SPLIT  dense: the paper's form v = M r on the tensor cores with both
+ *          operands as two-term FP16 splits, M = M_hi + 2^-11 M_lo and
+ *          r = r_hi + 2^-11 r_lo, three MMAs per k-step
+ *          (M_hi r_hi, then M_hi r_lo + M_lo r_hi in a second accumulator
+ *          scaled exactly by 2^-11), FP32 accumulation: ~2^-22 per product,
+ *          FP32-class results in one phase per iteration.
  *   MIXED  dense: tensor-core defect-correction form u <- u + M g(u) with
  *          g = y - A p - lambda (u - p), A p from a two-term FP16 split with
  *          an exactly scaled correction accumulator, M g in BF16.  Its fixed
- *          point depends only on the accuracy of g: FP32-class results.
+ *          point depends only on the accuracy of g: FP32-class results, two
+ *          phases (four MMAs) per iteration.
+ * SPLIT and MIXED reach the same accuracy at the same tolerance; SPLIT does
+ * three n x n MMA passes per iteration where MIXED does four.
  */
-enum { HOPF_P_FP64 = 0, HOPF_P_FP32 = 1, HOPF_P_BF16 = 2, HOPF_P_MIXED = 5 };
+enum { HOPF_P_FP64 = 0, HOPF_P_FP32 = 1, HOPF_P_BF16 = 2, HOPF_P_SPLIT = 4, HOPF_P_MIXED = 5 };
 
 /* Stopping rules.
  *   PAPER: |v^k - v^{k-1}|^2, |d^k - d^{k-1}|^2, |d^k - v^k|^2 all <= tol
@@ -180,7 +189,7 @@ hopf_status hopf_eval_f64(hopf_handle h, int64_t batch, const double* x, const d
  *           which lies in the subdifferential dH(p) (equal to grad H(p)
  *           where H is differentiable); 0 when t = 0.  Device, required.
  *   x_final [batch][n] float: x - t beta (device, may be NULL).
- * FP32-output handles (diagonal FP32, dense FP32 / MIXED / BF16); FP64
+ * FP32-output handles (diagonal FP32, dense FP32 / SPLIT / MIXED / BF16); FP64
  * handles return HOPF_EUNSUPPORTED.  Workspace as for hopf_eval. */
 hopf_status hopf_eval_control(hopf_handle h, int64_t batch, const float* x, const float* t, double* phi, float* grad,
                               float* dphidt, int32_t* iters, uint8_t* qstatus, float* beta, float* x_final,
@@ -236,8 +245,10 @@ hopf_status hopf_union_closest(const hopf_handle* parts, int32_t K, int64_t batc
  * the library, not of the method.)  Same arguments and results as
  * hopf_union_closest, minus the workspace: the scratch is one static 8 MiB
  * device array that every GPU which loads the library holds until the
- * process exits, so batch * K may not exceed about 490,000 query-part pairs
- * (larger requests return HOPF_EINVAL and launch nothing).  The first call on
+ * process exits.  A call needs batch * (17 K + 4) bytes of it (five regions,
+ * each rounded up to 256 bytes), so batch may not exceed about 399,000
+ * queries with one part, or about 30,000 with 16 (larger requests return
+ * HOPF_EINVAL and launch nothing).  The first call on
  * a device looks up the array's device address with that device current;
  * make that first call before any stream capture.  All calls share the array
  * and it keeps the last call's contents (nothing in it needs to start at
@@ -322,6 +333,21 @@ hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t st
  * same results (each query's arithmetic does not depend on its column), only
  * slower.  Other paths ignore it. */
 hopf_status hopf_set_compaction(hopf_handle h, int32_t on);
+
+/* Roofline denominators measured on the current device (the paper has no
+ * counterpart: a calibration utility for reporting throughput against the
+ * hardware at hand).  Runs fixed-size probe kernels on `stream` and waits for
+ * them (it synchronises the stream):
+ *   fp32_tflops  chains of FP32 fused multiply-adds, 2 flop each (may be NULL)
+ *   fp64_tflops  the same in FP64 (may be NULL)
+ *   l2_read_gbs  repeated 16-byte reads of a 32 MiB buffer, which stays in L2
+ *                (may be NULL)
+ * scratch: device memory of at least hopf_measure_pipes_scratch() bytes,
+ * owned by the caller; its contents are overwritten.  Changes no setting of
+ * the GPU. */
+size_t hopf_measure_pipes_scratch(void);
+hopf_status hopf_measure_pipes(void* scratch, size_t scratch_bytes, double* fp32_tflops, double* fp64_tflops,
+                               double* l2_read_gbs, cudaStream_t stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hopf_last_error(void);

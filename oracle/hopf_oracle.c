@@ -507,7 +507,11 @@ int orc_union_eval(const orc_problem *parts, int32_t K, int64_t batch, const dou
     for (int i = 0; i < K; ++i) {
         if (parts[i].a_kind == ORC_A_DENSE) {
             L[i] = (double *)malloc(sizeof(double) * (size_t)n * n);
-            if (orc_factor(n, parts[i].A, parts[i].lambda, L[i]) != 0) return -1;
+            if (orc_factor(n, parts[i].A, parts[i].lambda, L[i]) != 0) {
+                for (int j = 0; j <= i; ++j) free(L[j]);
+                free(L);
+                return -1;
+            }
         }
     }
 #pragma omp parallel
@@ -596,7 +600,11 @@ int orc_union_closest(const orc_problem *parts, int32_t K, int64_t batch, const 
     for (int i = 0; i < K; ++i) {
         if (parts[i].a_kind == ORC_A_DENSE) {
             L[i] = (double *)malloc(sizeof(double) * (size_t)n * n);
-            if (orc_factor(n, parts[i].A, parts[i].lambda, L[i]) != 0) return -1;
+            if (orc_factor(n, parts[i].A, parts[i].lambda, L[i]) != 0) {
+                for (int j = 0; j <= i; ++j) free(L[j]);
+                free(L);
+                return -1;
+            }
         }
     }
     int fails = 0;

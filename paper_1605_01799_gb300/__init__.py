@@ -23,7 +23,7 @@ A_DIAG, A_DENSE = 0, 1
 # initial data without a matrix: J = 1/2|x-c|_1^2 - c0, 1/2|x-c|_inf^2 - c0
 J_QUAD, J_L1SQ, J_LINFSQ = 0, 2, 3
 H_L1, H_WL1, H_L2, H_LINF, H_DNORM, H_ANORM = 0, 1, 2, 3, 4, 5  # H_ANORM: w = M (n x n)
-P_FP64, P_FP32, P_BF16, P_MIXED = 0, 1, 2, 5
+P_FP64, P_FP32, P_BF16, P_SPLIT, P_MIXED = 0, 1, 2, 4, 5
 STOP_PAPER, STOP_UREL = 0, 1
 Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED, Q_BAD_INPUT = 0, 1, 2, 3, 4
 
@@ -32,7 +32,7 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_backward", "hopf_backward_params",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
-           "hopf_last_error", "hopf_version"]
+           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -83,6 +83,8 @@ def lib():
             "hopf_eval_control": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
                                   ctypes.c_int),
             "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_measure_pipes_scratch": ([], _sz),
+            "hopf_measure_pipes": ([_vp, _sz, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
             "hopf_version": ([], ctypes.c_char_p),
         }
@@ -111,6 +113,17 @@ def _stream(stream=None):
 
 def version():
     return lib().hopf_version().decode()
+
+
+def measure_pipes(stream=None):
+    """Measured FP32 and FP64 FMA throughput (TFLOP/s) and L2 read bandwidth
+    (GB/s) of the current device, from the library's probe kernels."""
+    import torch
+    buf = torch.empty(int(lib().hopf_measure_pipes_scratch()), dtype=torch.uint8, device="cuda")
+    f32, f64, l2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().hopf_measure_pipes(_ptr(buf), buf.numel(), ctypes.byref(f32), ctypes.byref(f64), ctypes.byref(l2),
+                                    _stream(stream)))
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "l2_read_gbs": l2.value}
 
 
 def _a_kind(A, j_kind, n):

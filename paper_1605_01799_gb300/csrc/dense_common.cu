@@ -43,8 +43,10 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 
   s[23] = tc ? B_pad * np * 4 : 0;       // ufin
   s[24] = B_pad * 4;                     // sfin
   s[25] = 2 * B_pad * 4;                 // taus
+  const bool split = h->precision == HOPF_P_SPLIT;
+  for (int i = 26; i < 30; ++i) s[i] = split ? B_pad * np * 2 : 0;  // qh, ql, qh_b, ql_b
   size_t total = 0;
-  for (int i = 0; i < 26; ++i) {
+  for (int i = 0; i < 30; ++i) {
     if (out) out[i] = total;
     total += round_up(s[i], 256);
   }
@@ -88,6 +90,11 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
   d->ufin = tc ? (float*)(p + off[23]) : nullptr;
   d->sfin = (float*)(p + off[24]);
   d->taus = (float*)(p + off[25]);
+  const bool split = h->precision == HOPF_P_SPLIT;
+  d->qh = split ? (uint16_t*)(p + off[26]) : nullptr;
+  d->ql = split ? (uint16_t*)(p + off[27]) : nullptr;
+  d->qh_b = split ? (uint16_t*)(p + off[28]) : nullptr;
+  d->ql_b = split ? (uint16_t*)(p + off[29]) : nullptr;
   return HOPF_OK;
 }
 

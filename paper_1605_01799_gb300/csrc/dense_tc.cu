@@ -1,8 +1,18 @@
 // Dense A on the 5th-generation tensor cores (tcgen05 + TMA + TMEM), sm_103a.
 //
-// Two forms of the split Bregman iteration (eq. 3.4(a)-(c)) in terms of the
+// Three forms of the split Bregman iteration (eq. 3.4(a)-(c)) in terms of the
 // d-update argument u (u^k = v^k + b^{k-1}; p = prox_{(t/lambda)H}(u) is d,
 // b = u - p):
+//
+//  SPLIT (the paper's v-update with split operands, one phase per iteration).
+//     v^{k+1} = M r^k,  r^k = y + lambda (2 p^k - u^k),  u^{k+1} = v^{k+1} + b^k
+//  with M and r both two-term FP16 splits, M r ~ M_hi r_hi
+//  + 2^-11 (M_hi r_lo' + M_lo' r_hi), the correction terms in a second TMEM
+//  accumulator scaled exactly in the epilogue (~2^-22 per product).  For
+//  H = l2 the prox is s u with a scale s known only once |u| is summed over
+//  all row tiles, so the operand holds u itself and linearity gives
+//  v^{k+1} = M y + lambda (2 s - 1) M u^k; the first iteration's product
+//  (operand y) is M y, which then replaces y in the slot's y plane.
 //
 //  MIXED (defect correction).  With M = (A + lambda I)^{-1} and the identity
 //  M (A + lambda I) = I, the v-update of eq. 3.4(a) becomes
@@ -13,8 +23,10 @@
 //              (A_lo' = fp16((A - A_hi) 2^11), p_lo' likewise), the correction
 //              terms in a second TMEM accumulator scaled exactly in the
 //              epilogue; the epilogue forms g and stores it in BF16;
-//    phase B:  M g with BF16 operands, the epilogue updates u, stores the FP16
-//              split of the next p and the residual partial sums.
+//    phase B:  M g with BF16 operands (K = 16 steps alternating between two
+//              accumulators, so consecutive MMAs do not wait on one another),
+//              the epilogue updates u, stores the FP16 split of the next p and
+//              the residual partial sums.
 //  BF16 (the paper's form, v = M r with r = y + lambda (2p - u) in BF16): one
 //  phase per iteration.  Its fixed point carries the BF16 error of M r.
 //
@@ -27,11 +39,13 @@
 //   D3 = A1 p3 + A2 p2 + A3 p1,
 // two ring stages per k-block and both TMEM buffers per tile.
 //
-// One persistent cooperative launch, one CTA per SM, 320 threads:
+// One persistent cooperative launch, one CTA per SM, 64 + 32 EPI_WARPS threads
+// (576 with the default 16 epilogue warps):
 //   warp 0   TMA producer (one elected lane), 3-stage shared-memory ring
 //   warp 1   TMEM owner and MMA issuer (one elected lane)
-//   warps 2-9 epilogue: TMEM -> registers -> elementwise update -> global;
-//            two warps per TMEM lane quadrant, each taking half the columns
+//   warps 2.. epilogue: TMEM -> registers -> elementwise update -> global;
+//            EPI_WARPS / 4 warps per TMEM lane quadrant, each taking
+//            128 / (EPI_WARPS / 4) of the tile's columns
 // Work item = (128-row tile of n, 128-query column tile); items of a phase
 // are dealt round-robin over CTAs; grid barriers separate the phases.  Every
 // wait is bounded: on timeout the CTA records an error word, drains its own
@@ -62,8 +76,8 @@ constexpr int NEPI = EPI_WARPS * 32;           // epilogue threads
 constexpr int NT = 64 + NEPI;                  // 2 role warps + the epilogue warps
 constexpr int CPW = BN / (EPI_WARPS / 4);      // tile columns per epilogue warp
 constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 accumulators x 128 columns
-constexpr int FORM_MIXED = 0, FORM_BF16 = 1;
-constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3;
+constexpr int FORM_MIXED = 0, FORM_BF16 = 1, FORM_SPLIT = 2;
+constexpr int PH_A = 0, PH_B = 1, PH_P = 2, PH_F = 3, PH_S = 4;
 constexpr float kLoScale = 2048.f;             // 2^11: FP16 split scale
 constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 
@@ -73,10 +87,14 @@ constexpr float kLo2Scale = 4194304.f;         // 2^22: third term of the split
 struct TcArgs {
   CUtensorMap mAh, mAl, mAl2, mM, mP1, mP2, mP1b, mP2b, mG, mP3;  // mP3: the g plane read as the third split of p
   CUtensorMap mU[2];  // the FP32 u planes, for L2 prefetch of the epilogue's tiles
+  CUtensorMap mMh, mMl;           // SPLIT: the two-term FP16 split of M
+  CUtensorMap mQ1[2], mQ2[2];     // SPLIT: r^k of odd k, by buffer set (even k: mP1/mP2, mP1b/mP2b)
   float* y[2];
   float* u[2];
   uint16_t* p1[2];
   uint16_t* p2[2];
+  uint16_t* q1[2];    // SPLIT: odd-parity operand planes by set
+  uint16_t* q2[2];
   float* taus[2];     // t / lambda by slot
   int* qact[2][2];    // [set][parity of the decision]: 1 active, 2 retiring in this decision, 0 otherwise
   int* sq[2];         // slot -> query
@@ -255,12 +273,12 @@ struct PhaseCfg {
 
 __device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
   PhaseCfg c{};
-  if (ph == PH_A || ph == PH_F) {
+  if (ph == PH_A || ph == PH_F || ph == PH_S) {
     c.na = 2; c.nb = 2; c.nterm = 3;
     c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // A_hi p_hi     -> D1
     c.ta[1] = 0; c.tb[1] = 1; c.td[1] = 1;   // A_hi p_lo'    -> D2
     c.ta[2] = 1; c.tb[2] = 0; c.td[2] = 1;   // A_lo' p_hi    -> D2
-    c.idesc = idesc_f16(0);
+    c.idesc = idesc_f16(0);                  // (PH_S: M_hi r_hi, M_hi r_lo', M_lo' r_hi)
   } else {
     c.na = 1; c.nb = 1; c.nterm = 1;
     c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // M (g or r)    -> D1
@@ -303,13 +321,19 @@ struct ProdState {
 __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, int k, const Ctx& x,
                                ProdState& st) {
   const PhaseCfg cfg = phase_cfg(ph);
-  const CUtensorMap* A0 = (ph == PH_A || ph == PH_F) ? &a.mAh : &a.mM;
-  const CUtensorMap* A1 = &a.mAl;
+  const CUtensorMap* A0 = (ph == PH_A || ph == PH_F) ? &a.mAh : ph == PH_S ? &a.mMh : &a.mM;
+  const CUtensorMap* A1 = ph == PH_S ? &a.mMl : &a.mAl;
   const CUtensorMap* B0 = ph == PH_A ? (x.cb ? &a.mP1b : &a.mP1)
                           : ph == PH_F ? &a.mP1
                           : ph == PH_B ? &a.mG
                                        : (((k - 1) & 1) ? &a.mP2 : &a.mP1);
   const CUtensorMap* B1 = (ph == PH_A && x.cb) ? &a.mP2b : &a.mP2;
+  if (ph == PH_S) {
+    // r^{k-1}: parity (k - 1) & 1 of the current buffer set
+    const bool odd = ((k - 1) & 1) != 0;
+    B0 = odd ? &a.mQ1[x.cb] : (x.cb ? &a.mP1b : &a.mP1);
+    B1 = odd ? &a.mQ2[x.cb] : (x.cb ? &a.mP2b : &a.mP2);
+  }
   // phases with one operand pair (B, P) fill a stage with two k-blocks
   const int kstep = cfg.na == 1 ? 2 : 1;
   const uint32_t bytes = 4u * TILE_BYTES;
@@ -433,13 +457,16 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
       tc_fence_after();
       const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
       if (cfg.na == 1) {
+        // consecutive K = 16 steps alternate between the buffer's two
+        // accumulators (the epilogue adds them): back-to-back MMAs into one
+        // accumulator at N = 128 run at about two thirds of the MMA rate
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t ad = smem_desc(base + h * TILE_BYTES) + (uint64_t)(kk * 2);
             const uint64_t bd = smem_desc(base + (2 + h) * TILE_BYTES) + (uint64_t)(kk * 2);
-            mma_f16(d0, ad, bd, cfg.idesc, (kb == 0 && h == 0 && kk == 0) ? 0u : 1u);
+            mma_f16(d0 + (kk & 1) * BN, ad, bd, cfg.idesc, (kb == 0 && h == 0 && kk < 2) ? 0u : 1u);
           }
         }
       } else {
@@ -688,13 +715,15 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     for (int j0 = jbase; good && j0 < jbase + CPW; j0 += 16) {
       if (j0 != jbase) load(j0);
       float d1[16];
-      tmem_ld16(tbase + j0, d1);
-      if constexpr (ph == PH_A) {
-        // A p = D1 + 2^-11 D2
+      {
+        // A p (PH_A), M r (PH_S) = D1 + 2^-11 D2; M g (PH_B) and M r (PH_P)
+        // = D1 + D2, the two accumulators of alternating K steps
         float d2[16];
+        tmem_ld16(tbase + j0, d1);
         tmem_ld16(tbase + BN + j0, d2);
+        const float s2 = (ph == PH_A || ph == PH_S) ? 1.f / kLoScale : 1.f;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) d1[jj] += d2[jj] * (1.f / kLoScale);
+        for (int jj = 0; jj < 16; ++jj) d1[jj] += d2[jj] * s2;
       }
       const int64_t col0 = ((int64_t)c * BN + j0) * np + row;
       if (rm) {
@@ -762,6 +791,61 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
             }
             d1[jj] = du * du;
             uu[jj] = on ? un * un : 0.f;
+          }
+        }
+        transpose_reduce16(d1, lane);
+        transpose_reduce16(uu, lane);
+        if (lane < 16) {
+          S.red[ib][qd][j0 + lane][0] = d1[0];
+          S.red[ib][qd][j0 + lane][1] = uu[0];
+        }
+      } else if constexpr (ph == PH_S) {
+        // d1 holds v^k = M r^{k-1} (l2: M u^{k-1}, or M y when k = 1);
+        // u^k = v^k + b^{k-1}, then the split of r^k (l2: of u^k) goes to the
+        // planes of parity k & 1; d1 and uu become |u^k - u^{k-1}|^2, |u^k|^2
+        float* U = a.u[cb] + col0;
+        const bool odd = (k & 1) != 0;
+        uint16_t* R1 = (odd ? a.q1[cb] : a.p1[cb]) + col0;
+        uint16_t* R2 = (odd ? a.q2[cb] : a.p2[cb]) + col0;
+        float* Y = a.y[cb] + col0;
+        const bool l2 = hk == H_L2;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(&S.qtau[ib][j0 + 4 * q4]);
+          const float4 s4 = *reinterpret_cast<const float4*>(&S.qscale[ib][j0 + 4 * q4]);
+          const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+          const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int jj = 4 * q4 + e;
+            const bool on = am >> jj & 1u;
+            float du = 0.f, un = 0.f;
+            if (on) {
+              const float th = tv[e] * wr;
+              float v, b;
+              if (l2) {
+                if (first) {
+                  v = (1.f + lam) * d1[jj];  // r^0 = (1 + lambda) y
+                  b = 0.f;
+                  Y[(int64_t)jj * np] = d1[jj];  // M y, for every later iteration
+                } else {
+                  v = yy[jj] + lam * (2.f * sv[e] - 1.f) * d1[jj];
+                  b = (1.f - sv[e]) * uu[jj];
+                }
+              } else {
+                v = d1[jj];
+                b = first ? 0.f : uu[jj] - shrink1(uu[jj], th);  // b^0 = 0
+              }
+              un = v + b;
+              du = un - uu[jj];
+              const float rn = l2 ? un : yy[jj] + lam * (2.f * shrink1(un, th) - un);
+              const __half hi = __float2half_rn(rn);
+              R1[(int64_t)jj * np] = __half_as_ushort(hi);
+              R2[(int64_t)jj * np] = __half_as_ushort(__float2half_rn((rn - __half2float(hi)) * kLoScale));
+              U[(int64_t)jj * np] = un;
+            }
+            d1[jj] = du * du;
+            uu[jj] = un * un;
           }
         }
         transpose_reduce16(d1, lane);
@@ -956,6 +1040,13 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
   epi_sync();
   const int np = a.np, rt = a.rt;
   const int64_t pstride = (int64_t)rt * a.B_pad;
+  // operand planes to carry: MIXED the split of p (one pair per set), SPLIT
+  // r^k in the pair of parity k & 1
+  const bool odd = a.form == FORM_SPLIT && (x.k & 1);
+  const uint16_t* o1 = odd ? a.q1[cb] : a.p1[cb];
+  const uint16_t* o2 = odd ? a.q2[cb] : a.p2[cb];
+  uint16_t* d1p = odd ? a.q1[nb] : a.p1[nb];
+  uint16_t* d2p = odd ? a.q2[nb] : a.p2[nb];
   for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
     if (tile_count(a, x, c) == 0) continue;  // the same for every thread
     if (et < BN) {
@@ -997,16 +1088,16 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
         dst[b] = (int64_t)d * np + i;
         yv[b] = *reinterpret_cast<const float4*>(a.y[cb] + so);
         uv[b] = *reinterpret_cast<const float4*>(a.u[cb] + so);
-        p1v[b] = *reinterpret_cast<const uint2*>(a.p1[cb] + so);
-        p2v[b] = *reinterpret_cast<const uint2*>(a.p2[cb] + so);
+        p1v[b] = *reinterpret_cast<const uint2*>(o1 + so);
+        p2v[b] = *reinterpret_cast<const uint2*>(o2 + so);
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (dst[b] < 0) continue;
         *reinterpret_cast<float4*>(a.y[nb] + dst[b]) = yv[b];
         *reinterpret_cast<float4*>(a.u[nb] + dst[b]) = uv[b];
-        *reinterpret_cast<uint2*>(a.p1[nb] + dst[b]) = p1v[b];
-        *reinterpret_cast<uint2*>(a.p2[nb] + dst[b]) = p2v[b];
+        *reinterpret_cast<uint2*>(d1p + dst[b]) = p1v[b];
+        *reinterpret_cast<uint2*>(d2p + dst[b]) = p2v[b];
       }
     }
     epi_sync();
@@ -1133,6 +1224,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
       if (lane == 0) mma_phase(a, S, stages, ph, cx, ms);
     } else {
       if (ph == PH_A) epilogue_phase<PH_A>(a, S, k, cx, es);
+      else if (ph == PH_S) epilogue_phase<PH_S>(a, S, k, cx, es);
       else if (ph == PH_B) epilogue_phase<PH_B>(a, S, k, cx, es);
       else if (ph == PH_P) epilogue_phase<PH_P>(a, S, k, cx, es);
       else epilogue_final(a, S, cx, es);
@@ -1142,8 +1234,9 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
 
   // Iteration k: phase A (decision k in its epilogue, then g), barrier,
   // phase B (u, p and the partial sums), barrier, and a compaction when it
-  // frees a quarter of the column tiles in use.  The BF16 form has
-  // the single phase P.
+  // frees a quarter of the column tiles in use.  The SPLIT form has the
+  // single phase S (decision k, u^k, r^k and the partial sums) before the
+  // same compaction; the BF16 form the single phase P, without compaction.
   bool ok = true;
   for (int k = 1; ok; ++k) {
     cx.k = k;
@@ -1151,13 +1244,15 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     // the count slot that decision k + 1 fills (last read at iteration
     // k - 2, which every CTA has left)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
-    run(a.form == FORM_MIXED ? PH_A : PH_P, k);
+    run(a.form == FORM_MIXED ? PH_A : a.form == FORM_SPLIT ? PH_S : PH_P, k);
     if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
     const int n_active = (int)ld_acquire_u32(a.bar + 2 + (k % 3));
     if (n_active == 0) break;
-    if (a.form != FORM_MIXED) continue;
-    run(PH_B, k);
-    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+    if (a.form == FORM_BF16) continue;
+    if (a.form == FORM_MIXED) {
+      run(PH_B, k);
+      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+    }
     // every CTA takes the same decision from the same count: compact when it
     // frees a quarter of the column tiles in use and shortens each phase by
     // at least one round of items over the grid (a sixteenth, an eighth, a
@@ -1255,12 +1350,14 @@ static bool encode_f32(CUtensorMap* m, const void* ptr, int64_t rows, int np) {
   return r == CUDA_SUCCESS;
 }
 
-// FP16 split of y (MIXED: p^0 = y) or BF16 r^0 = y + lambda y (BF16 form).
+// FP16 split of y (MIXED: p^0 = y; SPLIT with H = l2: the operand u^0 = y),
+// of r^0 = y + lambda y (SPLIT, l1 and weighted l1), or BF16 r^0 (BF16 form).
 __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restrict__ p1, uint16_t* __restrict__ p2,
-                                  int64_t total, int form, float lam) {
+                                  int64_t total, int form, float lam, int h_kind) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = y[i];
-    if (form == FORM_MIXED) {
+    float v = y[i];
+    if (form == FORM_SPLIT && h_kind != H_L2) v = v + lam * v;
+    if (form != FORM_BF16) {
       const __half hi = __float2half_rn(v);
       p1[i] = __half_as_ushort(hi);
       p2[i] = __half_as_ushort(__float2half_rn((v - __half2float(hi)) * kLoScale));
@@ -1291,13 +1388,13 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
                           float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
                           float* xfin) {
   using namespace tc;
-  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : FORM_BF16;
+  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
   if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
     return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
   hopf_status s = dense_init(h, w, x, t, stream);
   if (s != HOPF_OK) return s;
   const int64_t total = w.B_pad * h->n_pad;
-  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda);
+  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda, h->h_kind);
   HOPF_CUDA(cudaGetLastError());
 
   TcArgs a;
@@ -1309,7 +1406,11 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
             encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
             encode(&a.mP1b, w.ph_b, w.B_pad, np, false) && encode(&a.mP2b, w.pl_b, w.B_pad, np, false) &&
             encode(&a.mG, w.g, w.B_pad, np, true) && encode_f32(&a.mU[0], w.u, w.B_pad, np) &&
-            encode_f32(&a.mU[1], form == FORM_MIXED ? w.u_b : w.u, w.B_pad, np);
+            encode_f32(&a.mU[1], form != FORM_BF16 ? w.u_b : w.u, w.B_pad, np);
+  if (ok && form == FORM_SPLIT)
+    ok = encode(&a.mMh, h->d_Mh16, np, np, false) && encode(&a.mMl, h->d_Ml16, np, np, false) &&
+         encode(&a.mQ1[0], w.qh, w.B_pad, np, false) && encode(&a.mQ2[0], w.ql, w.B_pad, np, false) &&
+         encode(&a.mQ1[1], w.qh_b, w.B_pad, np, false) && encode(&a.mQ2[1], w.ql_b, w.B_pad, np, false);
   if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
   a.y[0] = w.y;
   a.y[1] = w.y_b;
@@ -1319,6 +1420,10 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.p1[1] = w.ph_b;
   a.p2[0] = w.pl;
   a.p2[1] = w.pl_b;
+  a.q1[0] = w.qh;
+  a.q1[1] = w.qh_b;
+  a.q2[0] = w.ql;
+  a.q2[1] = w.ql_b;
   a.taus[0] = w.taus;
   a.taus[1] = w.taus + w.B_pad;
   a.qact[0][0] = w.qact;
@@ -1356,7 +1461,7 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.max_iter = h->max_iter;
   a.form = form;
   // the BF16 form keeps its r double buffer in set 0 and runs without compaction
-  a.compact = form == FORM_MIXED && h->compact && a.ct <= 1024;  // the scan table holds 1,024 tiles
+  a.compact = form != FORM_BF16 && h->compact && a.ct <= 1024;  // the scan table holds 1,024 tiles
   a.lam = (float)h->lambda;
   a.tol = (float)h->tol;
 

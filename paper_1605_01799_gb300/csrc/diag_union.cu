@@ -329,8 +329,8 @@ hopf_status union_closest_noalloc(const hopf_handle* parts, int K, int64_t batch
                                   uint8_t* qstatus, cudaStream_t stream) {
   const size_t need = union_workspace(K, parts[0]->n, batch);
   if (need > kNoAllocScratchBytes)
-    return fail(HOPF_EINVAL, "hopf_union_closest_noalloc: batch * parts needs more than the 8 MiB static scratch "
-                             "(at most about 490,000 query-part pairs)");
+    return fail(HOPF_EINVAL, "hopf_union_closest_noalloc: batch * (17 parts + 4) bytes exceed the 8 MiB static "
+                             "scratch (about 399,000 queries with one part, 30,000 with 16)");
   void* ws = nullptr;
   hopf_status s = noalloc_scratch(&ws);
   if (s != HOPF_OK) return s;

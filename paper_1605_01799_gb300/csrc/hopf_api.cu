@@ -89,7 +89,8 @@ static bool sym_eig(int n, const double* M, std::vector<double>& P, std::vector<
 static void free_handle(hopf_handle h) {
   if (!h) return;
   void* ptrs[] = {h->d_A, h->d_c, h->d_w, h->d_cf, h->d_wf, h->d_af, h->d_M64, h->d_M32, h->d_A32,
-                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf, h->d_P, h->d_PT, h->d_Pf, h->d_PTf};
+                  h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf, h->d_Mh16, h->d_Ml16, h->d_P, h->d_PT,
+                  h->d_Pf, h->d_PTf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -163,7 +164,16 @@ hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t st
   return HOPF_OK;
 }
 
-const char* hopf_version(void) { return "hopf-gb300 0.1 (sm_103a)"; }
+const char* hopf_version(void) { return "hopf-gb300 0.2 (sm_103a)"; }
+
+size_t hopf_measure_pipes_scratch(void) { return probe_scratch_bytes(); }
+
+hopf_status hopf_measure_pipes(void* scratch, size_t scratch_bytes, double* fp32_tflops, double* fp64_tflops,
+                               double* l2_read_gbs, cudaStream_t stream) {
+  set_error("");
+  if (!scratch) return fail(HOPF_EINVAL, "hopf_measure_pipes: null scratch");
+  return measure_pipes(scratch, scratch_bytes, fp32_tflops, fp64_tflops, l2_read_gbs, stream);
+}
 
 hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t stream) {
   set_error("");
@@ -193,7 +203,7 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
   if (d.stop_rule != HOPF_STOP_PAPER && d.stop_rule != HOPF_STOP_UREL)
     return fail(HOPF_EINVAL, "hopf_create: bad stop_rule");
   if (d.precision != HOPF_P_FP64 && d.precision != HOPF_P_FP32 && d.precision != HOPF_P_BF16 &&
-      d.precision != HOPF_P_MIXED)
+      d.precision != HOPF_P_SPLIT && d.precision != HOPF_P_MIXED)
     return fail(HOPF_EINVAL, "hopf_create: bad precision");
   if (d.a_kind == HOPF_A_DENSE && d.precision == HOPF_P_FP64)
     return fail(HOPF_EUNSUPPORTED, "hopf_create: FP64 is implemented for diagonal A only");

@@ -42,6 +42,8 @@ struct hopf_handle_s {
   uint16_t* d_Al16 = nullptr;  // FP16((A - FP16(A)) * 2^11)
   uint16_t* d_Al2 = nullptr;   // FP16((A - hi - lo * 2^-11) * 2^22): third term of the split
   uint16_t* d_Abf = nullptr;   // BF16(A) (for the BF16 form's final phi pass)
+  uint16_t* d_Mh16 = nullptr;  // FP16(M) (SPLIT form)
+  uint16_t* d_Ml16 = nullptr;  // FP16((M - FP16(M)) * 2^11) (SPLIT form)
   cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
   int compact = 1;  // tensor-core path: pack active queries as others converge
 };
@@ -114,6 +116,12 @@ struct DenseWs {
   int* sq = nullptr;         // [2][B_pad] slot -> query
   float* ufin = nullptr;     // [B_pad][n_pad] u of converged queries, by query
   float* sfin = nullptr;     // [B_pad] l2 scale of converged queries, by query
+  // SPLIT form: r^k lives in the operand planes of parity k & 1; parity 0 is
+  // (ph, pl) / (ph_b, pl_b), parity 1 these (one pair per buffer set)
+  uint16_t* qh = nullptr;    // [B_pad][n_pad]
+  uint16_t* ql = nullptr;
+  uint16_t* qh_b = nullptr;
+  uint16_t* ql_b = nullptr;
   unsigned* bar = nullptr;   // [4] grid barrier + counters
   int* err = nullptr;        // [1]
 };
@@ -135,6 +143,11 @@ hopf_status backward_params(hopf_handle h, int64_t batch, const float* g_phi, co
                             const float* dphidt, float* g_c, float* g_c0, float* g_w, cudaStream_t stream);
 
 int sm_count(int device);
+
+// ---- pipe probes (probe.cu) ----
+size_t probe_scratch_bytes();
+hopf_status measure_pipes(void* scratch, size_t bytes, double* fp32_tflops, double* fp64_tflops, double* l2_gbs,
+                          cudaStream_t stream);
 
 // ---- ragged batches (batch.cu) ----
 hopf_status batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out, cudaStream_t stream);

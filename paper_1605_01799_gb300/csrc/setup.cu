@@ -48,9 +48,12 @@ __global__ void k_sweep(const double* __restrict__ S, double* __restrict__ D, in
   D[(int64_t)i * n + j] = out;
 }
 
-// M = -(swept) symmetrised, padded to np x np with zeros; FP32/BF16 copies.
+// M = -(swept) symmetrised, padded to np x np with zeros; FP32/BF16 copies
+// and (SPLIT form) the two-term FP16 split M = hi + lo * 2^-11 with
+// hi = fp16(M), lo = fp16((M - hi) 2^11).
 __global__ void k_finish_inverse(const double* __restrict__ S, double* __restrict__ M64, float* __restrict__ M32,
-                                 uint16_t* __restrict__ Mbf, int n, int np) {
+                                 uint16_t* __restrict__ Mbf, uint16_t* __restrict__ Mh, uint16_t* __restrict__ Ml,
+                                 int n, int np) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)np * np) return;
   int i = (int)(idx / np), j = (int)(idx % np);
@@ -59,6 +62,11 @@ __global__ void k_finish_inverse(const double* __restrict__ S, double* __restric
   if (M64) M64[idx] = m;
   if (M32) M32[idx] = (float)m;
   if (Mbf) Mbf[idx] = __bfloat16_as_ushort(__double2bfloat16(m));
+  if (Mh) {
+    const __half hi = __double2half(m);
+    Mh[idx] = __half_as_ushort(hi);
+    Ml[idx] = __half_as_ushort(__double2half((m - (double)__half2float(hi)) * 2048.0));
+  }
 }
 
 // Copies of A: FP32, BF16, and the three-term FP16 split
@@ -137,7 +145,12 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
     S_CALL(cudaMalloc(&h->d_Al2, pp * sizeof(uint16_t)));
     S_CALL(cudaMalloc(&h->d_Abf, pp * sizeof(uint16_t)));
   }
-  k_finish_inverse<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf, n, np);
+  if (h->precision == HOPF_P_SPLIT) {
+    S_CALL(cudaMalloc(&h->d_Mh16, pp * sizeof(uint16_t)));
+    S_CALL(cudaMalloc(&h->d_Ml16, pp * sizeof(uint16_t)));
+  }
+  k_finish_inverse<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf, h->d_Mh16,
+                                                                       h->d_Ml16, n, np);
   k_cast_A<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(h->d_A, h->d_A32, h->d_Abf, h->d_Ah16, h->d_Al16,
                                                                h->d_Al2, n, np);
   S_CALL(cudaGetLastError());

@@ -17,6 +17,12 @@ import workloads as wl
 pytestmark = pytest.mark.gpu
 
 PHI_TOL, GRAD_MAX, GRAD_MED = 1e-6, 6e-6, 3e-6
+# The SPLIT form evaluates v = M r, whose error reaches the fixed point
+# amplified by |A + lambda I| (up to 11 here) where MIXED's error in A p enters
+# unamplified; the tensor cores' FP32 accumulation truncates (a bias of about
+# half an ulp per K = 16 step, 64 steps at n = 1024), so SPLIT's gradient
+# error sits near 1e-5 (measured 6.7e-6 at n = 384, 9.6e-6 at n = 1024).
+GRAD_BARS = {"FP32": (6e-6, 3e-6), "MIXED": (6e-6, 3e-6), "SPLIT": (2.5e-5, 1.2e-5)}
 # Relative stop |u^k - u^{k-1}|^2 <= TOL max(1, |u^k|^2).  FP32 storage of u
 # alone rounds by ~6e-8 relative, i.e. (6e-8)^2 ~ 4e-15 squared: 1e-13 keeps
 # the test a decade above that floor.
@@ -62,7 +68,7 @@ def _case(orc, n, B, h_kind, seed):
     return _REF[key]
 
 
-@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+@pytest.mark.parametrize("precision", ["FP32", "SPLIT", "MIXED"])
 @pytest.mark.parametrize("n,B,h_kind", [(128, 300, 1), (200, 129, 1), (384, 257, 0), (256, 64, 2), (129, 1, 1)])
 def test_dense_parity(hg, orc, precision, n, B, h_kind):
     """Ragged n (not a multiple of the 128-row tile) and ragged batches (not a
@@ -79,10 +85,11 @@ def test_dense_parity(hg, orc, precision, n, B, h_kind):
         raise
     torch.cuda.synchronize()
     ephi, eg = _errors(out, ref)
+    gmax, gmed = GRAD_BARS[precision]
     assert (out["status"].cpu().numpy() == hg.Q_OK).all()
     assert ephi.max() <= PHI_TOL, ephi.max()
-    assert eg.max() <= GRAD_MAX, eg.max()
-    assert np.median(eg) <= GRAD_MED, np.median(eg)
+    assert eg.max() <= gmax, eg.max()
+    assert np.median(eg) <= gmed, np.median(eg)
     dphidt = out["dphidt"].cpu().numpy()
     H = ref["dphidt"]
     assert np.allclose(dphidt, H, rtol=1e-5, atol=1e-5)
@@ -105,7 +112,7 @@ def test_dense_iteration_counts(hg, orc):
     assert np.abs(it - same["iters"]).max() <= 10
 
 
-@pytest.mark.parametrize("precision", ["FP32", "MIXED"])
+@pytest.mark.parametrize("precision", ["FP32", "SPLIT", "MIXED"])
 def test_dense_iterates_across_row_tiles(hg, orc, precision):
     """n = 384 (three row tiles per query): an item's product reads u^{k-1}
     over all rows while the other row tiles' epilogues write u^k, so the two
@@ -165,11 +172,13 @@ def test_dense_not_spd(hg):
     assert e.value.status == hg.HOPF_ENOTSPD
 
 
-def test_compaction_does_not_change_results(hg, orc):
+@pytest.mark.parametrize("precision,h_kind", [("MIXED", 1), ("SPLIT", 1), ("SPLIT", 2)])
+def test_compaction_does_not_change_results(hg, orc, precision, h_kind):
     """Packing the active queries into fewer column tiles as others converge
     moves a query's columns but not its arithmetic: with and without it the
     outputs agree bit for bit.  (2,000 queries: 16 column tiles, so several
-    packings happen.)"""
+    packings happen; the SPLIT form packs the operand pair of the iteration's
+    parity, and for l2 the M y plane that replaced y.)"""
     import torch
     n, B = 256, 2000
     A, Q, s = wl.spd_matrix(11801, 11802, n)
@@ -178,17 +187,15 @@ def test_compaction_does_not_change_results(hg, orc):
     t = wl.uniform(11805, B, 0.1, 3.0).astype(np.float32)
     t[::7] = 0.0  # queries that converge almost at once
     outs = []
+    wk = w if h_kind == 1 else None
     for on in (True, False):
-        try:
-            h = hg.Hopf(A, 1, w=w, tol=TOL, max_iter=3000, precision=hg.P_MIXED)
-        except hg.HopfError as e:
-            pytest.skip(str(e))
+        h = hg.Hopf(A, h_kind, w=wk, tol=TOL, max_iter=3000, precision=getattr(hg, "P_" + precision))
         h.set_compaction(on)
         outs.append(h.eval(_cuda(x), _cuda(t)))
     torch.cuda.synchronize()
     for key in ("phi", "grad", "iters", "status", "dphidt"):
         assert torch.equal(outs[0][key], outs[1][key]), key
-    ref = orc.Problem(A, 1, w=w, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
+    ref = orc.Problem(A, h_kind, w=wk, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
         x[:64].astype(np.float64), t[:64].astype(np.float64))
     phi = outs[0]["phi"][:64].cpu().numpy()
     assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= PHI_TOL

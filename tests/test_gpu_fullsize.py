@@ -29,16 +29,21 @@ def _sample(seed, count, total):
     return np.unique((wl.uniform(seed, 4 * count) * total).astype(np.int64))[:count]
 
 
-@pytest.mark.parametrize("precision", ["MIXED", "FP32"])
-def test_dense_n1024_b65536(hg, orc, precision):
-    """The metric's workload: n = 1024, 65,536 queries, weighted l1, tol 1e-13
-    (relative stop), exactly as bench.py runs it."""
+# (precision, relative stop tolerance, gradient bars max / median); the SPLIT
+# bars follow from its amplified accumulation error (tests/test_gpu_dense.py).
+DENSE_CASES = [("SPLIT", 1e-13, 2.5e-5, 1.2e-5), ("MIXED", 1e-13, 6e-6, 3e-6), ("FP32", 1e-13, 6e-6, 3e-6)]
+
+
+@pytest.mark.parametrize("precision,tol,gmax,gmed", DENSE_CASES)
+def test_dense_n1024_b65536(hg, orc, precision, tol, gmax, gmed):
+    """The metric's workload: n = 1024, 65,536 queries, weighted l1, relative
+    stop, exactly as bench.py runs it."""
     import torch
     n, B = 1024, 65536
     A, Q, s = wl.spd_matrix(2001, 2002, n)
     w = wl.uniform(2003, n, 0.5, 1.5)
     x, t = wl.queries_dense(n, B)
-    h = hg.Hopf(A, hg.H_WL1, w=w, tol=1e-13, max_iter=1000, precision=getattr(hg, "P_" + precision))
+    h = hg.Hopf(A, hg.H_WL1, w=w, tol=tol, max_iter=1000, precision=getattr(hg, "P_" + precision))
     out = h.eval(_cuda(x), _cuda(t))
     torch.cuda.synchronize()
     st = out["status"].cpu().numpy()
@@ -58,8 +63,8 @@ def test_dense_n1024_b65536(hg, orc, precision):
     ep = np.abs(phi[idx] - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
     eg = np.linalg.norm(g[idx] - ref["grad"], axis=1) / np.maximum(1, np.linalg.norm(ref["grad"], axis=1))
     assert ep.max() <= 1e-6, ep.max()
-    assert eg.max() <= 6e-6, eg.max()
-    assert np.median(eg) <= 3e-6, np.median(eg)
+    assert eg.max() <= gmax, eg.max()
+    assert np.median(eg) <= gmed, np.median(eg)
 
 
 def test_union_k16_n256_b16384(hg, orc):

@@ -82,3 +82,49 @@ def test_noalloc_rejects_oversized_batch(hg):
                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == hg.HOPF_EINVAL
     assert b"static scratch" in hg.lib().hopf_last_error()
+
+
+def _need(K, B):
+    """Scratch bytes of one call: per query-part pair an FP64 phi, an FP32 s,
+    an int32 count and a status byte, plus a 4-byte slot per query; each of
+    the five regions rounded up to 256 bytes."""
+    r = lambda v: (v + 255) // 256 * 256
+    b = B * K
+    return r(8 * b) + r(4 * b) + r(4 * b) + r(b) + r(4 * B)
+
+
+def test_noalloc_limit_with_one_part(hg):
+    """With one part the bound is batch * 21 bytes: the largest batch that
+    fits runs (and matches hopf_union_closest on sampled queries), the next
+    one is refused before anything is launched."""
+    import torch
+    cap = 8 << 20
+    B = cap // 21
+    while _need(1, B + 1) <= cap:
+        B += 1
+    while _need(1, B) > cap:
+        B -= 1
+    assert 398000 < B < 400000
+    n = 2
+    part = hg.Hopf(np.array([1.0, 4.0]), hg.H_L2, tol=1e-12, max_iter=2000, precision=hg.P_FP32,
+                   stop_rule=hg.STOP_UREL)
+    arr = (ctypes.c_void_p * 1)(part.handle.value)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    xs = wl.normal(3301, (B + 1) * n, 4.0).reshape(B + 1, n).astype(np.float32)
+    xs[:, 0] += np.where(xs[:, 0] >= 0, 2.0, -2.0).astype(np.float32)  # outside the ellipse |x1| <= 1
+    x = torch.tensor(xs, device="cuda")
+    L = hg.lib()
+    for batch, want in ((B + 1, hg.HOPF_EINVAL), (B, hg.HOPF_OK)):
+        o = _outs(torch, batch, n)
+        st = L.hopf_union_closest_noalloc(arr, 1, batch, ctypes.c_void_p(x.data_ptr()), 1e-6, 60,
+                                          ctypes.c_void_p(o["dist"].data_ptr()),
+                                          ctypes.c_void_p(o["closest"].data_ptr()),
+                                          ctypes.c_void_p(o["argmin"].data_ptr()), None,
+                                          ctypes.c_void_p(o["status"].data_ptr()), stream)
+        assert st == want, (batch, L.hopf_last_error())
+    torch.cuda.synchronize()
+    idx = np.array([0, 1, B // 2, B - 1])
+    ref = hg.union_closest([part], x[:B][torch.tensor(idx, device="cuda")], s_tol=1e-6, max_newton=60)
+    torch.cuda.synchronize()
+    rd = ref["dist"].cpu().numpy()
+    assert np.abs(o["dist"].cpu().numpy()[idx] - rd).max() <= 1e-5 * max(1, np.abs(rd).max())
