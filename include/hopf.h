@@ -327,6 +327,28 @@ hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph
  * Not thread-safe with concurrent hopf_eval calls on the same handle. */
 hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t stop);
 
+/* Limit of every bounded device-side wait of the dense solvers (their grid
+ * barriers and, on the tensor-core path, the waits on the TMA ring and the
+ * accumulator hand-offs), in SM clock cycles; 0 restores the default of 2^32
+ * (about two seconds).  A wait that runs out makes the kernel record an
+ * error word, drain its copies and MMAs, free its tensor memory and return:
+ * the call's queries then report HOPF_Q_ABORTED, and the handle stays usable.
+ * (The paper has no counterpart: this bounds the library's own waits.)  Not
+ * thread-safe with concurrent evaluations on the same handle. */
+hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles);
+
+/* Device allocator for the memory hopf_create and hopf_batch_create keep (the
+ * handle's copies of A, M and the weights, and their set-up scratch).
+ * alloc(bytes, ctx) returns device memory or NULL (then the create call
+ * frees what it already took and returns HOPF_ENOMEM); release(ptr, ctx)
+ * gives it back.  Both NULL restores cudaMalloc / cudaFree; exactly one NULL
+ * is HOPF_EINVAL.  Process-wide; each handle remembers the allocator it was
+ * made with and frees through it in hopf_destroy.  Install it while no create
+ * call runs on another thread.  (The paper has no counterpart.) */
+typedef void* (*hopf_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*hopf_free_fn)(void* ptr, void* ctx);
+hopf_status hopf_set_allocator(hopf_alloc_fn alloc, hopf_free_fn release, void* ctx);
+
 /* Query compaction of the dense tensor-core (MIXED) solver: as queries
  * converge, the still-active ones are packed into fewer column tiles so the
  * tensor cores work only on unconverged queries.  On by default; off gives the

@@ -32,7 +32,8 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_backward", "hopf_backward_params",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
-           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_last_error", "hopf_version"]
+           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_allocator",
+           "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -83,6 +84,8 @@ def lib():
             "hopf_eval_control": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
                                   ctypes.c_int),
             "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+            "hopf_set_wait_limit": ([_vp, _i64], ctypes.c_int),
+            "hopf_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_measure_pipes_scratch": ([], _sz),
             "hopf_measure_pipes": ([_vp, _sz, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_last_error": ([], ctypes.c_char_p),
@@ -232,6 +235,10 @@ class Hopf:
         sp = None if start is None else ctypes.c_void_p(start.cuda_event)
         ep = None if stop is None else ctypes.c_void_p(stop.cuda_event)
         _check(lib().hopf_profile_events(self.handle, sp, ep))
+
+    def set_wait_limit(self, cycles):
+        """Clock-cycle limit of the dense solvers' bounded waits (0: default)."""
+        _check(lib().hopf_set_wait_limit(self.handle, int(cycles)))
 
     def set_compaction(self, on):
         _check(lib().hopf_set_compaction(self.handle, 1 if on else 0))

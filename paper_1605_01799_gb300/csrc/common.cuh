@@ -43,8 +43,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Bounded spin limit: about a few seconds at most on a loaded GPU.
-constexpr unsigned long long kSpinLimit = 1ull << 25;
+// Default limit of every bounded device-side wait, in SM clock cycles (about
+// two seconds at 2 GHz); a handle may set its own (hopf_set_wait_limit).
+constexpr long long kWaitLimitCycles = 1ll << 32;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -53,10 +54,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
-// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded: on
-// timeout the CTA records ERR_BARRIER_TIMEOUT in *err and returns false, and
-// the caller leaves its loop; nothing spins forever.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded by
+// `limit` clock cycles: on timeout the CTA records ERR_BARRIER_TIMEOUT in *err
+// and returns false, and the caller leaves its loop; nothing spins forever.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                                             long long limit = kWaitLimitCycles) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -70,8 +72,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
       atomicAdd(bar + 1, 1u);
     } else {
       unsigned long long spins = 0;
+      const long long t0 = clock64();
       while (ld_acquire_u32(bar + 1) == gen) {
-        if (++spins > kSpinLimit) {
+        ++spins;
+        if (clock64() - t0 > limit) {
           atomicExch(err, ERR_BARRIER_TIMEOUT);
           s_ok = 0;
           break;

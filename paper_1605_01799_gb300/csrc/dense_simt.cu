@@ -38,6 +38,7 @@ struct SimtArgs {
   const float* w;   // [np] weights (1 when unweighted / padding)
   int n, np, rt, ct, h_kind, max_iter;
   float lam, tol;
+  long long wait_limit;  // clock cycles of every bounded wait
   DenseWs ws;
   float* grad;      // [B][n] user output
   const float* x;   // [B][n] the caller's queries (terminal point)
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_simt(SimtArgs a) {
         }
       }
     }
-    if (!grid_barrier(W.bar, gridDim.x, W.err)) return;
+    if (!grid_barrier(W.bar, gridDim.x, W.err, a.wait_limit)) return;
     const unsigned active = ld_acquire_u32(W.bar + 2 + (k % 3));
     if (active == 0) break;
   }
@@ -394,6 +395,7 @@ hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const flo
   a.ct = (int)(w.B_pad / BN);
   a.h_kind = h->h_kind;
   a.max_iter = h->max_iter;
+  a.wait_limit = h->wait_limit > 0 ? h->wait_limit : kWaitLimitCycles;
   a.lam = (float)h->lambda;
   a.tol = (float)h->tol;
   a.ws = w;

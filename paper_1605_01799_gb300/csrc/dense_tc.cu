@@ -119,6 +119,7 @@ struct TcArgs {
   int64_t B, B_pad;
   int n, np, rt, ct, h_kind, max_iter, form, compact;
   float lam, tol;
+  long long wait_limit;  // clock cycles of every bounded wait
 };
 
 // Per-CTA view of the slot layout; every CTA updates it identically.
@@ -151,12 +152,14 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2^32 cycles, or as soon as the CTA aborts.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort) {
+// Bounded wait: gives up after the kernel's wait limit (clock cycles; 2^32 by
+// default), or as soon as the CTA aborts.
+__device__ __forceinline__ bool mbar_wait_lim(uint32_t bar, uint32_t parity, int* err, volatile int* abort,
+                                              long long limit) {
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > (1ll << 32)) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, ERR_MBAR_TIMEOUT);
       *abort = 1;
       return false;
@@ -348,7 +351,7 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
     for (int kb = 0; kb < nk; kb += kstep) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
         const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
-        if (!mbar_wait(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort)) return;
+        if (!mbar_wait_lim(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
         const uint32_t full = sa(&S.full[s]);
         mbar_expect_tx(full, bytes);
         uint8_t* base = stages + (size_t)s * STAGE_BYTES;
@@ -397,7 +400,7 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
     if (ph != PH_F) st.nb ^= 1;
     for (uint32_t b = 0; b < 2; ++b) {
       if (ph != PH_F && b != buf) continue;
-      if (!mbar_wait(sa(&S.tempty[b]), (st.ue[b] & 1) ^ 1, a.err, &S.abort)) return;
+      if (!mbar_wait_lim(sa(&S.tempty[b]), (st.ue[b] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
       ++st.ue[b];
     }
     tc_fence_after();
@@ -411,7 +414,7 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
         // in the second buffer.  TMEM: D1 slots at 0 and 128, D2 at 256, D3 at 384.
         const uint32_t chunk = kb >> 1, slot = chunk & 1;
         if ((kb & 1) == 0) {
-          if (!mbar_wait(sa(&S.cempty[slot]), (st.ce[slot] & 1) ^ 1, a.err, &S.abort)) return;
+          if (!mbar_wait_lim(sa(&S.cempty[slot]), (st.ce[slot] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
           ++st.ce[slot];
           tc_fence_after();
         }
@@ -419,7 +422,7 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
         // sub-stage X: {A1, A2 | p1, p2};  sub-stage Y: {A1, A3 | p3, p1}
         for (int sub = 0; sub < 2; ++sub, ++st.kb) {
           const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
-          if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
+          if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
           tc_fence_after();
           const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
           const uint32_t idesc = idesc_f16(0);
@@ -453,7 +456,7 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
       if (cfg.na == 1 && (kb & 1)) continue;  // B, P: the stage of kb holds kb + 1 too
       const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
       ++st.kb;
-      if (!mbar_wait(sa(&S.full[s]), suse & 1, a.err, &S.abort)) return;
+      if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
       tc_fence_after();
       const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
       if (cfg.na == 1) {
@@ -710,7 +713,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     load(jbase);
     // a failed wait skips the work of this item but keeps the warp in step
     // with the others at the named barriers below
-    const bool good = mbar_wait(sa(&S.tfull[buf]), use & 1, a.err, &S.abort);
+    const bool good = mbar_wait_lim(sa(&S.tfull[buf]), use & 1, a.err, &S.abort, a.wait_limit);
     if (good) tc_fence_after();
     for (int j0 = jbase; good && j0 < jbase + CPW; j0 += 16) {
       if (j0 != jbase) load(j0);
@@ -929,7 +932,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     bool good = true;
     for (int chunk = 0; chunk < nk / 2; ++chunk) {
       const uint32_t slot = chunk & 1;
-      good = good && mbar_wait(sa(&S.cfull[slot]), st.cf[slot] & 1, a.err, &S.abort);
+      good = good && mbar_wait_lim(sa(&S.cfull[slot]), st.cf[slot] & 1, a.err, &S.abort, a.wait_limit);
       ++st.cf[slot];
       if (good) {
         tc_fence_after();
@@ -947,7 +950,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
       ++st.ce[slot];
     }
     const uint32_t use = st.uf[0]++;
-    good = good && mbar_wait(sa(&S.tfull[0]), use & 1, a.err, &S.abort);
+    good = good && mbar_wait_lim(sa(&S.tfull[0]), use & 1, a.err, &S.abort, a.wait_limit);
     if (good) tc_fence_after();
     const int row = r * BM + rloc;
     const float wr = a.w[row];
@@ -1245,13 +1248,13 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     // k - 2, which every CTA has left)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
     run(a.form == FORM_MIXED ? PH_A : a.form == FORM_SPLIT ? PH_S : PH_P, k);
-    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
     const int n_active = (int)ld_acquire_u32(a.bar + 2 + (k % 3));
     if (n_active == 0) break;
     if (a.form == FORM_BF16) continue;
     if (a.form == FORM_MIXED) {
       run(PH_B, k);
-      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
     }
     // every CTA takes the same decision from the same count: compact when it
     // frees a quarter of the column tiles in use and shortens each phase by
@@ -1265,7 +1268,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
         need + (cx.ct_on + 3) / 4 <= cx.ct_on && fewer_rounds) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
-      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err))) break;
+      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
       cx.cb ^= 1;
       cx.ct_on = need;
       cx.fresh = 1;
@@ -1276,7 +1279,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
   if (ok) {
     if (warp >= 2) prep_final_operand(a);
     proxy_fence_global();
-    ok = grid_barrier(a.bar, gridDim.x, a.err);
+    ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit);
   }
   if (ok) run(PH_F, 0);
 
@@ -1459,6 +1462,7 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.ct = (int)(w.B_pad / BN);
   a.h_kind = h->h_kind;
   a.max_iter = h->max_iter;
+  a.wait_limit = h->wait_limit > 0 ? h->wait_limit : kWaitLimitCycles;
   a.form = form;
   // the BF16 form keeps its r double buffer in set 0 and runs without compaction
   a.compact = form != FORM_BF16 && h->compact && a.ct <= 1024;  // the scan table holds 1,024 tiles

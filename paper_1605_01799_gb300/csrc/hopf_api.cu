@@ -91,8 +91,7 @@ static void free_handle(hopf_handle h) {
   void* ptrs[] = {h->d_A, h->d_c, h->d_w, h->d_cf, h->d_wf, h->d_af, h->d_M64, h->d_M32, h->d_A32,
                   h->d_Mbf, h->d_Ah16, h->d_Al16, h->d_Al2, h->d_Abf, h->d_Mh16, h->d_Ml16, h->d_P, h->d_PT,
                   h->d_Pf, h->d_PTf};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(h->alloc, p);
   delete h;
 }
 
@@ -146,6 +145,19 @@ hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph
   set_error("");
   if (!b) return fail(HOPF_EINVAL, "hopf_batch_info: null batch");
   return batch_info(b, nstreams, used_graph, tuned_ms);
+}
+
+hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles) {
+  set_error("");
+  if (!h) return fail(HOPF_EINVAL, "hopf_set_wait_limit: null handle");
+  if (cycles < 0) return fail(HOPF_EINVAL, "hopf_set_wait_limit: cycles must be >= 0");
+  h->wait_limit = cycles;
+  return HOPF_OK;
+}
+
+hopf_status hopf_set_allocator(hopf_alloc_fn alloc, hopf_free_fn release, void* ctx) {
+  set_error("");
+  return set_allocator(alloc, release, ctx);
 }
 
 hopf_status hopf_set_compaction(hopf_handle h, int32_t on) {
@@ -235,6 +247,7 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
   }
 
   hopf_handle h = new hopf_handle_s();
+  h->alloc = current_allocator();
   h->n = n;
   h->n_pad = (int)round_up(n, 128);
   h->a_kind = jnorm ? HOPF_A_DIAG : d.a_kind;
@@ -255,7 +268,7 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
 
 #define H_ALLOC(ptr, bytes)                           \
   do {                                                \
-    cudaError_t e2 = cudaMalloc((void**)&(ptr), (bytes)); \
+    cudaError_t e2 = dev_alloc(h->alloc, (void**)&(ptr), (bytes)); \
     if (e2 != cudaSuccess) {                          \
       free_handle(h);                                 \
       return cuda_fail(e2, "cudaMalloc");             \

@@ -8,6 +8,14 @@
 
 #include "../../include/hopf.h"
 
+// Device allocator of handle memory: cudaMalloc / cudaFree, or the functions
+// installed by hopf_set_allocator.
+struct Allocator {
+  hopf_alloc_fn alloc;
+  hopf_free_fn release;
+  void* ctx;
+};
+
 struct hopf_handle_s {
   int n = 0;          // problem dimension
   int n_pad = 0;      // leading dimension of padded device arrays (multiple of 128)
@@ -46,6 +54,8 @@ struct hopf_handle_s {
   uint16_t* d_Ml16 = nullptr;  // FP16((M - FP16(M)) * 2^11) (SPLIT form)
   cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
   int compact = 1;  // tensor-core path: pack active queries as others converge
+  long long wait_limit = 0;  // clock cycles of the dense solvers' bounded waits (0: the default)
+  Allocator alloc = {nullptr, nullptr, nullptr};  // the allocator this handle's memory came from
 };
 
 namespace hopf {
@@ -63,6 +73,10 @@ hopf_status cuda_fail(cudaError_t e, const char* what);
 
 // ---- setup (setup.cu) ----
 hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream);
+hopf_status set_allocator(hopf_alloc_fn alloc, hopf_free_fn release, void* ctx);
+Allocator current_allocator();
+cudaError_t dev_alloc(const Allocator& a, void** p, size_t bytes);
+void dev_free(const Allocator& a, void* p);
 
 // ---- diagonal path (diag.cu) ----
 size_t diag_workspace(const hopf_handle h, int64_t batch);

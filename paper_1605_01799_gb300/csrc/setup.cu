@@ -11,8 +11,16 @@
 //   S'_ij = S_ij - S_ik S_kj / S_kk            (i, j != k),
 // and sweeping every pivot of an SPD matrix yields -S^{-1}.  The pivots are the
 // Schur complements, so a non-positive pivot proves A + lambda I is not SPD.
+// The pivots go 64 at a time (a block sweep): n / 64 rounds of three
+// launches, the bulk of the 2 n^3 FP64 flop in a symmetric rank-64 update.
+//
+// Device memory of a handle comes from cudaMalloc, or from the allocator the
+// caller installed with hopf_set_allocator (captured by each handle, which
+// frees with it).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "hopf_internal.h"
@@ -28,24 +36,164 @@ __global__ void k_load_shifted(const double* __restrict__ A, double* __restrict_
   S[idx] = a + (i == j ? lam : 0.0);
 }
 
-__global__ void k_sweep(const double* __restrict__ S, double* __restrict__ D, int n, int k, int* err) {
-  if (*((volatile int*)err) != ERR_NONE) return;
-  const double dkk = S[(int64_t)k * n + k];
-  if (!(dkk > 0.0)) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, ERR_NOT_SPD);
-    return;
+// ---- blocked sweep ----------------------------------------------------------
+// Sweeping a block K of pivots at once is the composition of its single-pivot
+// sweeps:
+//   S'_KK = -S_KK^{-1},  S'_KJ = S_KK^{-1} S_KJ,  S'_IK = S_IK S_KK^{-1},
+//   S'_IJ = S_IJ - S_IK S_KK^{-1} S_KJ = S_IJ - S_KI^T T_KJ  (T = S_KK^{-1} S_K:),
+// which keeps S symmetric.  Per block of kSB pivots: one CTA sweeps the pivot
+// block in shared memory (checking each pivot), a second kernel forms T and
+// keeps the old rows of K, and a third applies the rank-kSB update to the
+// tiles on and above the diagonal, writing each tile and its mirror.
+constexpr int kSB = 64;  // pivots per block = tile edge of the update
+
+// Sweep the pivots of the diagonal block K = [k0, k0 + nb) in shared memory;
+// out = -S_KK^{-1} (nb x nb, leading dimension kSB).
+__global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restrict__ S, int n, int k0, int nb,
+                                                         double* __restrict__ out, int* err) {
+  __shared__ double B[kSB][kSB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    B[i][j] = S[(int64_t)(k0 + i) * n + k0 + j];
   }
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || j >= n) return;
-  const double inv = 1.0 / dkk;
-  const double aik = S[(int64_t)i * n + k], akj = S[(int64_t)k * n + j];
-  double out;
-  if (i == k && j == k) out = -inv;
-  else if (i == k) out = akj * inv;
-  else if (j == k) out = aik * inv;
-  else out = S[(int64_t)i * n + j] - aik * akj * inv;
-  D[(int64_t)i * n + j] = out;
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    const double dkk = B[k][k];
+    if (!(dkk > 0.0)) {  // a Schur-complement pivot of A + lambda I: not SPD
+      if (threadIdx.x == 0) {
+        bad = 1;
+        atomicExch(err, ERR_NOT_SPD);
+      }
+      break;  // dkk is the same for every thread: all leave together
+    }
+    const double inv = 1.0 / dkk;
+    double nv[kSB * kSB / 256 + 1];
+    int cnt = 0;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x, ++cnt) {
+      const int i = e / nb, j = e % nb;
+      double o;
+      if (i == k && j == k) o = -inv;
+      else if (i == k) o = B[k][j] * inv;
+      else if (j == k) o = B[i][k] * inv;
+      else o = B[i][j] - B[i][k] * B[k][j] * inv;
+      nv[cnt] = o;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x, ++cnt) B[e / nb][e % nb] = nv[cnt];
+    __syncthreads();
+  }
+  if (bad) return;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) out[(e / nb) * kSB + e % nb] = B[e / nb][e % nb];
+}
+
+// T[:, J] = -Kneg S[K, J] for one 64-column tile J (T = S_KK^{-1} S_K:), and the
+// old rows of K kept in Sold.  Both nb x n, leading dimension n.
+__global__ void __launch_bounds__(256) k_sweep_block_T(const double* __restrict__ S, int n, int k0, int nb,
+                                                       const double* __restrict__ Kneg, double* __restrict__ T,
+                                                       double* __restrict__ Sold, const int* err) {
+  if (*((volatile const int*)err) != ERR_NONE) return;
+  __shared__ double Sk[kSB][kSB + 1];
+  const int j0 = blockIdx.x * kSB;
+  const int w = min(kSB, n - j0);
+  for (int e = threadIdx.x; e < nb * kSB; e += blockDim.x) {
+    const int k = e / kSB, j = e % kSB;
+    const double v = j < w ? S[(int64_t)(k0 + k) * n + j0 + j] : 0.0;
+    Sk[k][j] = v;
+    if (j < w) Sold[(int64_t)k * n + j0 + j] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nb * kSB; e += blockDim.x) {
+    const int i = e / kSB, j = e % kSB;
+    if (j >= w) continue;
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc += __ldg(Kneg + i * kSB + k) * Sk[k][j];
+    T[(int64_t)i * n + j0 + j] = -acc;
+  }
+}
+
+// Rank-nb update of tile (I, J), I <= J, 64 x 64, with its mirror (J, I):
+//   I, J != K:  S_IJ -= Sold_K,I^T T_K,J
+//   J == K:     S_IK = T_K,I^T  (I != K);  S_KK = Kneg
+// Each thread owns a 4 x 4 block of the tile.
+__global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__ S, int n, int kt, int nb,
+                                                            const double* __restrict__ Kneg,
+                                                            const double* __restrict__ T,
+                                                            const double* __restrict__ Sold, const int* err) {
+  if (*((volatile const int*)err) != ERR_NONE) return;
+  // blockIdx.x enumerates the tiles on and above the diagonal, row by row
+  const int nt = (n + kSB - 1) / kSB;
+  int I = 0, rem = blockIdx.x;
+  while (rem >= nt - I) {
+    rem -= nt - I;
+    ++I;
+  }
+  const int J = I + rem;
+  const int i0 = I * kSB, j0 = J * kSB;
+  const int hi = min(kSB, n - i0), wj = min(kSB, n - j0);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double out[4][4];
+  if (I == kt || J == kt) {
+    // row / column block K: copies of T (or -S_KK^{-1} on the diagonal)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * ty + r, j = 4 * tx + c;
+        double v = 0.0;
+        if (i < hi && j < wj) {
+          if (I == kt && J == kt) v = Kneg[i * kSB + j];
+          else if (I == kt) v = T[(int64_t)i * n + j0 + j];  // S_KJ = T_KJ
+          else v = T[(int64_t)j * n + i0 + i];                // S_IK = T_KI^T
+        }
+        out[r][c] = v;
+      }
+  } else {
+    constexpr int KC = 32;            // k rows staged per round (32 KB of shared memory)
+    __shared__ double As[KC][kSB];    // As[k][i] = Sold[kc + k][i0 + i]
+    __shared__ double Bs[KC][kSB];    // Bs[k][j] = T[kc + k][j0 + j]
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * ty + r, j = 4 * tx + c;
+        out[r][c] = (i < hi && j < wj) ? S[(int64_t)(i0 + i) * n + j0 + j] : 0.0;
+      }
+    for (int kc = 0; kc < nb; kc += KC) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < KC * kSB; e += blockDim.x) {
+        const int k = e / kSB, c = e % kSB;
+        const bool kin = kc + k < nb;
+        As[k][c] = (kin && c < hi) ? Sold[(int64_t)(kc + k) * n + i0 + c] : 0.0;
+        Bs[k][c] = (kin && c < wj) ? T[(int64_t)(kc + k) * n + j0 + c] : 0.0;
+      }
+      __syncthreads();
+      for (int k = 0; k < KC; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[k][4 * ty + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = Bs[k][4 * tx + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) out[r][c] = fma(-a[r], b[c], out[r][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = 4 * ty + r, j = 4 * tx + c;
+      if (i < hi && j < wj) {
+        S[(int64_t)(i0 + i) * n + j0 + j] = out[r][c];
+        if (I != J) S[(int64_t)(j0 + j) * n + i0 + i] = out[r][c];
+      }
+    }
 }
 
 // M = -(swept) symmetrised, padded to np x np with zeros; FP32/BF16 copies
@@ -93,16 +241,47 @@ __global__ void k_cast_A(const double* __restrict__ A, float* __restrict__ A32, 
   }
 }
 
+static std::mutex g_alloc_mu;
+static Allocator g_alloc = {nullptr, nullptr, nullptr};
+
+hopf_status set_allocator(hopf_alloc_fn alloc, hopf_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(HOPF_EINVAL, "hopf_set_allocator: give both functions, or neither (cudaMalloc / cudaFree)");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc = {alloc, release, ctx};
+  return HOPF_OK;
+}
+
+Allocator current_allocator() {
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  return g_alloc;
+}
+
+cudaError_t dev_alloc(const Allocator& a, void** p, size_t bytes) {
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  *p = a.alloc(bytes, a.ctx);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void dev_free(const Allocator& a, void* p) {
+  if (!p) return;
+  if (a.release) a.release(p, a.ctx);
+  else cudaFree(p);
+}
+
 hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream) {
   const int n = h->n, np = h->n_pad;
   const size_t nn = (size_t)n * n, pp = (size_t)np * np;
-  double *S0 = nullptr, *S1 = nullptr;
+  const Allocator& al = h->alloc;
+  double *S0 = nullptr, *Tm = nullptr, *Sold = nullptr, *Kneg = nullptr;
   int* err = nullptr;
   hopf_status st = HOPF_OK;
   auto cleanup = [&]() {
-    if (S0) cudaFree(S0);
-    if (S1) cudaFree(S1);
-    if (err) cudaFree(err);
+    dev_free(al, S0);
+    dev_free(al, Tm);
+    dev_free(al, Sold);
+    dev_free(al, Kneg);
+    dev_free(al, err);
   };
 #define S_CALL(call)                   \
   do {                                 \
@@ -112,20 +291,24 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
       return cuda_fail(e_, #call);     \
     }                                  \
   } while (0)
-  S_CALL(cudaMalloc(&h->d_A, nn * sizeof(double)));
+#define S_ALLOC(ptr, bytes) S_CALL(dev_alloc(al, (void**)&(ptr), (bytes)))
+  S_ALLOC(h->d_A, nn * sizeof(double));
   S_CALL(cudaMemcpyAsync(h->d_A, A_host, nn * sizeof(double), cudaMemcpyHostToDevice, stream));
-  S_CALL(cudaMalloc(&S0, nn * sizeof(double)));
-  S_CALL(cudaMalloc(&S1, nn * sizeof(double)));
-  S_CALL(cudaMalloc(&err, sizeof(int)));
+  S_ALLOC(S0, nn * sizeof(double));
+  S_ALLOC(Tm, (size_t)kSB * n * sizeof(double));
+  S_ALLOC(Sold, (size_t)kSB * n * sizeof(double));
+  S_ALLOC(Kneg, (size_t)kSB * kSB * sizeof(double));
+  S_ALLOC(err, sizeof(int));
   S_CALL(cudaMemsetAsync(err, 0, sizeof(int), stream));
   const int tb = 256;
   k_load_shifted<<<(unsigned)((nn + tb - 1) / tb), tb, 0, stream>>>(h->d_A, S0, n, h->lambda);
-  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
-  for (int k = 0; k < n; ++k) {
-    k_sweep<<<grd, blk, 0, stream>>>(S0, S1, n, k, err);
-    double* tmp = S0;
-    S0 = S1;
-    S1 = tmp;
+  const int nt = (n + kSB - 1) / kSB;
+  const unsigned upper = (unsigned)(nt * (nt + 1) / 2);
+  for (int kt = 0; kt < nt; ++kt) {
+    const int k0 = kt * kSB, nb = n - k0 < kSB ? n - k0 : kSB;
+    k_sweep_block_inv<<<1, 256, 0, stream>>>(S0, n, k0, nb, Kneg, err);
+    k_sweep_block_T<<<(unsigned)nt, 256, 0, stream>>>(S0, n, k0, nb, Kneg, Tm, Sold, err);
+    k_sweep_block_update<<<upper, 256, 0, stream>>>(S0, n, kt, nb, Kneg, Tm, Sold, err);
   }
   S_CALL(cudaGetLastError());
   int herr = 0;
@@ -136,18 +319,18 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
     return fail(HOPF_ENOTSPD, "hopf_create: A + lambda I is not symmetric positive definite");
   }
   const bool simt = h->precision == HOPF_P_FP32;
-  S_CALL(cudaMalloc(&h->d_M32, pp * sizeof(float)));
-  S_CALL(cudaMalloc(&h->d_A32, pp * sizeof(float)));
+  S_ALLOC(h->d_M32, pp * sizeof(float));
+  S_ALLOC(h->d_A32, pp * sizeof(float));
   if (!simt) {
-    S_CALL(cudaMalloc(&h->d_Mbf, pp * sizeof(uint16_t)));
-    S_CALL(cudaMalloc(&h->d_Ah16, pp * sizeof(uint16_t)));
-    S_CALL(cudaMalloc(&h->d_Al16, pp * sizeof(uint16_t)));
-    S_CALL(cudaMalloc(&h->d_Al2, pp * sizeof(uint16_t)));
-    S_CALL(cudaMalloc(&h->d_Abf, pp * sizeof(uint16_t)));
+    S_ALLOC(h->d_Mbf, pp * sizeof(uint16_t));
+    S_ALLOC(h->d_Ah16, pp * sizeof(uint16_t));
+    S_ALLOC(h->d_Al16, pp * sizeof(uint16_t));
+    S_ALLOC(h->d_Al2, pp * sizeof(uint16_t));
+    S_ALLOC(h->d_Abf, pp * sizeof(uint16_t));
   }
   if (h->precision == HOPF_P_SPLIT) {
-    S_CALL(cudaMalloc(&h->d_Mh16, pp * sizeof(uint16_t)));
-    S_CALL(cudaMalloc(&h->d_Ml16, pp * sizeof(uint16_t)));
+    S_ALLOC(h->d_Mh16, pp * sizeof(uint16_t));
+    S_ALLOC(h->d_Ml16, pp * sizeof(uint16_t));
   }
   k_finish_inverse<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf, h->d_Mh16,
                                                                        h->d_Ml16, n, np);
@@ -156,6 +339,7 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
   S_CALL(cudaGetLastError());
   S_CALL(cudaStreamSynchronize(stream));
   cleanup();
+#undef S_ALLOC
 #undef S_CALL
   return st;
 }

@@ -194,6 +194,19 @@ def test_figure_grid_and_level_lines():
     assert (img[4] == 0).all() and (img[3] != 0).all()  # 4 -> 5 crosses a multiple of 5
 
 
+def test_allocator_and_wait_limit_arguments(hg):
+    """One allocator function without the other, a null handle or a negative
+    limit: refused before anything touches the device."""
+    import ctypes
+    L = hg.lib()
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+    fa = ALLOC(lambda n, c: None)
+    assert L.hopf_set_allocator(ctypes.cast(fa, ctypes.c_void_p), None, None) == hg.HOPF_EINVAL
+    assert b"both" in L.hopf_last_error()
+    assert L.hopf_set_allocator(None, None, None) == hg.HOPF_OK
+    assert L.hopf_set_wait_limit(None, 100) == hg.HOPF_EINVAL
+
+
 def test_backward_params_null_handle(hg):
     L = hg.lib()
     assert L.hopf_backward_params(None, 4, None, None, None, None, None, None, None, None) == hg.HOPF_EINVAL
