@@ -267,6 +267,19 @@ hopf_status hopf_union_closest_noalloc(const hopf_handle* parts, int32_t K, int6
 hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
                           float* g_t, float* g_A, cudaStream_t stream);
 
+/* hopf_backward with the dense g_A on the tensor cores (tcgen05): the same
+ * outputs, with g_A = -1/2 V^T diag(g) V computed from two-term FP16 splits of
+ * g V and V (about 2^-22 per product), the main product promoted from tensor
+ * memory to registers every 512 queries and the partial products of each
+ * 4,096-query range summed in FP64.  workspace: device memory of at least
+ * hopf_backward_workspace_size bytes (256-byte aligned), owned by the caller;
+ * nothing is allocated.  Without a dense A (or with g_A NULL or batch 0) it
+ * is hopf_backward.  A bounded device wait that gives up (see
+ * hopf_set_wait_limit) leaves NaN in g_A. */
+hopf_status hopf_backward_workspace_size(hopf_handle h, int64_t batch, size_t* bytes);
+hopf_status hopf_backward_ws(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
+                             float* g_t, float* g_A, void* workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* Gradients of L = sum_q g_phi[q] phi_q with respect to the problem's other
  * parameters, by the same envelope argument (phi = <x - c, p> - J*_0(p) - c0
  * - t H(p) at the minimiser p = vstar):

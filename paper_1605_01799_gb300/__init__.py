@@ -29,7 +29,7 @@ Q_OK, Q_NOT_CONVERGED, Q_NONFINITE, Q_ABORTED, Q_BAD_INPUT = 0, 1, 2, 3, 4
 
 EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "hopf_eval_f64",
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
-           "hopf_backward", "hopf_backward_params",
+           "hopf_backward", "hopf_backward_params", "hopf_backward_workspace_size", "hopf_backward_ws",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
            "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_allocator",
@@ -74,6 +74,8 @@ def lib():
                                            ctypes.c_int),
             "hopf_backward": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "hopf_backward_params": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "hopf_backward_workspace_size": ([_vp, _i64, ctypes.POINTER(_sz)], ctypes.c_int),
+            "hopf_backward_ws": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_profile_events": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_set_compaction": ([_vp, _i32], ctypes.c_int),
             "hopf_batch_create": ([ctypes.POINTER(hopf_desc), _i32, ctypes.POINTER(_vp), _vp], ctypes.c_int),
@@ -243,7 +245,11 @@ class Hopf:
     def set_compaction(self, on):
         _check(lib().hopf_set_compaction(self.handle, 1 if on else 0))
 
-    def backward(self, g_phi, vstar, want_x=True, want_t=True, want_A=True, stream=None):
+    def backward(self, g_phi, vstar, want_x=True, want_t=True, want_A=True, stream=None, tensor_cores=True):
+        """Envelope-theorem gradients (hopf_backward).  For a dense A, g_A runs
+        on the tensor cores (hopf_backward_ws, with a workspace kept between
+        calls of the same batch size) unless tensor_cores is False, which
+        selects the FP32 CUDA-core kernel."""
         import torch
         B = vstar.shape[0]
         gx = torch.empty_like(vstar) if want_x else None
@@ -252,6 +258,15 @@ class Hopf:
         if want_A and self.j_kind == J_QUAD:  # a norm J has no matrix
             shape = (self.n, self.n) if self.a_kind == A_DENSE else (self.n,)
             gA = torch.empty(shape, dtype=torch.float32, device=vstar.device)
+        if gA is not None and self.a_kind == A_DENSE and B > 0 and tensor_cores:
+            b = ctypes.c_size_t()
+            _check(lib().hopf_backward_workspace_size(self.handle, B, ctypes.byref(b)))
+            ws = getattr(self, "_bwd_ws", None)
+            if ws is None or ws.numel() < b.value or ws.device != vstar.device:
+                ws = self._bwd_ws = torch.empty(b.value, dtype=torch.uint8, device=vstar.device)
+            _check(lib().hopf_backward_ws(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
+                                          _ptr(ws), ws.numel(), _stream(stream)))
+            return gx, gt, gA
         _check(lib().hopf_backward(self.handle, B, _ptr(g_phi), _ptr(vstar), _ptr(gx), _ptr(gt), _ptr(gA),
                                    _stream(stream)))
         return gx, gt, gA

@@ -529,4 +529,26 @@ hopf_status hopf_backward(hopf_handle h, int64_t batch, const float* g_phi, cons
   return backward(h, batch, g_phi, vstar, g_x, g_t, g_A, stream);
 }
 
+hopf_status hopf_backward_workspace_size(hopf_handle h, int64_t batch, size_t* bytes) {
+  set_error("");
+  if (!h || !bytes || batch < 0) return fail(HOPF_EINVAL, "hopf_backward_workspace_size: bad argument");
+  *bytes = h->a_kind == HOPF_A_DENSE && h->j_kind == 0 ? syrk_workspace(h, batch) : 0;
+  return HOPF_OK;
+}
+
+hopf_status hopf_backward_ws(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x,
+                             float* g_t, float* g_A, void* workspace, size_t ws_bytes, cudaStream_t stream) {
+  set_error("");
+  if (!h || batch < 0) return fail(HOPF_EINVAL, "hopf_backward_ws: bad argument");
+  if (!g_A || h->a_kind != HOPF_A_DENSE || h->j_kind != 0 || batch == 0)
+    return hopf_backward(h, batch, g_phi, vstar, g_x, g_t, g_A, stream);
+  if (!g_phi || !vstar) return fail(HOPF_EINVAL, "hopf_backward_ws: null g_phi or vstar");
+  if (!workspace) return fail(HOPF_EINVAL, "hopf_backward_ws: null workspace");
+  if (g_x || g_t) {
+    hopf_status st = backward(h, batch, g_phi, vstar, g_x, g_t, nullptr, stream);
+    if (st != HOPF_OK) return st;
+  }
+  return backward_dense_tc(h, batch, g_phi, vstar, g_A, workspace, ws_bytes, stream);
+}
+
 }  // extern "C"

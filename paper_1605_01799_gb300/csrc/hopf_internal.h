@@ -150,6 +150,11 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
                           float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,
                           float* xfin = nullptr);
 
+// ---- backward on the tensor cores (syrk_tc.cu) ----
+size_t syrk_workspace(const hopf_handle h, int64_t batch);
+hopf_status backward_dense_tc(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_A,
+                              void* ws, size_t ws_bytes, cudaStream_t stream);
+
 // ---- backward (backward.cu) ----
 hopf_status backward(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_x, float* g_t,
                      float* g_A, cudaStream_t stream);

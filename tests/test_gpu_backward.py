@@ -24,8 +24,14 @@ def _cuda(a):
     return torch.tensor(np.ascontiguousarray(a), device="cuda")
 
 
-@pytest.mark.parametrize("n,B", [(128, 300), (200, 77)])
-def test_backward_dense_matches_oracle(hg, orc, n, B):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("n,B", [(128, 300), (200, 77), (384, 5000)])
+def test_backward_dense_matches_oracle(hg, orc, n, B, tensor_cores):
+    """g_x, g_t and the dense g_A = -1/2 V^T diag(g) V against the oracle's
+    FP64 sums over the same minimisers, on the tensor cores (two-term FP16
+    splits, chunked promotion, FP64 sums of K ranges: n = 384 has off-diagonal
+    tiles and their mirrors, 5,000 queries two K ranges and a ragged last
+    k-block) and on the FP32 CUDA cores."""
     import torch
     A, Q, s = wl.spd_matrix(12001 + n, 12002, n)
     x = wl.normal(12003, B * n, 2.0).reshape(B, n).astype(np.float32)
@@ -33,7 +39,7 @@ def test_backward_dense_matches_oracle(hg, orc, n, B):
     g = wl.normal(12005, B, 1.0).astype(np.float32)
     h = hg.Hopf(A, hg.H_L1, tol=1e-13, max_iter=3000, precision=hg.P_FP32)
     out = h.eval(_cuda(x), _cuda(t))
-    gx, gt, gA = h.backward(_cuda(g), out["grad"])
+    gx, gt, gA = h.backward(_cuda(g), out["grad"], tensor_cores=tensor_cores)
     torch.cuda.synchronize()
     v = out["grad"].cpu().numpy().astype(np.float64)
     ref = orc.backward(n, orc.A_DENSE, orc.H_L1, None, g.astype(np.float64), v, t.astype(np.float64))
@@ -41,6 +47,28 @@ def test_backward_dense_matches_oracle(hg, orc, n, B):
     assert np.allclose(gt.cpu().numpy(), ref["g_t"], rtol=1e-5, atol=1e-5)
     scale = np.abs(ref["g_A"]).max()
     assert np.abs(gA.cpu().numpy() - ref["g_A"]).max() <= 1e-5 * scale
+
+
+def test_backward_tc_scale_and_zero_weights(hg, orc):
+    """Upstream weights of very different magnitudes (1e-6 and 1e+4 scales,
+    some exact zeros): the power-of-two scaling of g keeps the FP16 operands in
+    range, and g_A follows the oracle at the same bar."""
+    import torch
+    n, B = 256, 700
+    A, Q, s = wl.spd_matrix(12301, 12302, n)
+    x = wl.normal(12303, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(12304, B, 0.1, 3.0).astype(np.float32)
+    h = hg.Hopf(A, hg.H_L1, tol=1e-13, max_iter=3000, precision=hg.P_MIXED)
+    out = h.eval(_cuda(x), _cuda(t))
+    v = out["grad"].cpu().numpy().astype(np.float64)
+    for mag in (1e-6, 1e4):
+        g = (wl.normal(12305, B, 1.0) * mag).astype(np.float32)
+        g[::5] = 0.0
+        _, _, gA = h.backward(_cuda(g), out["grad"], want_x=False, want_t=False)
+        torch.cuda.synchronize()
+        ref = orc.backward(n, orc.A_DENSE, orc.H_L1, None, g.astype(np.float64), v, t.astype(np.float64))
+        scale = np.abs(ref["g_A"]).max()
+        assert np.abs(gA.cpu().numpy() - ref["g_A"]).max() <= 1e-5 * scale, mag
 
 
 def test_backward_diag(hg, orc):

@@ -55,3 +55,46 @@ def test_fit_diagonal_of_A(hg):
     # coordinates where the l1 minimiser is mostly zero barely move phi, so
     # delta is only partly identifiable: ask for a clear decrease
     assert errs[-1] < 0.75 * errs[0], errs
+
+
+def test_fit_diagonal_of_A_full_size(hg):
+    """The differentiation workload at its stated size: n = 2048, 32,768
+    queries, H = l1, 100 Adam steps, the handle (FP64 inverse of A + lambda I)
+    rebuilt at every step.  The loss falls by two orders of magnitude and
+    |delta - delta*| by a third."""
+    import time
+    import torch
+    d = wl.dense_l1_grad()
+    A0, s0, n, B = d["A"], d["s"], d["n"], len(d["t"])
+    x = torch.tensor(d["x"], device="cuda")
+    t = torch.tensor(d["t"], device="cuda")
+    d_star = wl.uniform(5009, n, 0.0, 0.5)
+    Fn = hg.HopfFn()
+    h = hg.Hopf(A0 + np.diag(d_star), hg.H_L1, tol=1e-13, max_iter=2000, precision=hg.P_MIXED)
+    phi_star = h.eval(x, t)["phi"].clone()
+    del h
+    lo = -0.05 * s0.min()
+    delta = torch.zeros(n, dtype=torch.float32, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([delta], lr=0.02)
+    A0t = torch.tensor(A0, dtype=torch.float32, device="cuda")
+    losses, errs, create = [], [], []
+    for step in range(100):
+        opt.zero_grad()
+        A_np = A0 + np.diag(delta.detach().double().cpu().numpy())
+        t0 = time.perf_counter()
+        hs = hg.Hopf(A_np, hg.H_L1, tol=1e-13, max_iter=2000, precision=hg.P_MIXED)
+        create.append(time.perf_counter() - t0)
+        phi = Fn.apply(x, t, A0t + torch.diag(delta), hs)
+        loss = ((phi - phi_star) ** 2).mean()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            delta.clamp_(min=lo)
+        losses.append(loss.item())
+        errs.append(float(np.linalg.norm(delta.detach().double().cpu().numpy() - d_star)))
+        del hs
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 1e-2 * losses[0], losses[::10]
+    assert errs[-1] < 0.67 * errs[0], errs[::10]
+    # the set-up (FP64 inverse) stays well under a forward evaluation's time
+    assert np.median(create) < 0.1, np.median(create)

@@ -106,8 +106,9 @@ def test_union_k16_n256_b16384(hg, orc):
 def test_dense_n2048_b32768_forward_backward(hg, orc):
     """Differentiation workload: n = 2048, H = l1, 32,768 queries; forward in
     the MIXED form, backward by the envelope theorem; dphi/dA checked by FP64
-    central differences (h = 1e-6) of exact active-set values on sampled
-    queries, and g_A against -1/2 V^T diag(g) V on a sampled block."""
+    central differences (h = 1e-6) of exact active-set values on the 64
+    sampled queries, g_x and g_t likewise, and g_A (tensor cores) against
+    -1/2 V^T diag(g) V on a sampled block and the CUDA-core kernel."""
     import torch
     d = wl.dense_l1_grad()
     A, n, B = d["A"], d["n"], len(d["t"])
@@ -123,15 +124,24 @@ def test_dense_n2048_b32768_forward_backward(hg, orc):
     cols = _sample(77004, 64, n)
     blk = -0.5 * (V[:, rows] * g[:, None]).T @ V[:, cols]
     gAb = gA.cpu().numpy()[np.ix_(rows, cols)]
-    assert np.abs(gAb - blk).max() <= 1e-4 * np.abs(blk).max()
+    assert np.abs(gAb - blk).max() <= 1e-5 * np.abs(blk).max()
+    # the tensor-core g_A against the FP32 CUDA-core kernel on the whole matrix
+    _, _, gA32 = h.backward(_cuda(g), out["grad"], want_x=False, want_t=False, tensor_cores=False)
+    torch.cuda.synchronize()
+    gAf = gA.cpu().numpy()
+    assert np.abs(gAf - gA32.cpu().numpy()).max() <= 1e-5 * np.abs(gAf).max()
+    assert np.array_equal(gAf, gAf.T)
     assert np.allclose(gx.cpu().numpy(), g[:, None] * V, rtol=1e-6, atol=1e-6)
     assert np.allclose(gt.cpu().numpy(), -g * np.abs(V).sum(1), rtol=1e-5, atol=1e-5)
-    # forward parity and FD of dphi/dA on sampled queries
-    idx = d["fd_queries"][:6]
+    # forward parity on the 64 sampled queries, and FP64 central differences
+    # (h = 1e-6) of exact active-set values in A, x and t at each of them
+    idx = d["fd_queries"]
+    assert len(idx) == 64
     P = orc.Problem(A, orc.H_L1, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL)
     ref = P.eval(d["x"][idx].astype(np.float64), d["t"][idx].astype(np.float64))
     phi = out["phi"].cpu().numpy()[idx]
     assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= 1e-6
+    gxh, gth = gx.cpu().numpy(), gt.cpu().numpy()
     w1 = np.ones(n)
     rng = np.random.default_rng(9)
     for j, q in enumerate(idx):
@@ -139,32 +149,44 @@ def test_dense_n2048_b32768_forward_backward(hg, orc):
         vq, ok = pins.kkt_active_set(A, xq, tq, w1, ref["grad"][j])
         assert ok
         S = np.nonzero(vq)[0]
+
+        def phi_at(Am, xx, tt):
+            vv, ok2 = pins.kkt_active_set(Am, xx, tt, w1, vq)
+            assert ok2
+            return pins.objective_neg(Am, xx, tt, w1, vv)
+
+        # the GPU's gradient error bound (the 6e-6 relative l2 bar of the
+        # dense tests) carried into each derivative
+        dv = 6e-6 * max(1.0, np.linalg.norm(vq))
+        # d phi / dt = -H(v*) and d phi / dx_i = v*_i (g_t, g_x with g = g_q)
+        fd_t = (phi_at(A, xq, tq + 1e-6) - phi_at(A, xq, tq - 1e-6)) / 2e-6
+        assert abs(fd_t + np.abs(vq).sum()) <= 1e-5 * max(1, abs(fd_t))
+        assert abs(gth[q] / g[q] - fd_t) <= np.sqrt(n) * dv + 1e-5 * abs(fd_t), (q, gth[q] / g[q], fd_t)
+        i0 = int(rng.choice(S)) if len(S) else 0
+        e = np.zeros(n)
+        e[i0] = 1e-6
+        fd_x = (phi_at(A, xq + e, tq) - phi_at(A, xq - e, tq)) / 2e-6
+        assert abs(fd_x - vq[i0]) <= 1e-5 * max(1, abs(fd_x))
+        assert abs(gxh[q, i0] / g[q] - fd_x) <= dv + 1e-5 * abs(fd_x)
+        # d phi / dA_ij (symmetric perturbation: twice -1/2 v_i v_j off the
+        # diagonal), against the g_A of this query alone
         one = np.zeros(B, np.float32)
         one[q] = 1.0
         _, _, gAq = h.backward(_cuda(one), out["grad"], want_x=False, want_t=False)
         torch.cuda.synchronize()
         gAq = gAq.cpu().numpy()
-        # the GPU's gradient error bound (the 6e-6 relative l2 bar of the
-        # dense tests) carried into -1/2 v_i v_j
-        dv = 6e-6 * np.linalg.norm(vq)
         for _ in range(2):
-            i1, i2 = rng.choice(S, 2)
+            i1, i2 = rng.choice(S, 2) if len(S) else (0, 0)
             E = np.zeros((n, n))
             E[i1, i2] += 1e-6
             if i1 != i2:
                 E[i2, i1] += 1e-6
-
-            def phi_of(Am):
-                vv, ok2 = pins.kkt_active_set(Am, xq, tq, w1, vq)
-                assert ok2
-                return pins.objective_neg(Am, xq, tq, w1, vv)
-
-            fd = (phi_of(A + E) - phi_of(A - E)) / 2e-6
+            fd = (phi_at(A + E, xq, tq) - phi_at(A - E, xq, tq)) / 2e-6
             f = 1 if i1 == i2 else 2
             exact = -0.5 * vq[i1] * vq[i2] * f  # envelope theorem at the exact minimiser
             assert abs(fd - exact) <= 1e-5 * max(1, abs(fd)), (q, i1, i2, fd, exact)
             bound = 0.5 * f * (abs(vq[i1]) * dv + abs(vq[i2]) * dv + dv * dv)
-            assert abs(gAq[i1, i2] * f - exact) <= bound + 1e-6 * abs(exact), (q, i1, i2, gAq[i1, i2] * f, exact)
+            assert abs(gAq[i1, i2] * f - exact) <= bound + 1e-5 * abs(exact), (q, i1, i2, gAq[i1, i2] * f, exact)
 
 
 def _h_of(g, h_kind, w):
