@@ -46,8 +46,8 @@ METRIC = ("Hopf evals/s (phi at 1e-6 rel, grad phi at 6e-6 rel) n=1024 batch 64K
 # the dominant kernel at the default workload, from the ncu capture summarised
 # in profiles/k_dense_tc_n1024_b65536.md; reported only while the kernel
 # source still has the hash it had at capture.
-MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "e57d9f3b4535720a",
-                              "bytes": 155.75e9, "n": 1024, "batch": 65536}}
+MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "4747f900ec3c3421",
+                              "bytes": 155.24e9, "n": 1024, "batch": 65536}}
 TOL = 1e-13
 MAX_ITER = 1000
 

@@ -288,10 +288,76 @@ struct MmaState {
   uint32_t ue[2] = {0, 0}, uf[2] = {0, 0};
   uint32_t ce[2] = {0, 0}, cf[2] = {0, 0};  // final-pass chunk slots
   bool issued = false;
+  uint64_t sdesc[STAGES];  // shared-memory descriptor of each ring stage's first tile
 };
+
+// The ordinary phases with as few instructions per MMA as possible: one
+// thread issues every MMA of the CTA, on a sub-partition it shares with
+// epilogue warps, and each instruction it spends delays the tensor pipe.
+// Descriptors are the stage's precomputed base plus constants (a tile is
+// 16 KB = 1024 descriptor units, a K = 16 step 32 bytes = 2 units), the
+// terms are fixed at compile time, and the next item's column check is
+// loaded while this item's MMAs are issued.
+//   THREE: phases A and S, one k-block per stage {A0, A1 | B0, B1}:
+//          A0 B0 -> D1, A0 B1 + A1 B0 -> D2;
+//   else:  phases B and P, two k-blocks per stage {M_kb, M_kb+1 | g_kb, g_kb+1},
+//          K steps alternating between D1 and D2.
+template <bool THREE>
+__device__ __forceinline__ void mma_items(const TcArgs& a, Smem& S, int ph, const Ctx& x, MmaState& st,
+                                          uint32_t idesc) {
+  const int nst = THREE ? a.np / BK : a.np / (2 * BK);  // stages per item
+  const int items = phase_items(a, x, ph);
+  int it = blockIdx.x;
+  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+  uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
+  while (it < items) {
+    const int nx = it + gridDim.x;
+    const bool nx_on = nx < items && tile_on(a, x, ph, nx / a.rt);  // used after this item
+    const uint32_t buf = st.nb;
+    st.nb ^= 1;
+    if (!mbar_wait_lim(sa(&S.tempty[buf]), (st.ue[buf] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
+    ++st.ue[buf];
+    tc_fence_after();
+    const uint32_t d1 = S.tmem_base + buf * 256, d2 = d1 + BN;
+    for (int j = 0; j < nst; ++j) {
+      if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+      tc_fence_after();
+      const uint64_t b = st.sdesc[s];
+      if constexpr (THREE) {
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          mma_f16(d1, b + kk * 2, b + 2048 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
+          mma_f16(d2, b + kk * 2, b + 3072 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
+          mma_f16(d2, b + 1024 + kk * 2, b + 2048 + kk * 2, idesc, 1u);
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_f16((kk & 1) ? d2 : d1, b + h * 1024 + kk * 2, b + (2 + h) * 1024 + kk * 2, idesc,
+                    (j == 0 && h == 0 && kk < 2) ? 0u : 1u);
+      }
+      st.issued = true;
+      mma_commit(sa(&S.empty[s]));  // frees the stage once these MMAs have read it
+      if (++s == STAGES) {
+        s = 0;
+        ++suse;
+      }
+    }
+    st.kb += nst;
+    mma_commit(sa(&S.tfull[buf]));  // accumulator ready for the epilogue
+    ++st.uf[buf];
+    it = nx;
+    if (!nx_on)
+      while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+  }
+}
 
 __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, const Ctx& x, MmaState& st) {
   const PhaseCfg cfg = phase_cfg(ph);
+  if (ph == PH_A || ph == PH_S) return mma_items<true>(a, S, ph, x, st, cfg.idesc);
+  if (ph == PH_B || ph == PH_P) return mma_items<false>(a, S, ph, x, st, cfg.idesc);
   const int nk = a.np / BK, items = phase_items(a, x, ph);
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int c = it / a.rt;
@@ -1110,6 +1176,7 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
   ProdState ps;
   for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
   MmaState ms;
+  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
   EpiState es;
   Ctx cx;
   cx.cb = 0;

@@ -70,20 +70,28 @@ __global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restric
       break;  // dkk is the same for every thread: all leave together
     }
     const double inv = 1.0 / dkk;
-    double nv[kSB * kSB / 256 + 1];
-    int cnt = 0;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x, ++cnt) {
-      const int i = e / nb, j = e % nb;
-      double o;
-      if (i == k && j == k) o = -inv;
-      else if (i == k) o = B[k][j] * inv;
-      else if (j == k) o = B[i][k] * inv;
-      else o = B[i][j] - B[i][k] * B[k][j] * inv;
-      nv[cnt] = o;
+    // each thread owns the entries e = threadIdx.x + 256 r (static indices:
+    // the new values stay in registers until every thread has read the old)
+    constexpr int R = kSB * kSB / 256;
+    double nv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      nv[r] = 0.0;
+      if (e < nb * nb) {
+        const int i = e / nb, j = e % nb;
+        if (i == k && j == k) nv[r] = -inv;
+        else if (i == k) nv[r] = B[k][j] * inv;
+        else if (j == k) nv[r] = B[i][k] * inv;
+        else nv[r] = B[i][j] - B[i][k] * B[k][j] * inv;
+      }
     }
     __syncthreads();
-    cnt = 0;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x, ++cnt) B[e / nb][e % nb] = nv[cnt];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      if (e < nb * nb) B[e / nb][e % nb] = nv[r];
+    }
     __syncthreads();
   }
   if (bad) return;
