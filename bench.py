@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-arms", action="store_true", help="time the chosen form only (no FP32 / SPLIT arms)")
+    p.add_argument("--ragged-mode", type=int, default=0, choices=[0, 1, 2],
+                   help="--workload ragged: 0 the tuner picks, 1 the persistent launch, 2 the stream schedule")
     p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh", "paper", "fit"])
     p.add_argument("--paper-only", default="",
                    help="--workload paper: only these configurations, J:H:n[,J:H:n...] "
@@ -198,7 +200,7 @@ def run_reference(args):
 
 
 RAGGED_METRIC = ("Hopf evals/s, ragged batch of 512 instances (n log-uniform 16-4096, 64-8192 queries each, "
-                 "half diagonal FP32, half dense MIXED, H cycling l1 / weighted l1 / l2)")
+                 "half diagonal FP32, half dense MIXED, H cycling l1 / weighted l1 / l2), one graph replay per step")
 
 
 def ragged_workload():
@@ -261,6 +263,7 @@ def run_ragged(args):
     for e in bd:
         e.pop("dense")
     b = hg.HopfBatch(bd)
+    b.set_mode(args.ragged_mode)
     xd = torch.from_numpy(x).to(dev)
     td = torch.from_numpy(t).to(dev)
     Q = int(counts.sum())
@@ -269,11 +272,32 @@ def run_ragged(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    out = b.eval(counts, xd, td)  # the first call tunes the lane count and captures the graph
+    out = b.eval(counts, xd, td)  # the first call tunes the schedule and lanes, and captures the graph
     for _ in range(args.warmup):
         out = b.eval(counts, xd, td, out=out)
     torch.cuda.synchronize()
     info = b.info()
+    # the other schedule, tuned and timed apart (a few replays), for the record
+    other = None
+    if not args.no_arms:
+        b2 = hg.HopfBatch(bd)
+        b2.set_mode(2 if info["schedule"] == "persistent" else 1)
+        o2 = b2.eval(counts, xd, td)
+        for _ in range(2):
+            o2 = b2.eval(counts, xd, td, out=o2)
+        torch.cuda.synchronize()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record()
+        for _ in range(3):
+            o2 = b2.eval(counts, xd, td, out=o2)
+        t1e.record()
+        torch.cuda.synchronize()
+        i2 = b2.info()
+        same = all(torch.equal(out[k], o2[k]) for k in ("phi", "grad", "iters"))
+        other = {"schedule": i2["schedule"], "lanes": i2["nstreams"], "ms_per_step": t0e.elapsed_time(t1e) / 3,
+                 "tuned_ms": i2["tuned_ms"], "outputs_bit_identical": bool(same)}
+        b2.close()
+        del o2
     iters = out["iters"].cpu().numpy().astype(np.float64)
     status = out["status"].cpu().numpy()
     clk_path = tempfile.mktemp(suffix=".csv")
@@ -343,6 +367,8 @@ def run_ragged(args):
         else:
             alu_flops += float(np.sum(10.0 * n * K))
             launches += 1
+    if info["schedule"] == "persistent":
+        launches = 1  # one cooperative launch per replay (every instance here is taken by it)
     t_roof = tc_flops / (tc_peak * 1e12) + alu_flops / (alu_peak * 1e12)
     t_exec = tc_exec / (tc_peak * 1e12) + alu_flops / (alu_peak * 1e12)
     frac = t_roof / (ms * 1e-3)
@@ -365,7 +391,8 @@ def run_ragged(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (diagonal) / bf16+f16 (dense)",
                 "data": "synthetic",
                 "config": {"workload": "ragged_512", "instances": len(inst), "queries": Q,
-                           "x_floats": int(x.size), "lanes": info["nstreams"], "tuned_ms": info["tuned_ms"],
+                           "x_floats": int(x.size), "schedule": info["schedule"], "lanes": info["nstreams"],
+                           "tuned_ms": info["tuned_ms"], "other_schedule": other,
                            "parallelism": "replicas" if ws == 1 else "dp%d (each rank its own batch)" % ws,
                            "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
                 "iters": {"mean": float(iters.mean()), "max": int(iters.max())},

@@ -300,15 +300,23 @@ hopf_status hopf_backward_params(hopf_handle h, int64_t batch, const float* g_ph
 /* ---- ragged batches -----------------------------------------------------
  * Many independent instances (each with its own A, H, n and number of
  * queries) evaluated together.  Queries share no state (Section 1; Section
- * 4.5 runs them one per core), so the batch is a set of single
- * evaluations recorded into one CUDA graph and replayed by later calls that
- * pass the same buffers and counts.  In the graph, dense instances with at
- * least one 128 x 128 tile per SM run one after another on the whole GPU;
- * the smaller dense instances then run side by side on worker streams
- * ("lanes"), each capped at an equal share of the SMs so that the
- * cooperative grids in flight fit together; diagonal instances are spread
- * over the lanes and overlap both phases.  Instances go longest-first to the
- * least loaded lane.
+ * 4.5 runs them one per core), so the batch is a set of single evaluations,
+ * recorded into one CUDA graph and replayed by later calls that pass the same
+ * buffers and counts.  Two schedules:
+ *   persistent  one cooperative launch of the ragged solver: the dense
+ *               tensor-core instances run on a schedule of CTA groups (an
+ *               instance with at least one 128 x 128 tile per SM on the whole
+ *               GPU, the others side by side on "lanes" of the SMs, longest
+ *               first to the least loaded lane), then every diagonal instance
+ *               from a shared work list (256 queries of a thread-per-query
+ *               instance, 8 of a warp-per-query one or one query of a
+ *               256-thread one per item).  The arithmetic of every query is
+ *               that of hopf_eval: results are the same bit for bit.
+ *   streams     per instance the kernels hopf_eval launches, forked onto
+ *               worker streams ("lanes", the dense solvers capped at an equal
+ *               share of the SMs).
+ * Instances the persistent solver does not take (dense FP32, the diagonal
+ * runtime kinds, diagonal n > 4096) run their own launches beside it.
  *
  * Layout: instance i has counts[i] queries.  Per-query arrays (t, phi, dphidt,
  * iters, qstatus) hold the instances one after another: instance i starts at
@@ -317,10 +325,13 @@ hopf_status hopf_backward_params(hopf_handle h, int64_t batch, const float* g_ph
  * everything else is device memory, as for hopf_eval.
  *
  * The first hopf_batch_eval call tunes the schedule: it captures and times
- * the batch with 1, 2, 4, 8 and 16 lanes and keeps the fastest (so it
- * synchronises `stream`; its results are those of the kept graph);
- * hopf_batch_info reports the choice.  Instances
- * with FP64 precision are not accepted. */
+ * the persistent schedule with 4 to 32 lanes, wide instances on the whole GPU
+ * or on lanes too, some SMs starting on the diagonal instances, and the stream
+ * schedule with the best lane count, and keeps
+ * the fastest (so it synchronises `stream`; its results are complete when it
+ * returns); hopf_batch_info reports the choice.  Instances with FP64 precision are not accepted.
+ * hopf_batch_create keeps a pinned host copy of the persistent schedule
+ * (O(instances x SMs) bytes). */
 typedef struct hopf_batch_s* hopf_batch;
 hopf_status hopf_batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out, cudaStream_t stream);
 void hopf_batch_destroy(hopf_batch b);
@@ -328,10 +339,19 @@ hopf_status hopf_batch_workspace_size(hopf_batch b, const int64_t* counts, size_
 hopf_status hopf_batch_eval(hopf_batch b, const int64_t* counts, const float* x, const float* t, double* phi,
                             float* grad, float* dphidt, int32_t* iters, uint8_t* qstatus, void* workspace,
                             size_t ws_bytes, cudaStream_t stream);
-/* nstreams: worker streams chosen (0 before the first eval); used_graph: 1
- * once the batch runs as a graph replay; tuned_ms[5]: the timed candidates
- * (may be NULL). */
+/* nstreams: lanes chosen (0 before the first eval); used_graph: 0 before the
+ * first eval, 1 when the batch replays the persistent schedule's graph, 2 the
+ * stream schedule's; tuned_ms[8]: the timed candidates (may be NULL): the
+ * persistent schedule with 4, 8, 16, 32 lanes (wide dense instances on the
+ * whole GPU), 8 and 16 lanes with 8 SMs and 16 lanes with 16 SMs starting on
+ * the diagonal work list, and 8 lanes taking every dense instance; with
+ * mode 2 the stream schedule with 1, 2, 4, 8, 16 lanes in the first five. */
 hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms);
+
+/* Schedule the tuner may pick: 0 either (the default), 1 persistent only,
+ * 2 streams only.  Drops the current graph; the next hopf_batch_eval tunes
+ * again. */
+hopf_status hopf_batch_set_mode(hopf_batch b, int32_t mode);
 
 /* Instrumentation: when `start` and `stop` are non-NULL CUDA events, every
  * later hopf_eval on this handle records `start` on its stream immediately

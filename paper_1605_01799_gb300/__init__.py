@@ -31,7 +31,8 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_union_workspace_size", "hopf_union_eval", "hopf_union_closest", "hopf_union_closest_noalloc",
            "hopf_backward", "hopf_backward_params", "hopf_backward_workspace_size", "hopf_backward_ws",
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
-           "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_eval_control", "hopf_maxH_eval",
+           "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_batch_set_mode",
+           "hopf_eval_control", "hopf_maxH_eval",
            "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_allocator",
            "hopf_last_error", "hopf_version"]
 
@@ -83,6 +84,7 @@ def lib():
             "hopf_batch_workspace_size": ([_vp, _vp, ctypes.POINTER(_sz)], ctypes.c_int),
             "hopf_batch_eval": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_batch_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "hopf_batch_set_mode": ([_vp, _i32], ctypes.c_int),
             "hopf_eval_control": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
                                   ctypes.c_int),
             "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
@@ -348,9 +350,15 @@ class HopfBatch:
 
     def info(self):
         ns, ug = ctypes.c_int32(), ctypes.c_int32()
-        ms = (ctypes.c_float * 5)()
+        ms = (ctypes.c_float * 8)()
         _check(lib().hopf_batch_info(self.handle, ctypes.byref(ns), ctypes.byref(ug), ms))
-        return {"nstreams": ns.value, "used_graph": bool(ug.value), "tuned_ms": list(ms)}
+        return {"nstreams": ns.value, "used_graph": bool(ug.value), "tuned_ms": list(ms),
+                "schedule": {0: None, 1: "persistent", 2: "streams"}[ug.value]}
+
+    def set_mode(self, mode):
+        """0: the tuner picks the persistent or the stream schedule; 1: the
+        persistent one only; 2: the streams only."""
+        _check(lib().hopf_batch_set_mode(self.handle, int(mode)))
 
 
 def _parts_array(parts):

@@ -54,7 +54,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <new>
+
 #include "common.cuh"
+#include "diag_query.cuh"
 #include "hopf_internal.h"
 #include "tc_ptx.cuh"
 
@@ -130,6 +133,7 @@ struct Ctx {
   int fresh;  // compacted before this iteration: every tile below ct_on holds active slots
   int k;      // iteration
   int par;    // parity of this iteration's decision (k & 1)
+  int gr, gs; // this CTA's rank in the group of CTAs solving the instance, and the group's size
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -242,7 +246,7 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
   const uint32_t bytes = 4u * TILE_BYTES;
   const int nk = a.np / BK, items = phase_items(a, x, ph);
   const int nsub = ph == PH_F ? 2 : 1;  // PH_F: {A1, A2 | p1, p2} then {A1, A3 | p3, p1}
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = x.gr; it < items; it += x.gs) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, x, ph, c)) continue;
     // the epilogue of this item reads u of its tile one to two items from
@@ -307,11 +311,11 @@ __device__ __forceinline__ void mma_items(const TcArgs& a, Smem& S, int ph, cons
                                           uint32_t idesc) {
   const int nst = THREE ? a.np / BK : a.np / (2 * BK);  // stages per item
   const int items = phase_items(a, x, ph);
-  int it = blockIdx.x;
-  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+  int it = x.gr;
+  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
   uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
   while (it < items) {
-    const int nx = it + gridDim.x;
+    const int nx = it + x.gs;
     const bool nx_on = nx < items && tile_on(a, x, ph, nx / a.rt);  // used after this item
     const uint32_t buf = st.nb;
     st.nb ^= 1;
@@ -350,7 +354,7 @@ __device__ __forceinline__ void mma_items(const TcArgs& a, Smem& S, int ph, cons
     ++st.uf[buf];
     it = nx;
     if (!nx_on)
-      while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+      while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
   }
 }
 
@@ -359,7 +363,7 @@ __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, con
   if (ph == PH_A || ph == PH_S) return mma_items<true>(a, S, ph, x, st, cfg.idesc);
   if (ph == PH_B || ph == PH_P) return mma_items<false>(a, S, ph, x, st, cfg.idesc);
   const int nk = a.np / BK, items = phase_items(a, x, ph);
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = x.gr; it < items; it += x.gs) {
     const int c = it / a.rt;
     if (!tile_on(a, x, ph, c)) continue;
     const uint32_t buf = ph == PH_F ? 0 : st.nb;
@@ -586,8 +590,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   const int cb = x.cb;
   // the slot data (and, in phases A and P, the decision) of the next item is
   // loaded into registers while the current item is processed
-  int it = blockIdx.x;
-  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += gridDim.x;
+  int it = x.gr;
+  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
   float pf_tau = 0.f, pf_sc = 1.f;
   int pf_act = 0, pf_qid = 0;
   if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
@@ -612,8 +616,8 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
   };
   while (it < items) {
     const int r = it % a.rt, c = it / a.rt;
-    int it_next = it + gridDim.x;
-    while (it_next < items && !tile_on(a, x, ph, it_next / a.rt)) it_next += gridDim.x;
+    int it_next = it + x.gs;
+    while (it_next < items && !tile_on(a, x, ph, it_next / a.rt)) it_next += x.gs;
     const uint32_t buf = st.nb;
     st.nb ^= 1;
     const uint32_t use = st.uf[buf]++;
@@ -882,7 +886,7 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
   const int rloc = qd * 32 + lane;
   const int items = phase_items(a, x, PH_F), nk = a.np / BK;
   const int np = a.np, hk = a.h_kind;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = x.gr; it < items; it += x.gs) {
     const int r = it % a.rt, c = it / a.rt;
     if (!tile_on(a, x, PH_F, c)) continue;
     epi_sync();
@@ -1016,7 +1020,7 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
   const uint16_t* o2 = odd ? a.q2[cb] : a.p2[cb];
   uint16_t* d1p = odd ? a.q1[nb] : a.p1[nb];
   uint16_t* d2p = odd ? a.q2[nb] : a.p2[nb];
-  for (int c = blockIdx.x; c < x.ct_on; c += gridDim.x) {
+  for (int c = x.gr; c < x.ct_on; c += x.gs) {
     if (tile_count(a, x, c) == 0) continue;  // the same for every thread
     if (et < BN) {
       const int64_t sl = (int64_t)c * BN + et;
@@ -1073,7 +1077,7 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
   }
   // the tail of the last new tile
   const int need = (n_active + BN - 1) / BN;
-  for (int64_t sl = (int64_t)n_active + blockIdx.x * NEPI + et; sl < (int64_t)need * BN; sl += (int64_t)gridDim.x * NEPI) {
+  for (int64_t sl = (int64_t)n_active + x.gr * NEPI + et; sl < (int64_t)need * BN; sl += (int64_t)x.gs * NEPI) {
     a.qact[nb][par][sl] = 0;
     a.sq[nb][sl] = 0;
     a.taus[nb][sl] = 0.f;
@@ -1083,13 +1087,13 @@ __device__ __noinline__ void compact(const TcArgs& a, Smem& S, const Ctx& x, int
 // Before the final pass: the three-term FP16 split of p = prox(u) for every
 // query (query-indexed p1 and p2 planes of buffer set 0, the third term in the
 // g plane), from the retired u.
-__device__ __noinline__ void prep_final_operand(const TcArgs& a) {
+__device__ __noinline__ void prep_final_operand(const TcArgs& a, const Ctx& x) {
   // four consecutive rows of one query per piece (np is a multiple of 128),
   // two pieces per thread in flight
   const int per_q = a.np / 4;
   const int64_t total = a.B_pad * per_q;
-  const int64_t stride = (int64_t)gridDim.x * NEPI;
-  for (int64_t i0 = (int64_t)blockIdx.x * NEPI + (threadIdx.x - 64); i0 < total; i0 += 2 * stride) {
+  const int64_t stride = (int64_t)x.gs * NEPI;
+  for (int64_t i0 = (int64_t)x.gr * NEPI + (threadIdx.x - 64); i0 < total; i0 += 2 * stride) {
     float4 uv[2];
     int64_t q[2];
     int row[2];
@@ -1133,57 +1137,25 @@ __device__ __noinline__ void prep_final_operand(const TcArgs& a) {
   }
 }
 
-// Registers: each of the 4 sub-partitions holds 16,384, shared by the warps
-// placed on it (warp w on sub-partition w % 4): 18 warps put 5 on two of them,
-// hence at most 96 per thread; 10 warps allow 168.
-__global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Smem& S = *reinterpret_cast<Smem*>(stages + STAGES * STAGE_BYTES);
+// One instance solved by a group of gs CTAs (this one has rank gr) that share
+// the instance's barrier words: the whole grid for hopf_eval, a lane of the
+// grid in a ragged batch.  The ring, the TMEM and the role states carry over
+// from one instance to the next.  Returns false when a wait gave up.
+__device__ bool solve_instance(const TcArgs& a, Smem& S, uint8_t* stages, ProdState& ps, MmaState& ms, EpiState& es,
+                               int gr, int gs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(sa(&S.full[s]), 1);
-      mbar_init(sa(&S.empty[s]), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(sa(&S.tfull[b]), 1);
-      mbar_init(sa(&S.tempty[b]), EPI_WARPS);
-    }
-    mbar_init(sa(&S.drain), 1);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(sa(&S.cfull[b]), 1);
-      mbar_init(sa(&S.cempty[b]), EPI_WARPS);
-    }
-    S.abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    tc_fence_before();
-  }
-  __syncthreads();
-  tc_fence_after();
   if (warp == 0 && lane == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.mAh)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&a.mM)) : "memory");
   }
-
-  ProdState ps;
-  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
-  MmaState ms;
-  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
-  EpiState es;
   Ctx cx;
   cx.cb = 0;
   cx.ct_on = a.ct;
   cx.fresh = 0;
   cx.k = 0;
   cx.par = 0;
+  cx.gr = gr;
+  cx.gs = gs;
   auto run = [&](int ph, int k) {
     if (warp == 0) {
       if (lane == 0) {
@@ -1213,29 +1185,28 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     cx.par = k & 1;
     // the count slot that decision k + 1 fills (last read at iteration
     // k - 2, which every CTA has left)
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
+    if (gr == 0 && threadIdx.x == 0) atomicExch(a.bar + 2 + ((k + 1) % 3), 0u);
     run(a.form == FORM_MIXED ? PH_A : a.form == FORM_SPLIT ? PH_S : PH_P, k);
-    if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
+    if (!(ok = grid_barrier(a.bar, gs, a.err, a.wait_limit))) break;
     const int n_active = (int)ld_acquire_u32(a.bar + 2 + (k % 3));
     if (n_active == 0) break;
     if (a.form == FORM_BF16) continue;
     if (a.form == FORM_MIXED) {
       run(PH_B, k);
-      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
+      if (!(ok = grid_barrier(a.bar, gs, a.err, a.wait_limit))) break;
     }
     // every CTA takes the same decision from the same count: compact when it
     // frees a quarter of the column tiles in use and shortens each phase by
-    // at least one round of items over the grid (a sixteenth, an eighth, a
+    // at least one round of items over the group (a sixteenth, an eighth, a
     // third and a half were each measured slower)
     const int need = (n_active + BN - 1) / BN;
-    const int g = (int)gridDim.x;
-    const bool fewer_rounds = (need * a.rt + g - 1) / g < (cx.ct_on * a.rt + g - 1) / g;
+    const bool fewer_rounds = (need * a.rt + gs - 1) / gs < (cx.ct_on * a.rt + gs - 1) / gs;
     // (the packing offsets of the column tiles live in shared memory)
     if (a.compact && cx.ct_on <= (int)(sizeof(S.base) / sizeof(S.base[0])) &&
         need + (cx.ct_on + 3) / 4 <= cx.ct_on && fewer_rounds) {
       if (warp >= 2) compact(a, S, cx, n_active);
       proxy_fence_global();
-      if (!(ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit))) break;
+      if (!(ok = grid_barrier(a.bar, gs, a.err, a.wait_limit))) break;
       cx.cb ^= 1;
       cx.ct_on = need;
       cx.fresh = 1;
@@ -1244,13 +1215,53 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     }
   }
   if (ok) {
-    if (warp >= 2) prep_final_operand(a);
+    if (warp >= 2) prep_final_operand(a, cx);
     proxy_fence_global();
-    ok = grid_barrier(a.bar, gridDim.x, a.err, a.wait_limit);
+    ok = grid_barrier(a.bar, gs, a.err, a.wait_limit);
   }
   if (ok) run(PH_F, 0);
+  return ok;
+}
 
-  // drain: no copy or MMA of this CTA may be in flight when TMEM is freed
+// Shared memory, mbarriers and TMEM of a solver CTA (set up once per launch).
+__device__ __forceinline__ Smem& tc_setup(uint8_t*& stages) {
+  extern __shared__ uint8_t smem_raw[];
+  stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Smem& S = *reinterpret_cast<Smem*>(stages + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(sa(&S.full[s]), 1);
+      mbar_init(sa(&S.empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(sa(&S.tfull[b]), 1);
+      mbar_init(sa(&S.tempty[b]), EPI_WARPS);
+    }
+    mbar_init(sa(&S.drain), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(sa(&S.cfull[b]), 1);
+      mbar_init(sa(&S.cempty[b]), EPI_WARPS);
+    }
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  return S;
+}
+
+// Drain (no copy or MMA of this CTA may be in flight when TMEM is freed) and
+// free the TMEM.
+__device__ __forceinline__ void tc_teardown(Smem& S, const ProdState& ps, const MmaState& ms) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s)
       if (ps.used[s]) {
@@ -1272,6 +1283,21 @@ __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcAr
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(TMEM_COLS)
                  : "memory");
   }
+}
+
+// Registers: each of the 4 sub-partitions holds 16,384, shared by the warps
+// placed on it (warp w on sub-partition w % 4): 18 warps put 5 on two of them,
+// hence at most 96 per thread; 10 warps allow 168.
+__global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
+  uint8_t* stages;
+  Smem& S = tc_setup(stages);
+  ProdState ps;
+  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
+  MmaState ms;
+  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
+  EpiState es;
+  solve_instance(a, S, stages, ps, ms, es, blockIdx.x, gridDim.x);
+  tc_teardown(S, ps, ms);
 }
 
 // ------------------------------------------------------------------- host side
@@ -1337,6 +1363,189 @@ __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restr
   }
 }
 
+
+// ------------------------------------------------------------ ragged batches
+// One persistent cooperative launch runs a whole ragged batch (hopf_batch_*):
+// the dense instances by a schedule of CTA groups, then the diagonal
+// instances from a shared work list.
+//
+// Dense.  Every CTA walks its own list of (instance, rank, group size)
+// entries.  A group is the whole grid for a wide instance (at least one tile
+// per SM) and a lane of the grid for the others; all CTAs of a group hold the
+// same instances in the same order, so each instance's barrier words are used
+// by exactly its group.  Per instance the group initialises the state (what
+// k_dense_init and k_tc_init_operand do for hopf_eval), solves it with
+// solve_instance, and writes phi, d phi / dt, the iteration count and the
+// status (what k_dense_finalize does): the arithmetic of every query is that
+// of hopf_eval, so the results are the same bit for bit.  A CTA whose wait
+// gave up (its ring and TMEM state are then unusable) marks every later
+// instance of its list aborted, and their groups report HOPF_Q_ABORTED.
+//
+// Diagonal.  When its list is done, each CTA's first 256 threads take work
+// items (instance, first query, query count, group shape) from an atomic
+// counter: 256 queries of a thread-per-query instance, 8 of a warp-per-query
+// one, or one query of a 256-thread one; the group shape is the one hopf_eval
+// picks for the instance's n, so again the results are the same.
+struct alignas(64) RagDense {
+  TcArgs a;
+  const float* t;     // the caller's t for the instance
+  float* tq;          // [B_pad] t by query
+  double* phi;
+  float* dphidt;
+  int32_t* iters;
+  uint8_t* qstatus;
+  double c0;
+};
+
+struct RagDiag {
+  DiagEvalArgs<float> e;
+};
+
+struct RaggedArgs {
+  const RagDense* dense;
+  const int4* sched;      // per CTA entries (instance, rank, size, -)
+  const int* sched_off;   // [grid + 1]
+  const RagDiag* diag;
+  const int4* dinfo;      // per diagonal instance (queries, queries per item, shape class, first item)
+  int n_diag, n_items;
+  unsigned* ctr;          // work-list counter (zero before the launch)
+};
+
+__device__ void rag_init(const RagDense& d, int gr, int gs) {
+  const TcArgs& a = d.a;
+  const int64_t nthr = (int64_t)gs * NT, tid = (int64_t)gr * NT + threadIdx.x;
+  const int np = a.np;
+  const float lam = a.lam;
+  for (int64_t e = tid; e < a.B_pad * np; e += nthr) {
+    const int64_t q = e / np;
+    const int i = (int)(e - q * np);
+    float v = 0.f;
+    if (q < a.B && i < a.n) v = a.x[q * a.n + i] - a.cf[i];
+    a.y[0][e] = v;
+    a.u[0][e] = v;
+    // the first operand: the FP16 split of y (MIXED; SPLIT with l2), of
+    // r^0 = y + lambda y (SPLIT), or BF16 r^0 (BF16 form)
+    float o = v;
+    if (a.form == FORM_SPLIT && a.h_kind != H_L2) o = v + lam * v;
+    if (a.form != FORM_BF16) {
+      const __half hi = __float2half_rn(o);
+      a.p1[0][e] = __half_as_ushort(hi);
+      a.p2[0][e] = __half_as_ushort(__float2half_rn((o - __half2float(hi)) * kLoScale));
+    } else {
+      a.p1[0][e] = __bfloat16_as_ushort(__float2bfloat16_rn(v + lam * v));
+    }
+  }
+  for (int64_t q = tid; q < a.B_pad; q += nthr) {
+    const float tt = q < a.B ? d.t[q] : 0.f;
+    d.tq[q] = tt;
+    a.tau[q] = tt / lam;
+    a.taus[0][q] = tt / lam;
+    a.qiter[q] = 0;
+    a.qdone[q] = q < a.B ? 0 : 1;
+    a.sq[0][q] = (int)q;
+  }
+  for (int64_t c = tid; c < a.B_pad / BN; c += nthr) {
+    a.tile_k[c] = 0;
+    a.tile_cnt[c] = 0;
+  }
+  proxy_fence_global();  // the operand planes are read by TMA
+}
+
+__device__ void rag_finalize(const RagDense& d, int gr, int gs) {
+  const TcArgs& a = d.a;
+  const int64_t nthr = (int64_t)gs * NT, tid = (int64_t)gr * NT + threadIdx.x;
+  const bool aborted = *((volatile int*)a.err) != ERR_NONE;
+  for (int64_t q = tid; q < a.B; q += nthr) {
+    double sum = 0.0, hh = 0.0;
+    for (int r = 0; r < a.rt; ++r) {
+      sum += a.fpart[(int64_t)r * a.B_pad + q];
+      hh += a.fpart[(int64_t)(a.rt + r) * a.B_pad + q];
+    }
+    const double H = a.h_kind == H_L2 ? sqrt(hh) : hh;
+    const double ph = sum - d.c0 - (double)d.tq[q] * H;
+    d.phi[q] = ph;
+    if (d.dphidt) d.dphidt[q] = (float)(-H);
+    if (d.iters) d.iters[q] = a.qiter[q];
+    if (d.qstatus) {
+      uint8_t st = a.qdone[q] == 1 ? Q_OK : Q_NOT_CONVERGED;
+      if (!isfinite(ph)) st = Q_NONFINITE;
+      if (!(d.tq[q] >= 0.f)) st = Q_BAD_INPUT;
+      if (aborted) st = Q_ABORTED;
+      d.qstatus[q] = st;
+    }
+  }
+}
+
+template <int G, int VPT>
+__device__ void rag_diag_item(const RagDiag& D, int64_t q0, int nq) {
+  const int qi = G == 1 ? (int)threadIdx.x : (G == 32 ? (int)(threadIdx.x >> 5) : 0);
+  if (qi >= nq) return;  // whole groups leave together
+  const int64_t q = q0 + qi;
+  Query<float, G, VPT> Q;
+  Q.load(D.e.P, D.e.x + q * D.e.n, D.e.n);
+  Q.cold_start();
+  const float tq = D.e.t[q];
+  bool conv;
+  const int k = Q.template solve<false>(D.e.P, tq, &conv);
+  emit<false>(D.e, Q, q, tq, k, conv);
+}
+
+__device__ void rag_diag_loop(const RaggedArgs& r) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(r.ctr, 1u);
+    group_sync<256>();
+    const int it = s_item;
+    group_sync<256>();
+    if (it >= r.n_items) break;
+    // the instance whose item range holds `it` (first items ascending)
+    int lo = 0, hi = r.n_diag - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (r.dinfo[mid].w <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const int4 w = r.dinfo[lo];
+    const RagDiag& D = r.diag[lo];
+    const int64_t q0 = (int64_t)(it - w.w) * w.y;
+    const int nq = (int)min((int64_t)w.y, (int64_t)w.x - q0);
+    switch (w.z) {
+      case 0: rag_diag_item<1, 4>(D, q0, nq); break;
+      case 1: rag_diag_item<1, 8>(D, q0, nq); break;
+      case 2: rag_diag_item<1, 16>(D, q0, nq); break;
+      case 3: rag_diag_item<32, 2>(D, q0, nq); break;
+      case 4: rag_diag_item<32, 8>(D, q0, nq); break;
+      case 5: rag_diag_item<32, 16>(D, q0, nq); break;
+      default: rag_diag_item<256, 16>(D, q0, nq); break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_ragged(const __grid_constant__ RaggedArgs r) {
+  uint8_t* stages;
+  Smem& S = tc_setup(stages);
+  ProdState ps;
+  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
+  MmaState ms;
+  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
+  EpiState es;
+  bool alive = true;
+  for (int e = r.sched_off[blockIdx.x]; e < r.sched_off[blockIdx.x + 1]; ++e) {
+    const int4 w = r.sched[e];
+    const RagDense& d = r.dense[w.x];
+    const TcArgs& a = d.a;
+    if (!alive && threadIdx.x == 0) atomicExch(a.err, ERR_MBAR_TIMEOUT);
+    rag_init(d, w.y, w.z);
+    bool ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
+    if (ok) ok = solve_instance(a, S, stages, ps, ms, es, w.y, w.z);
+    if (ok) ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
+    else __syncthreads();
+    rag_finalize(d, w.y, w.z);
+    if (S.abort) alive = false;
+  }
+  if (threadIdx.x < 256) rag_diag_loop(r);
+  tc_teardown(S, ps, ms);
+}
 }  // namespace tc
 
 bool tc_encode_f16(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols) {
@@ -1367,20 +1576,10 @@ hopf_status dense_tc_prepare() {
   return HOPF_OK;
 }
 
-hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
-                          float* xfin) {
+static hopf_status build_tc_args(hopf_handle h, DenseWs& w, const float* x, float* grad, float* beta, float* xfin,
+                                 int form, tc::TcArgs* out) {
   using namespace tc;
-  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
-  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
-    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
-  hopf_status s = dense_init(h, w, x, t, stream);
-  if (s != HOPF_OK) return s;
-  const int64_t total = w.B_pad * h->n_pad;
-  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda, h->h_kind);
-  HOPF_CUDA(cudaGetLastError());
-
-  TcArgs a;
+  TcArgs& a = *out;
   memset(&a, 0, sizeof(a));
   const int np = h->n_pad;
   bool ok = encode(&a.mAh, h->d_Ah16, np, np, false) && encode(&a.mAl, h->d_Al16, np, np, false) &&
@@ -1449,6 +1648,27 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   a.lam = (float)h->lambda;
   a.tol = (float)h->tol;
 
+  return HOPF_OK;
+}
+
+hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
+                          float* xfin) {
+  using namespace tc;
+  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
+  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
+    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
+  hopf_status s = dense_init(h, w, x, t, stream);
+  if (s != HOPF_OK) return s;
+  const int64_t total = w.B_pad * h->n_pad;
+  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda, h->h_kind);
+  HOPF_CUDA(cudaGetLastError());
+
+  TcArgs a;
+  s = build_tc_args(h, w, x, grad, beta, xfin, form, &a);
+  if (s != HOPF_OK) return s;
+  const int np = h->n_pad;
+
   const size_t smem = tc_smem_bytes();
   int per_sm = 0;
   HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc, NT, smem));
@@ -1465,4 +1685,67 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   return dense_finalize(h, w, phi, dphidt, iters, qstatus, stream);
 }
 
+
+size_t ragged_dense_record_bytes() { return sizeof(tc::RagDense); }
+size_t ragged_diag_record_bytes() { return sizeof(tc::RagDiag); }
+
+hopf_status ragged_build_dense(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                               float* dphidt, int32_t* iters, uint8_t* qstatus, void* rec) {
+  using namespace tc;
+  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
+  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
+    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
+  RagDense* d = new (rec) RagDense();
+  hopf_status s = build_tc_args(h, w, x, grad, nullptr, nullptr, form, &d->a);
+  if (s != HOPF_OK) return s;
+  d->t = t;
+  d->tq = w.tq;
+  d->phi = phi;
+  d->dphidt = dphidt;
+  d->iters = iters;
+  d->qstatus = qstatus;
+  d->c0 = h->c0;
+  return HOPF_OK;
+}
+
+int ragged_diag_class(hopf_handle h) {
+  if (h->precision == HOPF_P_FP64 || h->j_kind != 0 || h->h_kind > HOPF_H_L2) return -1;  // runtime kinds: own launch
+  const int n = h->n;
+  return n <= 4 ? 0 : n <= 8 ? 1 : n <= 16 ? 2 : n <= 64 ? 3 : n <= 256 ? 4 : n <= 512 ? 5 : n <= 4096 ? 6 : -1;
+}
+
+void ragged_build_diag(hopf_handle h, int64_t B, const float* x, const float* t, double* phi, float* grad,
+                       float* dphidt, int32_t* iters, uint8_t* qstatus, void* rec) {
+  tc::RagDiag* d = new (rec) tc::RagDiag();
+  d->e = DiagEvalArgs<float>{part_of<float>(h), h->n, B, x, t, phi, grad, dphidt, iters, qstatus, nullptr, nullptr};
+}
+
+hopf_status ragged_prepare() {
+  static bool done[256] = {};
+  int dev = 0;
+  HOPF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 256 && !done[dev]) {
+    HOPF_CUDA(cudaFuncSetAttribute(tc::k_ragged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+    done[dev] = true;
+  }
+  return HOPF_OK;
+}
+
+hopf_status ragged_launch(const void* dense, const int4* sched, const int* sched_off, int grid, const void* diag,
+                          const int4* dinfo, int n_diag, int n_items, unsigned* ctr, cudaStream_t stream) {
+  HOPF_CUDA(ragged_prepare() == HOPF_OK ? cudaSuccess : cudaErrorUnknown);
+  tc::RaggedArgs r;
+  r.dense = (const tc::RagDense*)dense;
+  r.sched = sched;
+  r.sched_off = sched_off;
+  r.diag = (const tc::RagDiag*)diag;
+  r.dinfo = dinfo;
+  r.n_diag = n_diag;
+  r.n_items = n_items;
+  r.ctr = ctr;
+  void* args[] = {&r};
+  HOPF_CUDA(cudaLaunchCooperativeKernel((const void*)tc::k_ragged, dim3(grid), dim3(tc::NT), args, tc_smem_bytes(),
+                                        stream));
+  return HOPF_OK;
+}
 }  // namespace hopf

@@ -4,57 +4,6 @@
 
 namespace hopf {
 
-template <typename T>
-struct DiagEvalArgs {
-  DiagPart<T> P;
-  int n;
-  int64_t batch;
-  const T* x;
-  const T* t;
-  double* phi;
-  T* grad;
-  T* dphidt;
-  int32_t* iters;
-  uint8_t* qstatus;
-  T* beta;  // optional: control in dH(grad phi), [batch][n]
-  T* xfin;  // optional: terminal point x - t beta, [batch][n]
-};
-
-// Writes one query's outputs from its final state (any group shape).
-template <bool GEN, typename T, int G, int VPT>
-__device__ void emit(const DiagEvalArgs<T>& A, Query<T, G, VPT>& Q, int64_t q, T tq, int k, bool conv) {
-  double H;
-  const double phi = Q.template objective<GEN>(A.P, (double)tq, &H);
-  const int l = group_lane<G>();
-  const bool finite = isfinite(phi);
-#pragma unroll
-  for (int j = 0; j < VPT; ++j) {
-    const int i = l + G * j;
-    if (i < A.n) A.grad[q * A.n + i] = Q.d[j];
-  }
-  if (A.beta) {
-    // at the fixed point lambda b = y - A d, so the control
-    // (y - A p) / t = b / tau lies in dH(p) (b = u - prox(u) in tau dH)
-    const T tau = tq / A.P.lam;
-#pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-      const int i = l + G * j;
-      if (i < A.n) {
-        const T bt = tau > T(0) ? Q.b[j] / tau : T(0);
-        A.beta[q * A.n + i] = bt;
-        if (A.xfin) A.xfin[q * A.n + i] = A.x[q * A.n + i] - tq * bt;
-      }
-    }
-  }
-  if (l == 0) {
-    A.phi[q] = phi;
-    if (A.dphidt) A.dphidt[q] = (T)(-H);
-    if (A.iters) A.iters[q] = k;
-    if (A.qstatus)
-      A.qstatus[q] = !(tq >= T(0)) ? Q_BAD_INPUT : (!finite ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED));
-  }
-}
-
 // Lanes of a thread-per-query warp still iterating when at most this many
 // remain hand their query to the whole warp (the runtime kinds, whose
 // iteration counts run on a heavy tail: 1/2|x|_1^2 needs 10^2 iterations on

@@ -36,6 +36,15 @@ struct DiagPart {
   const double* P64;  // H_ANORM: the FP64 eigenvectors (H in the objective)
 };
 
+// Barrier over the G threads of a query group larger than a warp: named
+// barrier 15 with G threads (the whole block in the plain kernels, whose
+// blocks are one group; the first G threads of a persistent solver CTA that
+// runs diagonal work next to its other roles).
+template <int G>
+__device__ __forceinline__ void group_sync() {
+  asm volatile("bar.sync 15, %0;" ::"n"(G) : "memory");
+}
+
 // Sum of three values over the G threads of a query group.
 template <int G, typename T>
 struct Group {
@@ -52,13 +61,13 @@ struct Group {
       a = warp_sum(a);
       b = warp_sum(b);
       c = warp_sum(c);
-      __syncthreads();
+      group_sync<G>();
       if (lane == 0) {
         s[0][wid] = a;
         s[1][wid] = b;
         s[2][wid] = c;
       }
-      __syncthreads();
+      group_sync<G>();
       a = T(0);
       b = T(0);
       c = T(0);
@@ -83,9 +92,9 @@ struct Group {
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-      __syncthreads();
+      group_sync<G>();
       if (lane == 0) sm[wid] = a;
-      __syncthreads();
+      group_sync<G>();
       a = sm[0];
 #pragma unroll
       for (int k = 1; k < G / 32; ++k) a = fmax(a, sm[k]);
@@ -100,9 +109,9 @@ struct Group {
       return __shfl_sync(0xffffffffu, a, 0);
     } else {
       __shared__ T s0;
-      __syncthreads();
+      group_sync<G>();
       if (threadIdx.x == 0) s0 = a;
-      __syncthreads();
+      group_sync<G>();
       return s0;
     }
   }
@@ -586,6 +595,59 @@ template <>
 inline DiagPart<double> part_of<double>(hopf_handle h) {
   return DiagPart<double>{h->d_A, h->d_c, h->d_w, h->c0,        h->lambda,
                           h->tol, h->max_iter, h->stop_rule, h->h_kind, h->j_kind, h->d_P, h->d_PT, h->d_P};
+}
+
+// Arguments of a plain diagonal evaluation and the write-out of one query's
+// results (shared by the per-instance kernels and the ragged work list).
+template <typename T>
+struct DiagEvalArgs {
+  DiagPart<T> P;
+  int n;
+  int64_t batch;
+  const T* x;
+  const T* t;
+  double* phi;
+  T* grad;
+  T* dphidt;
+  int32_t* iters;
+  uint8_t* qstatus;
+  T* beta;  // optional: control in dH(grad phi), [batch][n]
+  T* xfin;  // optional: terminal point x - t beta, [batch][n]
+};
+
+// Writes one query's outputs from its final state (any group shape).
+template <bool GEN, typename T, int G, int VPT>
+__device__ void emit(const DiagEvalArgs<T>& A, Query<T, G, VPT>& Q, int64_t q, T tq, int k, bool conv) {
+  double H;
+  const double phi = Q.template objective<GEN>(A.P, (double)tq, &H);
+  const int l = group_lane<G>();
+  const bool finite = isfinite(phi);
+#pragma unroll
+  for (int j = 0; j < VPT; ++j) {
+    const int i = l + G * j;
+    if (i < A.n) A.grad[q * A.n + i] = Q.d[j];
+  }
+  if (A.beta) {
+    // at the fixed point lambda b = y - A d, so the control
+    // (y - A p) / t = b / tau lies in dH(p) (b = u - prox(u) in tau dH)
+    const T tau = tq / A.P.lam;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      const int i = l + G * j;
+      if (i < A.n) {
+        const T bt = tau > T(0) ? Q.b[j] / tau : T(0);
+        A.beta[q * A.n + i] = bt;
+        if (A.xfin) A.xfin[q * A.n + i] = A.x[q * A.n + i] - tq * bt;
+      }
+    }
+  }
+  if (l == 0) {
+    A.phi[q] = phi;
+    if (A.dphidt) A.dphidt[q] = (T)(-H);
+    if (A.iters) A.iters[q] = k;
+    if (A.qstatus)
+      A.qstatus[q] = !(tq >= T(0)) ? Q_BAD_INPUT : (!finite ? Q_NONFINITE : (conv ? Q_OK : Q_NOT_CONVERGED));
+  }
 }
 
 }  // namespace hopf

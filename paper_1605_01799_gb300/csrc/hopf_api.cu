@@ -141,6 +141,13 @@ hopf_status hopf_batch_eval(hopf_batch b, const int64_t* counts, const float* x,
   return batch_eval(b, counts, x, t, phi, grad, dphidt, iters, qstatus, workspace, ws_bytes, stream);
 }
 
+hopf_status hopf_batch_set_mode(hopf_batch b, int32_t mode) {
+  set_error("");
+  if (!b || mode < 0 || mode > 2) return fail(HOPF_EINVAL, "hopf_batch_set_mode: bad batch or mode");
+  batch_set_mode(b, mode);
+  return HOPF_OK;
+}
+
 hopf_status hopf_batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms) {
   set_error("");
   if (!b) return fail(HOPF_EINVAL, "hopf_batch_info: null batch");

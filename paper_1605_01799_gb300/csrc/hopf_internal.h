@@ -150,6 +150,18 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
                           float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,
                           float* xfin = nullptr);
 
+// ---- ragged batches in one persistent launch (dense_tc.cu) ----
+size_t ragged_dense_record_bytes();
+size_t ragged_diag_record_bytes();
+hopf_status ragged_build_dense(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                               float* dphidt, int32_t* iters, uint8_t* qstatus, void* rec);
+int ragged_diag_class(hopf_handle h);  // work-list shape class of a diagonal instance, -1: its own launch
+void ragged_build_diag(hopf_handle h, int64_t B, const float* x, const float* t, double* phi, float* grad,
+                       float* dphidt, int32_t* iters, uint8_t* qstatus, void* rec);
+hopf_status ragged_prepare();
+hopf_status ragged_launch(const void* dense, const int4* sched, const int* sched_off, int grid, const void* diag,
+                          const int4* dinfo, int n_diag, int n_items, unsigned* ctr, cudaStream_t stream);
+
 // ---- backward on the tensor cores (syrk_tc.cu) ----
 size_t syrk_workspace(const hopf_handle h, int64_t batch);
 hopf_status backward_dense_tc(hopf_handle h, int64_t batch, const float* g_phi, const float* vstar, float* g_A,
@@ -177,5 +189,6 @@ hopf_status batch_eval(hopf_batch b, const int64_t* counts, const float* x, cons
                        float* dphidt, int32_t* iters, uint8_t* qstatus, void* ws, size_t ws_bytes,
                        cudaStream_t stream);
 hopf_status batch_info(hopf_batch b, int32_t* nstreams, int32_t* used_graph, float* tuned_ms);
+void batch_set_mode(hopf_batch b, int mode);
 
 }  // namespace hopf

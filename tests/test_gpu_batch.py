@@ -81,18 +81,24 @@ def _alloc(inst):
             "status": torch.empty(Q, dtype=torch.uint8, device="cuda")}
 
 
-def test_ragged_batch_against_oracle_and_single(hg, orc):
+@pytest.mark.parametrize("mode", [1, 2, 0])
+def test_ragged_batch_against_oracle_and_single(hg, orc, mode):
+    """Each schedule (1: the persistent launch, 2: per-instance launches on
+    streams, 0: the tuner's pick)."""
     import torch
     inst = _instances()
     descs = _descs(inst, hg)
     b = hg.HopfBatch(descs)
+    b.set_mode(mode)
     counts = [d["x"].shape[0] for d in inst]
     x, t = _flat(inst)
     out = b.eval(counts, x, t, out=_alloc(inst))
     torch.cuda.synchronize()
     info = b.info()
-    assert info["nstreams"] in (1, 2, 4, 8, 16) and info["used_graph"]
-    assert all(ms > 0 for ms in info["tuned_ms"])
+    assert info["nstreams"] in (1, 2, 4, 8, 16, 32) and info["used_graph"]
+    assert all(ms > 0 for ms in info["tuned_ms"][:5])
+    if mode:
+        assert info["schedule"] == {1: "persistent", 2: "streams"}[mode]
     per = _split(out, inst)
     for i, (d, desc, r) in enumerate(zip(inst, descs, per)):
         B = d["x"].shape[0]
@@ -153,4 +159,52 @@ def test_ragged_batch_replay_and_recapture(hg):
         c = half[i]
         assert np.array_equal(f["phi"][:c], p["phi"]), i
         assert np.array_equal(f["grad"][:c], p["grad"]), i
+    b.close()
+
+
+def test_persistent_schedule_every_branch(hg, orc):
+    """The persistent launch with every kind of instance it meets: a wide
+    dense instance (152 tiles: the whole grid), dense MIXED and SPLIT
+    instances on lanes, a dense FP32 one and a diagonal l_inf one on their
+    own launches beside it, and diagonal instances of every work-list shape
+    (thread per query for n <= 4, 8, 16; warp per query for n <= 64, 256, 512;
+    256 threads per query for n <= 4096).  Every output bit-identical to the
+    instance evaluated alone; sampled queries against the oracle."""
+    import torch
+    P = hg
+    spec = [  # (n, queries, dense, h_kind, precision)
+        (512, 4864, True, 1, P.P_MIXED), (200, 300, True, 0, P.P_SPLIT), (150, 100, True, 2, P.P_FP32),
+        (260, 700, True, 2, P.P_MIXED), (3, 1000, False, 0, P.P_FP32), (6, 500, False, 1, P.P_FP32),
+        (12, 300, False, 2, P.P_FP32), (40, 257, False, 0, P.P_FP32), (200, 90, False, 1, P.P_FP32),
+        (400, 33, False, 2, P.P_FP32), (3000, 40, False, 0, P.P_FP32), (20, 100, False, P.H_LINF, P.P_FP32)]
+    inst, descs = [], []
+    for i, (n, B, dense, hk, prec) in enumerate(spec):
+        d = wl.ragged_instance({"index": 300 + i, "n": n, "queries": B, "dense": dense, "h_kind": hk % 3})
+        d["A"] = d["A"] if dense else d["a"]
+        d["h_kind"] = hk
+        inst.append(d)
+        descs.append({"A": d["A"], "h_kind": hk, "w": d["w"], "c0": d["c0"], "lam": d["lam"],
+                      "tol": 1e-13 if dense else 1e-12, "max_iter": 3000, "precision": prec,
+                      "stop_rule": P.STOP_UREL})
+    b = hg.HopfBatch(descs)
+    b.set_mode(1)
+    counts = [d["x"].shape[0] for d in inst]
+    x, t = _flat(inst)
+    out = b.eval(counts, x, t, out=_alloc(inst))
+    torch.cuda.synchronize()
+    assert b.info()["schedule"] == "persistent"
+    per = _split(out, inst)
+    for i, (d, desc, r) in enumerate(zip(inst, descs, per)):
+        assert (r["status"] == P.Q_OK).all(), i
+        h = hg.Hopf(desc["A"], desc["h_kind"], w=desc["w"], c0=desc["c0"], lam=desc["lam"], tol=desc["tol"],
+                    max_iter=desc["max_iter"], precision=desc["precision"], stop_rule=desc["stop_rule"])
+        one = h.eval(torch.tensor(d["x"], device="cuda"), torch.tensor(d["t"], device="cuda"))
+        torch.cuda.synchronize()
+        for key in ("phi", "grad", "iters", "status"):
+            assert np.array_equal(one[key].cpu().numpy().reshape(r[key].shape), r[key]), (i, key)
+        q = np.unique([0, len(r["phi"]) // 2, len(r["phi"]) - 1])
+        ref = orc.Problem(d["A"], desc["h_kind"], w=d["w"], c0=d["c0"], lam=d["lam"], tol=1e-28, max_iter=100000,
+                          stop_rule=orc.STOP_UREL).eval(d["x"][q].astype(np.float64), d["t"][q].astype(np.float64))
+        ep = np.abs(r["phi"][q] - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))
+        assert ep.max() <= 1e-6, (i, ep.max())
     b.close()
