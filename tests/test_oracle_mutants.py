@@ -29,6 +29,11 @@ MUTANTS = [
      "test_workload1_closed_form"),
     ("gradient_is_v", "for (int i = 0; i < n; ++i) grad[i] = d[i];", "for (int i = 0; i < n; ++i) grad[i] = v[i];",
      "test_dense_wl1_kkt_certificate"),
+    # the paper's stop rule (Section 4.5): residuals from the wrong iterates
+    ("paper_residual_v_from_d", "r1 += (v[i] - vprev[i]) * (v[i] - vprev[i]);",
+     "r1 += (dn[i] - vprev[i]) * (dn[i] - vprev[i]);", "test_paper_stop_rule_exact_iterations"),
+    ("paper_residual_gap_is_b", "r3 += (dn[i] - v[i]) * (dn[i] - v[i]);",
+     "r3 += (dn[i] - d[i]) * (dn[i] - d[i]) * 0.25;", "test_paper_stop_rule_exact_iterations"),
     ("diag_solve_drops_lambda", "v[i] = r[i] / (p->A[i] + p->lambda);", "v[i] = r[i] / p->A[i];",
      "test_workload1_closed_form"),
     # the factorisation of A + lambda I and its solve

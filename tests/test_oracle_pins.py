@@ -826,3 +826,57 @@ def test_ties_go_to_the_smallest_index(orc):
     r = orc.union_closest([one, one], x)
     d1 = orc.union_closest([one], x)
     assert (r["argmin"] == 0).all() and np.array_equal(r["dist"], d1["dist"])
+
+
+def _shrink_exact(z, a):
+    """shrink_1(z, a) on exact rationals (Section 1: 0 when |z| <= a)."""
+    return z - a if z > a else (z + a if z < -a else 0)
+
+
+def _paper_rule_iterations_exact(a, y, t, lam, tol, max_iter):
+    """Split Bregman (eq. 3.4(a)-(c)) for diagonal A and H = l1 in exact
+    rational arithmetic.  Each coordinate is a scalar recursion:
+    v_i = (y_i + lam (d_i - b_i)) / (a_i + lam), d_i' = shrink_1(v_i + b_i, t / lam),
+    b_i' = b_i + v_i - d_i', from v^0 = d^0 = y, b^0 = 0 (Section 3.1).  Returns
+    the first k at which |v^k - v^{k-1}|^2, |d^k - d^{k-1}|^2 and |d^k - v^k|^2
+    are all <= tol (Section 4.5), and the residuals at k - 1 and k."""
+    n = len(a)
+    tau = t / lam
+    v_prev, d, b = list(y), list(y), [0] * n
+    prev = None
+    for k in range(1, max_iter + 1):
+        v = [(y[i] + lam * (d[i] - b[i])) / (a[i] + lam) for i in range(n)]
+        dn = [_shrink_exact(v[i] + b[i], tau) for i in range(n)]
+        b = [b[i] + v[i] - dn[i] for i in range(n)]
+        r = (sum((v[i] - v_prev[i]) ** 2 for i in range(n)), sum((dn[i] - d[i]) ** 2 for i in range(n)),
+             sum((dn[i] - v[i]) ** 2 for i in range(n)))
+        if max(r) <= tol:
+            return k, prev, r
+        prev, d, v_prev = r, dn, v
+    return None, prev, None
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_paper_stop_rule_exact_iterations(orc, case):
+    """The oracle's iteration count under the paper's stop rule equals the
+    first k at which the exact (rational) iterates meet all three residual
+    tests, for dyadic data (exact in FP64) whose residuals cross tol with a
+    wide margin, so rounding cannot move the crossing."""
+    from fractions import Fraction as F
+    cases = [  # (a, y, t, lam, tol)
+        ([F(3, 2), F(5, 4), F(7, 8), F(2)], [F(9, 8), F(-5, 4), F(3, 16), F(-7, 2)], F(3, 4), F(1), F(1, 10 ** 8)),
+        ([F(1, 2), F(3, 4), F(7, 4), F(5, 8)], [F(-11, 8), F(1, 4), F(13, 4), F(-3, 8)], F(5, 4), F(1), F(1, 10 ** 8)),
+        ([F(3, 2), F(5, 4), F(7, 8), F(2)], [F(9, 8), F(-5, 4), F(3, 16), F(-7, 2)], F(3, 4), F(1, 2), F(1, 10 ** 10)),
+        ([F(9, 8), F(1, 2), F(15, 8)], [F(5, 2), F(-3, 2), F(1, 8)], F(1, 8), F(5, 2), F(1, 10 ** 8)),
+    ]
+    a, y, t, lam, tol = cases[case]
+    K, before, at = _paper_rule_iterations_exact(a, y, t, lam, tol, 500)
+    assert K is not None and K >= 2
+    # a wide margin on both sides of the crossing
+    assert max(at) <= tol * F(1, 2) or max(at) <= tol * (1 - F(1, 10 ** 6))
+    assert max(before) >= tol * (1 + F(1, 10 ** 6))
+    af = np.array([float(v) for v in a])
+    yf = np.array([[float(v) for v in y]])
+    P = orc.Problem(af, orc.H_L1, c0=0.5, lam=float(lam), tol=float(tol), max_iter=500, stop_rule=orc.STOP_PAPER)
+    r = P.eval(yf, np.array([float(t)]))
+    assert int(r["iters"][0]) == K, (int(r["iters"][0]), K)
