@@ -718,7 +718,7 @@ def run_control(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
-        rate, threads, r, dt = oracle_sample(A, w, x, t, args.cpu_sample, tol)
+        rate, threads, r, dt = oracle_sample(A, w, x, t, args.cpu_sample, TOL)
         P = oracle.Problem(A, oracle.H_WL1, w=w, tol=TOL, max_iter=MAX_ITER, stop_rule=oracle.STOP_UREL)
         m = args.cpu_sample
         t0 = time.perf_counter()
