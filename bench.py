@@ -46,8 +46,8 @@ METRIC = ("Hopf evals/s (phi at 1e-6 rel, grad phi at 6e-6 rel) n=1024 batch 64K
 # the dominant kernel at the default workload, from the ncu capture summarised
 # in profiles/k_dense_tc_n1024_b65536.md; reported only while the kernel
 # source still has the hash it had at capture.
-MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "4747f900ec3c3421",
-                              "bytes": 155.24e9, "n": 1024, "batch": 65536}}
+MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "16674fec0d4087f3",
+                              "bytes": 155.57e9, "n": 1024, "batch": 65536}}
 TOL = 1e-13
 MAX_ITER = 1000
 
@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-arms", action="store_true", help="time the chosen form only (no FP32 / SPLIT arms)")
+    p.add_argument("--tc-pairs", type=int, default=0, choices=[0, 1],
+                   help="dense tensor-core forms: SM pairs (cta_group::2) on (1) or off (0, the default)")
     p.add_argument("--ragged-mode", type=int, default=0, choices=[0, 1, 2],
                    help="--workload ragged: 0 the tuner picks, 1 the persistent launch, 2 the stream schedule")
     p.add_argument("--workload", default="dense", choices=["dense", "ragged", "union", "grad", "control", "maxh", "paper", "fit"])
@@ -1128,6 +1130,7 @@ def main():
         """Time `steps` hopf_eval calls of one form on the device-resident
         workload; the solver kernel alone is timed by the handle's events."""
         h = hg.Hopf(A, hg.H_WL1, w=w, tol=tol, max_iter=MAX_ITER, precision=PREC[variant])
+        h.set_tc_pairs(args.tc_pairs)
         wsbuf = h.workspace(B)
         out = None
         for _ in range(warmup):
@@ -1276,6 +1279,7 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": "dense_wl1_n%d_b%d" % (n, B), "n": n, "batch_per_gpu": B,
                            "variant": main_variant, "tol_urel": tol, "max_iter": MAX_ITER,
+                           "sm_pairs": bool(args.tc_pairs),
                            "parallelism": "replicas" if ws == 1 else "dp%d (independent query shards)" % ws,
                            "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
                 "iters": {"mean": float(K.mean()), "max": int(K.max()), "min": int(K.min())},

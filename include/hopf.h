@@ -370,6 +370,17 @@ hopf_status hopf_profile_events(hopf_handle h, cudaEvent_t start, cudaEvent_t st
  * thread-safe with concurrent evaluations on the same handle. */
 hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles);
 
+/* Dense A on the tensor cores: with on != 0 a call whose padded n is a
+ * multiple of 256 runs each MMA over an SM pair (a cluster of two CTAs,
+ * tcgen05 cta_group::2: a 256 x 128 tile per pair, each CTA bringing in its
+ * own 128 rows of A and half of the 128 query rows of the operand); on == 0
+ * (the default: on GB300 the pairs measured 5-9 % slower on the dense
+ * workloads) keeps one CTA per 128 x 128 tile.  Both compute every product in
+ * the same K order, so the outputs agree bit for bit.  Takes effect at the
+ * next evaluation; ragged batches always use single CTAs.  (The paper has no
+ * counterpart.) */
+hopf_status hopf_set_tc_pairs(hopf_handle h, int32_t on);
+
 /* Device allocator for the memory hopf_create and hopf_batch_create keep (the
  * handle's copies of A, M and the weights, and their set-up scratch).
  * alloc(bytes, ctx) returns device memory or NULL (then the create call

@@ -33,8 +33,8 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_batch_set_mode",
            "hopf_eval_control", "hopf_maxH_eval",
-           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_allocator",
-           "hopf_last_error", "hopf_version"]
+           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_tc_pairs",
+           "hopf_set_allocator", "hopf_last_error", "hopf_version"]
 
 
 class HopfError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
                                   ctypes.c_int),
             "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_set_wait_limit": ([_vp, _i64], ctypes.c_int),
+            "hopf_set_tc_pairs": ([_vp, ctypes.c_int32], ctypes.c_int),
             "hopf_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_measure_pipes_scratch": ([], _sz),
             "hopf_measure_pipes": ([_vp, _sz, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -243,6 +244,10 @@ class Hopf:
     def set_wait_limit(self, cycles):
         """Clock-cycle limit of the dense solvers' bounded waits (0: default)."""
         _check(lib().hopf_set_wait_limit(self.handle, int(cycles)))
+
+    def set_tc_pairs(self, on):
+        """Dense tensor-core path: SM pairs (cta_group::2) on or off."""
+        _check(lib().hopf_set_tc_pairs(self.handle, 1 if on else 0))
 
     def set_compaction(self, on):
         _check(lib().hopf_set_compaction(self.handle, 1 if on else 0))

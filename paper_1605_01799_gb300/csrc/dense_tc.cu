@@ -69,9 +69,26 @@ hopf_status dense_finalize(hopf_handle h, DenseWs& w, double* phi, float* dphidt
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;        // 16 KB: 128 rows x 128 bytes
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // up to 2 A tiles + 2 B tiles
+// The ring by CG, the number of CTAs per MMA: CG = 1, one CTA per 128 x 128
+// tile, three stages of 64 KB; CG = 2, an SM pair (a cluster of two CTAs) per
+// 256 x 128 tile, each CTA holding its 128 rows of A and 64 of the 128 B rows,
+// four stages of 48 KB.  A stage holds two A tiles and two B tiles.
+template <int CG>
+struct Ring {
+  static constexpr int STAGES = CG == 1 ? 3 : 4;
+  static constexpr int BH = BN / CG;                         // B rows held by one CTA
+  static constexpr int B_BYTES = BH * BK * 2;                // one B tile
+  static constexpr int STAGE_BYTES = 2 * TILE_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t A1 = TILE_BYTES >> 4;            // descriptor offsets within a stage
+  static constexpr uint32_t B0 = (2 * TILE_BYTES) >> 4;
+  static constexpr uint32_t B1 = (2 * TILE_BYTES + B_BYTES) >> 4;
+};
+constexpr int MAX_STAGES = 4;
+constexpr int RING_BYTES = 3 * 4 * TILE_BYTES;
+static_assert(Ring<1>::STAGES * Ring<1>::STAGE_BYTES == RING_BYTES, "ring size");
+static_assert(Ring<2>::STAGES * Ring<2>::STAGE_BYTES == RING_BYTES, "ring size");
 #ifndef HOPF_TC_EPI_WARPS
 #define HOPF_TC_EPI_WARPS 16
 #endif
@@ -155,7 +172,8 @@ __device__ __forceinline__ float prox1(float u, float w, float tau, float sc, in
 
 // -------------------------------------------------------------- shared state
 struct Smem {
-  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  uint64_t full[MAX_STAGES], empty[MAX_STAGES], tfull[2], tempty[2], drain;
+  uint64_t pfull[MAX_STAGES];  // SM pairs: the second CTA's stage is full (arrivals from the pair's CTA 1)
   uint64_t cfull[2], cempty[2];  // final pass: hand-off of the D1 chunks
   uint32_t tmem_base;
   int abort;
@@ -178,6 +196,7 @@ struct PhaseCfg {
   uint32_t idesc;
 };
 
+template <int CG>
 __device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
   PhaseCfg c{};
   if (ph == PH_A || ph == PH_F || ph == PH_S) {
@@ -185,11 +204,11 @@ __device__ __forceinline__ PhaseCfg phase_cfg(int ph) {
     c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // A_hi p_hi     -> D1
     c.ta[1] = 0; c.tb[1] = 1; c.td[1] = 1;   // A_hi p_lo'    -> D2
     c.ta[2] = 1; c.tb[2] = 0; c.td[2] = 1;   // A_lo' p_hi    -> D2
-    c.idesc = idesc_f16(0);                  // (PH_S: M_hi r_hi, M_hi r_lo', M_lo' r_hi)
+    c.idesc = idesc_f16_mn(0, BM * CG, BN);  // (PH_S: M_hi r_hi, M_hi r_lo', M_lo' r_hi)
   } else {
     c.na = 1; c.nb = 1; c.nterm = 1;
     c.ta[0] = 0; c.tb[0] = 0; c.td[0] = 0;   // M (g or r)    -> D1
-    c.idesc = idesc_f16(1);
+    c.idesc = idesc_f16_mn(1, BM * CG, BN);
   }
   return c;
 }
@@ -211,23 +230,30 @@ __device__ __forceinline__ bool tile_on(const TcArgs& a, const Ctx& x, int ph, i
   if (ph == PH_B) return a.tile_k[c] == x.k;
   return x.k == 1 || x.fresh || a.tile_k[c] >= x.k - 1;
 }
+// The items of a phase, dealt round-robin over the group's CTAs (CG = 1) or
+// SM pairs (CG = 2): item it is column tile it / (rt / CG) and row tile
+// CG (it % (rt / CG)) + (gr % CG), so the two CTAs of a pair take the two
+// row tiles of one 256-row block of the same column tile.
+template <int CG>
 __device__ __forceinline__ int phase_items(const TcArgs& a, const Ctx& x, int ph) {
-  return a.rt * (ph == PH_F ? a.ct : x.ct_on);
+  return (a.rt / CG) * (ph == PH_F ? a.ct : x.ct_on);
 }
 
 // ------------------------------------------------------------ role: producer
 struct ProdState {
   uint32_t kb = 0;                 // k-blocks issued so far (ring position)
-  uint32_t last_par[STAGES];       // parity of the last load issued into each stage
-  bool used[STAGES];
+  uint32_t last_par[MAX_STAGES];   // parity of the last load issued into each stage
+  bool used[MAX_STAGES];
 };
 
 // BF16 form: r^{k-1} lives in buffer (k-1) & 1 (p1 = buffer 0, p2 = buffer 1)
 // and the epilogue of iteration k writes r^k into the other one, so no CTA
 // overwrites an operand another CTA may still be loading.
+template <int CG>
 __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, int k, const Ctx& x,
                                ProdState& st) {
-  const PhaseCfg cfg = phase_cfg(ph);
+  using R = Ring<CG>;
+  const PhaseCfg cfg = phase_cfg<CG>(ph);
   const CUtensorMap* A0 = (ph == PH_A || ph == PH_F) ? &a.mAh : ph == PH_S ? &a.mMh : &a.mM;
   const CUtensorMap* A1 = ph == PH_S ? &a.mMl : &a.mAl;
   const CUtensorMap* B0 = ph == PH_A ? (x.cb ? &a.mP1b : &a.mP1)
@@ -243,37 +269,40 @@ __device__ void producer_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph
   }
   // phases with one operand pair (B, P) fill a stage with two k-blocks
   const int kstep = cfg.na == 1 ? 2 : 1;
-  const uint32_t bytes = 4u * TILE_BYTES;
-  const int nk = a.np / BK, items = phase_items(a, x, ph);
+  const uint32_t bytes = R::STAGE_BYTES;
+  const int nk = a.np / BK, items = phase_items<CG>(a, x, ph), rpc = a.rt / CG, rank = x.gr % CG;
   const int nsub = ph == PH_F ? 2 : 1;  // PH_F: {A1, A2 | p1, p2} then {A1, A3 | p3, p1}
-  for (int it = x.gr; it < items; it += x.gs) {
-    const int r = it % a.rt, c = it / a.rt;
+  for (int it = x.gr / CG; it < items; it += x.gs / CG) {
+    const int r = CG * (it % rpc) + rank, c = it / rpc;
     if (!tile_on(a, x, ph, c)) continue;
+    const int cq = c * BN + rank * R::BH;  // the first B row (query) this CTA loads
     // the epilogue of this item reads u of its tile one to two items from
     // now: start the DRAM reads now (a prefetch of y as well measured slower)
     if (ph != PH_F) tma_prefetch_l2(&a.mU[x.cb], r * BM, c * BN);
     for (int kb = 0; kb < nk; kb += kstep) {
       for (int sub = 0; sub < nsub; ++sub, ++st.kb) {
-        const uint32_t s = st.kb % STAGES, use = st.kb / STAGES;
+        const uint32_t s = st.kb % R::STAGES, use = st.kb / R::STAGES;
         if (!mbar_wait_lim(sa(&S.empty[s]), (use & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
         const uint32_t full = sa(&S.full[s]);
         mbar_expect_tx(full, bytes);
-        uint8_t* base = stages + (size_t)s * STAGE_BYTES;
+        uint8_t* base = stages + (size_t)s * R::STAGE_BYTES;
+        uint8_t* bt0 = base + 2 * TILE_BYTES;
+        uint8_t* bt1 = bt0 + R::B_BYTES;
         const int kx = kb * BK;
         if (kstep == 2) {
           // {M_kb, M_kb+1 | g_kb, g_kb+1}
           tma_load(sa(base), A0, full, kx, r * BM);
           tma_load(sa(base + TILE_BYTES), A0, full, kx + BK, r * BM);
-          tma_load(sa(base + 2 * TILE_BYTES), B0, full, kx, c * BN);
-          tma_load(sa(base + 3 * TILE_BYTES), B0, full, kx + BK, c * BN);
+          tma_load(sa(bt0), B0, full, kx, cq);
+          tma_load(sa(bt1), B0, full, kx + BK, cq);
         } else {
           const CUtensorMap* a1 = sub ? &a.mAl2 : A1;
           const CUtensorMap* b0 = sub ? &a.mP3 : B0;
           const CUtensorMap* b1 = sub ? &a.mP1 : B1;
           tma_load(sa(base), A0, full, kx, r * BM);
           tma_load(sa(base + TILE_BYTES), a1, full, kx, r * BM);
-          tma_load(sa(base + 2 * TILE_BYTES), b0, full, kx, c * BN);
-          tma_load(sa(base + 3 * TILE_BYTES), b1, full, kx, c * BN);
+          tma_load(sa(bt0), b0, full, kx, cq);
+          tma_load(sa(bt1), b1, full, kx, cq);
         }
         st.last_par[s] = use & 1;
         st.used[s] = true;
@@ -292,7 +321,7 @@ struct MmaState {
   uint32_t ue[2] = {0, 0}, uf[2] = {0, 0};
   uint32_t ce[2] = {0, 0}, cf[2] = {0, 0};  // final-pass chunk slots
   bool issued = false;
-  uint64_t sdesc[STAGES];  // shared-memory descriptor of each ring stage's first tile
+  uint64_t sdesc[MAX_STAGES];  // shared-memory descriptor of each ring stage's first tile
 };
 
 // The ordinary phases with as few instructions per MMA as possible: one
@@ -306,159 +335,153 @@ struct MmaState {
 //          A0 B0 -> D1, A0 B1 + A1 B0 -> D2;
 //   else:  phases B and P, two k-blocks per stage {M_kb, M_kb+1 | g_kb, g_kb+1},
 //          K steps alternating between D1 and D2.
-template <bool THREE>
+//   SM pairs: CTA 0 of the pair issues M = 256 MMAs over both CTAs' stages
+//   once its own stage and the other CTA's are full (CTA 1's MMA thread
+//   relays its full barriers to CTA 0's pfull); the commits arrive in both
+//   CTAs, and both CTAs' epilogues release the accumulator to CTA 0.
+template <int CG, bool THREE>
 __device__ __forceinline__ void mma_items(const TcArgs& a, Smem& S, int ph, const Ctx& x, MmaState& st,
                                           uint32_t idesc) {
+  using R = Ring<CG>;
   const int nst = THREE ? a.np / BK : a.np / (2 * BK);  // stages per item
-  const int items = phase_items(a, x, ph);
-  int it = x.gr;
-  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
-  uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
+  const int items = phase_items<CG>(a, x, ph), rpc = a.rt / CG, step = x.gs / CG;
+  const bool lead = CG == 1 || x.gr % CG == 0;
+  int it = x.gr / CG;
+  while (it < items && !tile_on(a, x, ph, it / rpc)) it += step;
+  uint32_t s = st.kb % R::STAGES, suse = st.kb / R::STAGES;
   while (it < items) {
-    const int nx = it + x.gs;
-    const bool nx_on = nx < items && tile_on(a, x, ph, nx / a.rt);  // used after this item
-    const uint32_t buf = st.nb;
-    st.nb ^= 1;
-    if (!mbar_wait_lim(sa(&S.tempty[buf]), (st.ue[buf] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
-    ++st.ue[buf];
-    tc_fence_after();
-    const uint32_t d1 = S.tmem_base + buf * 256, d2 = d1 + BN;
-    for (int j = 0; j < nst; ++j) {
-      if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
-      tc_fence_after();
-      const uint64_t b = st.sdesc[s];
-      if constexpr (THREE) {
-#pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          mma_f16(d1, b + kk * 2, b + 2048 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
-          mma_f16(d2, b + kk * 2, b + 3072 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
-          mma_f16(d2, b + 1024 + kk * 2, b + 2048 + kk * 2, idesc, 1u);
+    const int nx = it + step;
+    const bool nx_on = nx < items && tile_on(a, x, ph, nx / rpc);  // used after this item
+    if (!lead) {
+      for (int j = 0; j < nst; ++j) {
+        if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+        mbar_arrive_rank(sa(&S.pfull[s]), 0);
+        if (++s == R::STAGES) {
+          s = 0;
+          ++suse;
         }
-      } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            mma_f16((kk & 1) ? d2 : d1, b + h * 1024 + kk * 2, b + (2 + h) * 1024 + kk * 2, idesc,
-                    (j == 0 && h == 0 && kk < 2) ? 0u : 1u);
       }
-      st.issued = true;
-      mma_commit(sa(&S.empty[s]));  // frees the stage once these MMAs have read it
-      if (++s == STAGES) {
-        s = 0;
-        ++suse;
+      st.kb += nst;
+    } else {
+      const uint32_t buf = st.nb;
+      st.nb ^= 1;
+      const uint32_t tpar = (st.ue[buf] & 1) ^ 1;
+      if (!mbar_wait_lim(sa(&S.tempty[buf]), tpar, a.err, &S.abort, a.wait_limit)) return;
+      ++st.ue[buf];
+      tc_fence_after();
+      const uint32_t d1 = S.tmem_base + buf * 256, d2 = d1 + BN;
+      for (int j = 0; j < nst; ++j) {
+        if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+        if (CG == 2 && !mbar_wait_lim(sa(&S.pfull[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+        tc_fence_after();
+        const uint64_t b = st.sdesc[s];
+        if constexpr (THREE) {
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            mma_f16_cg<CG>(d1, b + kk * 2, b + R::B0 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
+            mma_f16_cg<CG>(d2, b + kk * 2, b + R::B1 + kk * 2, idesc, (j == 0 && kk == 0) ? 0u : 1u);
+            mma_f16_cg<CG>(d2, b + R::A1 + kk * 2, b + R::B0 + kk * 2, idesc, 1u);
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_f16_cg<CG>((kk & 1) ? d2 : d1, b + h * R::A1 + kk * 2, b + (h ? R::B1 : R::B0) + kk * 2, idesc,
+                             (j == 0 && h == 0 && kk < 2) ? 0u : 1u);
+        }
+        st.issued = true;
+        mma_commit_cg<CG>(sa(&S.empty[s]));  // frees the stage (in both CTAs) once these MMAs have read it
+        if (++s == R::STAGES) {
+          s = 0;
+          ++suse;
+        }
       }
+      st.kb += nst;
+      mma_commit_cg<CG>(sa(&S.tfull[buf]));  // accumulator ready for the epilogue(s)
+      ++st.uf[buf];
     }
-    st.kb += nst;
-    mma_commit(sa(&S.tfull[buf]));  // accumulator ready for the epilogue
-    ++st.uf[buf];
     it = nx;
     if (!nx_on)
-      while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
+      while (it < items && !tile_on(a, x, ph, it / rpc)) it += step;
   }
 }
 
+template <int CG>
 __device__ void mma_phase(const TcArgs& a, Smem& S, uint8_t* stages, int ph, const Ctx& x, MmaState& st) {
-  const PhaseCfg cfg = phase_cfg(ph);
-  if (ph == PH_A || ph == PH_S) return mma_items<true>(a, S, ph, x, st, cfg.idesc);
-  if (ph == PH_B || ph == PH_P) return mma_items<false>(a, S, ph, x, st, cfg.idesc);
-  const int nk = a.np / BK, items = phase_items(a, x, ph);
-  for (int it = x.gr; it < items; it += x.gs) {
-    const int c = it / a.rt;
-    if (!tile_on(a, x, ph, c)) continue;
-    const uint32_t buf = ph == PH_F ? 0 : st.nb;
-    if (ph != PH_F) st.nb ^= 1;
+  using R = Ring<CG>;
+  const PhaseCfg cfg = phase_cfg<CG>(ph);
+  if (ph == PH_A || ph == PH_S) return mma_items<CG, true>(a, S, ph, x, st, cfg.idesc);
+  if (ph == PH_B || ph == PH_P) return mma_items<CG, false>(a, S, ph, x, st, cfg.idesc);
+  // the final pass (PH_F): both TMEM buffers per item
+  const int nk = a.np / BK, items = phase_items<CG>(a, x, PH_F), rpc = a.rt / CG;
+  const bool lead = CG == 1 || x.gr % CG == 0;
+  const uint32_t idesc = idesc_f16_mn(0, BM * CG, BN);
+  for (int it = x.gr / CG; it < items; it += x.gs / CG) {
+    const int c = it / rpc;
+    if (!tile_on(a, x, PH_F, c)) continue;
+    if (!lead) {
+      for (int kb = 0; kb < nk; ++kb)
+        for (int sub = 0; sub < 2; ++sub, ++st.kb) {
+          const uint32_t s = st.kb % R::STAGES, suse = st.kb / R::STAGES;
+          if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+          mbar_arrive_rank(sa(&S.pfull[s]), 0);
+        }
+      continue;
+    }
     for (uint32_t b = 0; b < 2; ++b) {
-      if (ph != PH_F && b != buf) continue;
-      if (!mbar_wait_lim(sa(&S.tempty[b]), (st.ue[b] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
+      const uint32_t tpar = (st.ue[b] & 1) ^ 1;
+      if (!mbar_wait_lim(sa(&S.tempty[b]), tpar, a.err, &S.abort, a.wait_limit)) return;
       ++st.ue[b];
     }
     tc_fence_after();
-    const uint32_t d0 = S.tmem_base + buf * 256;
     for (int kb = 0; kb < nk; ++kb) {
-      if (ph == PH_F) {
-        // The main term D1 = A1 p1 goes into one of two 128-column slots per
-        // 128-wide K chunk (two k-blocks); the epilogue adds the chunks up in
-        // registers, so no TMEM accumulator sums more than 8 products of
-        // K = 16.  D2 and D3 (scaled by 2^-11, 2^-22) accumulate over all of K
-        // in the second buffer.  TMEM: D1 slots at 0 and 128, D2 at 256, D3 at 384.
-        const uint32_t chunk = kb >> 1, slot = chunk & 1;
-        if ((kb & 1) == 0) {
-          if (!mbar_wait_lim(sa(&S.cempty[slot]), (st.ce[slot] & 1) ^ 1, a.err, &S.abort, a.wait_limit)) return;
-          ++st.ce[slot];
-          tc_fence_after();
-        }
-        const uint32_t d1 = S.tmem_base + slot * BN, d2 = S.tmem_base + 256, d3 = S.tmem_base + 384;
-        // sub-stage X: {A1, A2 | p1, p2};  sub-stage Y: {A1, A3 | p3, p1}
-        for (int sub = 0; sub < 2; ++sub, ++st.kb) {
-          const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
-          if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
-          tc_fence_after();
-          const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
-          const uint32_t idesc = idesc_f16(0);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t a0 = smem_desc(base) + (uint64_t)(kk * 2);
-            const uint64_t a1 = smem_desc(base + TILE_BYTES) + (uint64_t)(kk * 2);
-            const uint64_t b0 = smem_desc(base + 2 * TILE_BYTES) + (uint64_t)(kk * 2);
-            const uint64_t b1 = smem_desc(base + 3 * TILE_BYTES) + (uint64_t)(kk * 2);
-            const uint32_t fc = ((kb & 1) == 0 && kk == 0) ? 0u : 1u;  // chunk start overwrites D1
-            const uint32_t fi = (kb == 0 && kk == 0) ? 0u : 1u;        // item start overwrites D2, D3
-            if (sub == 0) {
-              mma_f16(d1, a0, b0, idesc, fc);    // D1 += A1 p1
-              mma_f16(d2, a0, b1, idesc, fi);    // D2 += A1 p2
-              mma_f16(d2, a1, b0, idesc, 1u);    // D2 += A2 p1
-              mma_f16(d3, a1, b1, idesc, fi);    // D3 += A2 p2
-            } else {
-              mma_f16(d3, a0, b0, idesc, 1u);    // D3 += A1 p3
-              mma_f16(d3, a1, b1, idesc, 1u);    // D3 += A3 p1
-            }
-          }
-          st.issued = true;
-          mma_commit(sa(&S.empty[s]));
-        }
-        if (kb & 1) {
-          mma_commit(sa(&S.cfull[slot]));  // this chunk of D1 is ready
-          ++st.cf[slot];
-        }
-        continue;
+      // The main term D1 = A1 p1 goes into one of two 128-column slots per
+      // 128-wide K chunk (two k-blocks); the epilogue adds the chunks up in
+      // registers, so no TMEM accumulator sums more than 8 products of
+      // K = 16.  D2 and D3 (scaled by 2^-11, 2^-22) accumulate over all of K
+      // in the second buffer.  TMEM: D1 slots at 0 and 128, D2 at 256, D3 at 384.
+      const uint32_t chunk = kb >> 1, slot = chunk & 1;
+      if ((kb & 1) == 0) {
+        const uint32_t cpar = (st.ce[slot] & 1) ^ 1;
+        if (!mbar_wait_lim(sa(&S.cempty[slot]), cpar, a.err, &S.abort, a.wait_limit)) return;
+        ++st.ce[slot];
+        tc_fence_after();
       }
-      if (cfg.na == 1 && (kb & 1)) continue;  // B, P: the stage of kb holds kb + 1 too
-      const uint32_t s = st.kb % STAGES, suse = st.kb / STAGES;
-      ++st.kb;
-      if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
-      tc_fence_after();
-      const uint32_t base = sa(stages + (size_t)s * STAGE_BYTES);
-      if (cfg.na == 1) {
-        // consecutive K = 16 steps alternate between the buffer's two
-        // accumulators (the epilogue adds them): back-to-back MMAs into one
-        // accumulator at N = 128 run at about two thirds of the MMA rate
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ad = smem_desc(base + h * TILE_BYTES) + (uint64_t)(kk * 2);
-            const uint64_t bd = smem_desc(base + (2 + h) * TILE_BYTES) + (uint64_t)(kk * 2);
-            mma_f16(d0 + (kk & 1) * BN, ad, bd, cfg.idesc, (kb == 0 && h == 0 && kk < 2) ? 0u : 1u);
-          }
-        }
-      } else {
+      const uint32_t d1 = S.tmem_base + slot * BN, d2 = S.tmem_base + 256, d3 = S.tmem_base + 384;
+      // sub-stage X: {A1, A2 | p1, p2};  sub-stage Y: {A1, A3 | p3, p1}
+      for (int sub = 0; sub < 2; ++sub, ++st.kb) {
+        const uint32_t s = st.kb % R::STAGES, suse = st.kb / R::STAGES;
+        if (!mbar_wait_lim(sa(&S.full[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+        if (CG == 2 && !mbar_wait_lim(sa(&S.pfull[s]), suse & 1, a.err, &S.abort, a.wait_limit)) return;
+        tc_fence_after();
+        const uint64_t b = st.sdesc[s];
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          for (int tm = 0; tm < cfg.nterm; ++tm) {
-            const uint64_t ad = smem_desc(base + cfg.ta[tm] * TILE_BYTES) + (uint64_t)(kk * 2);
-            const uint64_t bd = smem_desc(base + (2 + cfg.tb[tm]) * TILE_BYTES) + (uint64_t)(kk * 2);
-            // the first product into an accumulator overwrites it
-            const bool first_into = (kb == 0 && kk == 0) && (tm == 0 || cfg.td[tm] != cfg.td[tm - 1]);
-            mma_f16(d0 + cfg.td[tm] * BN, ad, bd, cfg.idesc, first_into ? 0u : 1u);
+          const uint64_t a0 = b + kk * 2, a1 = b + R::A1 + kk * 2;
+          const uint64_t b0 = b + R::B0 + kk * 2, b1 = b + R::B1 + kk * 2;
+          const uint32_t fc = ((kb & 1) == 0 && kk == 0) ? 0u : 1u;  // chunk start overwrites D1
+          const uint32_t fi = (kb == 0 && kk == 0) ? 0u : 1u;        // item start overwrites D2, D3
+          if (sub == 0) {
+            mma_f16_cg<CG>(d1, a0, b0, idesc, fc);    // D1 += A1 p1
+            mma_f16_cg<CG>(d2, a0, b1, idesc, fi);    // D2 += A1 p2
+            mma_f16_cg<CG>(d2, a1, b0, idesc, 1u);    // D2 += A2 p1
+            mma_f16_cg<CG>(d3, a1, b1, idesc, fi);    // D3 += A2 p2
+          } else {
+            mma_f16_cg<CG>(d3, a0, b0, idesc, 1u);    // D3 += A1 p3
+            mma_f16_cg<CG>(d3, a1, b1, idesc, 1u);    // D3 += A3 p1
           }
         }
+        st.issued = true;
+        mma_commit_cg<CG>(sa(&S.empty[s]));
       }
-      st.issued = true;
-      mma_commit(sa(&S.empty[s]));  // frees the stage once these MMAs have read it
+      if (kb & 1) {
+        mma_commit_cg<CG>(sa(&S.cfull[slot]));  // this chunk of D1 is ready
+        ++st.cf[slot];
+      }
     }
-    mma_commit(sa(&S.tfull[buf]));  // accumulator ready for the epilogue
-    ++st.uf[buf];
+    mma_commit_cg<CG>(sa(&S.tfull[0]));  // D2, D3 ready for the epilogue(s)
+    ++st.uf[0];
   }
 }
 
@@ -577,24 +600,24 @@ __device__ __forceinline__ void slot_prefetch(const TcArgs& a, const Ctx& x, int
   for (int rr = 0; rr < 2 * a.rt; ++rr) asm volatile("prefetch.global.L1 [%0];" ::"l"(P + (int64_t)rr * a.B_pad));
 }
 
-template <int ph>
+template <int CG, int ph>
 __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;      // 0..255
   const int qd = warp & 3;              // TMEM lane quadrant of this warp
   const int jbase = ((warp - 2) >> 2) * CPW;  // this warp's share of the columns
   const int rloc = qd * 32 + lane;      // row within the tile
-  const int items = phase_items(a, x, ph);
+  const int items = phase_items<CG>(a, x, ph), rpc = a.rt / CG, rank = x.gr % CG, step = x.gs / CG;
   const int np = a.np, hk = a.h_kind;
   const float lam = a.lam;
   const int cb = x.cb;
   // the slot data (and, in phases A and P, the decision) of the next item is
   // loaded into registers while the current item is processed
-  int it = x.gr;
-  while (it < items && !tile_on(a, x, ph, it / a.rt)) it += x.gs;
+  int it = x.gr / CG;
+  while (it < items && !tile_on(a, x, ph, it / rpc)) it += step;
   float pf_tau = 0.f, pf_sc = 1.f;
   int pf_act = 0, pf_qid = 0;
-  if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
+  if (it < items && et < BN) slot_data(a, x, ph, (int64_t)(it / rpc) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
   // One named barrier per item: the shared query data and row sums are
   // double-buffered by item parity ib.  A warp that writes item i + 1's has
   // passed item i's barrier, so every warp has finished reading item i - 1's.
@@ -615,9 +638,9 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     }
   };
   while (it < items) {
-    const int r = it % a.rt, c = it / a.rt;
-    int it_next = it + x.gs;
-    while (it_next < items && !tile_on(a, x, ph, it_next / a.rt)) it_next += x.gs;
+    const int r = CG * (it % rpc) + rank, c = it / rpc;
+    int it_next = it + step;
+    while (it_next < items && !tile_on(a, x, ph, it_next / rpc)) it_next += step;
     const uint32_t buf = st.nb;
     st.nb ^= 1;
     const uint32_t use = st.uf[buf]++;
@@ -640,7 +663,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
       }
       // one lane in 32 asks for each 128-byte line of the next item's slot data
       if (it_next < items && (et & 31) == 0)
-        slot_prefetch(a, x, ph, (int64_t)(it_next / a.rt) * BN + et);
+        slot_prefetch(a, x, ph, (int64_t)(it_next / rpc) * BN + et);
     }
     if (et == 0) S.epi_abort[ib] = S.abort;
     epi_sync();
@@ -854,10 +877,13 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         }
       }
     }
-    // release the accumulator buffer to the MMA warp
+    // release the accumulator buffer to the MMA warp (of the pair's CTA 0)
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(sa(&S.tempty[buf]));
+    if (lane == 0) {
+      if (CG == 1) mbar_arrive(sa(&S.tempty[buf]));
+      else mbar_arrive_rank(sa(&S.tempty[buf]), 0);
+    }
     ++st.ue[buf];
     if constexpr (ph != PH_A) {
       prev_on = et < BN && S.qact[ib][et] == 1;
@@ -866,7 +892,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
       prev_par = ib;
     }
     // the next item's slot data (and decision), from lines asked for above
-    if (et < BN && it_next < items) slot_data(a, x, ph, (int64_t)(it_next / a.rt) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
+    if (et < BN && it_next < items) slot_data(a, x, ph, (int64_t)(it_next / rpc) * BN + et, pf_tau, pf_sc, pf_act, pf_qid);
     it = it_next;
     ib ^= 1;
   }
@@ -878,16 +904,17 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
 
 // The final pass runs once per call: kept out of line so its FP64 registers do
 // not weigh on the per-iteration epilogues.
+template <int CG>
 __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx& x, EpiState& st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int et = threadIdx.x - 64;
   const int qd = warp & 3;
   const int jbase = ((warp - 2) >> 2) * CPW;
   const int rloc = qd * 32 + lane;
-  const int items = phase_items(a, x, PH_F), nk = a.np / BK;
+  const int items = phase_items<CG>(a, x, PH_F), nk = a.np / BK, rpc = a.rt / CG;
   const int np = a.np, hk = a.h_kind;
-  for (int it = x.gr; it < items; it += x.gs) {
-    const int r = it % a.rt, c = it / a.rt;
+  for (int it = x.gr / CG; it < items; it += x.gs / CG) {
+    const int r = CG * (it % rpc) + x.gr % CG, c = it / rpc;
     if (!tile_on(a, x, PH_F, c)) continue;
     epi_sync();
     epi_stage_final(a, S, c, et);
@@ -916,7 +943,10 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(sa(&S.cempty[slot]));
+      if (lane == 0) {
+        if (CG == 1) mbar_arrive(sa(&S.cempty[slot]));
+        else mbar_arrive_rank(sa(&S.cempty[slot]), 0);
+      }
       ++st.ce[slot];
     }
     const uint32_t use = st.uf[0]++;
@@ -978,8 +1008,13 @@ __device__ __noinline__ void epilogue_final(const TcArgs& a, Smem& S, const Ctx&
     tc_fence_before();
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive(sa(&S.tempty[0]));
-      mbar_arrive(sa(&S.tempty[1]));
+      if (CG == 1) {
+        mbar_arrive(sa(&S.tempty[0]));
+        mbar_arrive(sa(&S.tempty[1]));
+      } else {
+        mbar_arrive_rank(sa(&S.tempty[0]), 0);
+        mbar_arrive_rank(sa(&S.tempty[1]), 0);
+      }
     }
     ++st.ue[0];
     ++st.ue[1];
@@ -1141,6 +1176,7 @@ __device__ __noinline__ void prep_final_operand(const TcArgs& a, const Ctx& x) {
 // the instance's barrier words: the whole grid for hopf_eval, a lane of the
 // grid in a ragged batch.  The ring, the TMEM and the role states carry over
 // from one instance to the next.  Returns false when a wait gave up.
+template <int CG>
 __device__ bool solve_instance(const TcArgs& a, Smem& S, uint8_t* stages, ProdState& ps, MmaState& ms, EpiState& es,
                                int gr, int gs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1160,16 +1196,16 @@ __device__ bool solve_instance(const TcArgs& a, Smem& S, uint8_t* stages, ProdSt
     if (warp == 0) {
       if (lane == 0) {
         proxy_fence_global();  // generic-proxy writes of the last phase, then TMA reads
-        producer_phase(a, S, stages, ph, k, cx, ps);
+        producer_phase<CG>(a, S, stages, ph, k, cx, ps);
       }
     } else if (warp == 1) {
-      if (lane == 0) mma_phase(a, S, stages, ph, cx, ms);
+      if (lane == 0) mma_phase<CG>(a, S, stages, ph, cx, ms);
     } else {
-      if (ph == PH_A) epilogue_phase<PH_A>(a, S, k, cx, es);
-      else if (ph == PH_S) epilogue_phase<PH_S>(a, S, k, cx, es);
-      else if (ph == PH_B) epilogue_phase<PH_B>(a, S, k, cx, es);
-      else if (ph == PH_P) epilogue_phase<PH_P>(a, S, k, cx, es);
-      else epilogue_final(a, S, cx, es);
+      if (ph == PH_A) epilogue_phase<CG, PH_A>(a, S, k, cx, es);
+      else if (ph == PH_S) epilogue_phase<CG, PH_S>(a, S, k, cx, es);
+      else if (ph == PH_B) epilogue_phase<CG, PH_B>(a, S, k, cx, es);
+      else if (ph == PH_P) epilogue_phase<CG, PH_P>(a, S, k, cx, es);
+      else epilogue_final<CG>(a, S, cx, es);
       proxy_fence_global();
     }
   };
@@ -1224,80 +1260,103 @@ __device__ bool solve_instance(const TcArgs& a, Smem& S, uint8_t* stages, ProdSt
 }
 
 // Shared memory, mbarriers and TMEM of a solver CTA (set up once per launch).
+// SM pairs: the accumulator-empty barriers of CTA 0 count both CTAs'
+// epilogue warps; the TMEM is allocated by one warp of each CTA together, and
+// neither CTA goes on before the other's barriers exist.
+template <int CG>
 __device__ __forceinline__ Smem& tc_setup(uint8_t*& stages) {
   extern __shared__ uint8_t smem_raw[];
   stages = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Smem& S = *reinterpret_cast<Smem*>(stages + STAGES * STAGE_BYTES);
+  Smem& S = *reinterpret_cast<Smem*>(stages + RING_BYTES);
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < MAX_STAGES; ++s) {
       mbar_init(sa(&S.full[s]), 1);
       mbar_init(sa(&S.empty[s]), 1);
+      mbar_init(sa(&S.pfull[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(sa(&S.tfull[b]), 1);
-      mbar_init(sa(&S.tempty[b]), EPI_WARPS);
+      mbar_init(sa(&S.tempty[b]), EPI_WARPS * CG);
     }
     mbar_init(sa(&S.drain), 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(sa(&S.cfull[b]), 1);
-      mbar_init(sa(&S.cempty[b]), EPI_WARPS);
+      mbar_init(sa(&S.cempty[b]), EPI_WARPS * CG);
     }
     S.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
     tc_fence_before();
   }
   __syncthreads();
+  if constexpr (CG == 2) cluster_sync_all();
   tc_fence_after();
   return S;
 }
 
 // Drain (no copy or MMA of this CTA may be in flight when TMEM is freed) and
-// free the TMEM.
-__device__ __forceinline__ void tc_teardown(Smem& S, const ProdState& ps, const MmaState& ms) {
+// free the TMEM.  SM pairs: CTA 0 commits the drain in both CTAs (its MMAs
+// read CTA 1's shared memory and write its TMEM), and both CTAs pass a
+// cluster barrier before either frees its TMEM or leaves.
+template <int CG>
+__device__ __forceinline__ void tc_teardown(Smem& S, const ProdState& ps, const MmaState& ms, bool lead = true) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0 && lane == 0) {
-    for (int s = 0; s < STAGES; ++s)
+    for (int s = 0; s < MAX_STAGES; ++s)
       if (ps.used[s]) {
         const long long t0 = clock64();
         while (!mbar_test(sa(&S.full[s]), ps.last_par[s]) && clock64() - t0 < (1ll << 31)) {
         }
       }
   }
-  if (warp == 1 && lane == 0 && ms.issued) {
-    mma_commit(sa(&S.drain));
+  if (warp == 1 && lane == 0 && (CG == 2 || ms.issued)) {
+    if (lead) mma_commit_cg<CG>(sa(&S.drain));
     const long long t0 = clock64();
     while (!mbar_test(sa(&S.drain), 0) && clock64() - t0 < (1ll << 31)) {
     }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CG == 2) cluster_sync_all();
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(TMEM_COLS)
-                 : "memory");
+    if constexpr (CG == 1)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(TMEM_COLS)
+                   : "memory");
   }
 }
 
 // Registers: each of the 4 sub-partitions holds 16,384, shared by the warps
 // placed on it (warp w on sub-partition w % 4): 18 warps put 5 on two of them,
 // hence at most 96 per thread; 10 warps allow 168.
+// CG = 2 runs in clusters of two CTAs (consecutive blocks: rank = block & 1).
+template <int CG>
 __global__ void __launch_bounds__(NT, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
   uint8_t* stages;
-  Smem& S = tc_setup(stages);
+  Smem& S = tc_setup<CG>(stages);
   ProdState ps;
-  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
+  for (int s = 0; s < MAX_STAGES; ++s) ps.used[s] = false;
   MmaState ms;
-  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
+  for (int s = 0; s < Ring<CG>::STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * Ring<CG>::STAGE_BYTES));
   EpiState es;
-  solve_instance(a, S, stages, ps, ms, es, blockIdx.x, gridDim.x);
-  tc_teardown(S, ps, ms);
+  solve_instance<CG>(a, S, stages, ps, ms, es, blockIdx.x, gridDim.x);
+  tc_teardown<CG>(S, ps, ms, blockIdx.x % CG == 0);
 }
 
 // ------------------------------------------------------------------- host side
@@ -1318,12 +1377,12 @@ static EncodeTiled encode_fn() {
 }
 
 // 2-D tensor [rows][np] of 16-bit elements, box 128 rows x 64 elements.
-static bool encode(CUtensorMap* m, const void* ptr, int64_t rows, int np, bool bf16) {
+static bool encode(CUtensorMap* m, const void* ptr, int64_t rows, int np, bool bf16, int box_rows = 128) {
   EncodeTiled fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)np * 2};
-  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                   const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1386,7 +1445,7 @@ __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restr
 // counter: 256 queries of a thread-per-query instance, 8 of a warp-per-query
 // one, or one query of a 256-thread one; the group shape is the one hopf_eval
 // picks for the instance's n, so again the results are the same.
-struct alignas(64) RagDense {
+struct alignas(128) RagDense {
   TcArgs a;
   const float* t;     // the caller's t for the instance
   float* tq;          // [B_pad] t by query
@@ -1416,23 +1475,39 @@ __device__ void rag_init(const RagDense& d, int gr, int gs) {
   const int64_t nthr = (int64_t)gs * NT, tid = (int64_t)gr * NT + threadIdx.x;
   const int np = a.np;
   const float lam = a.lam;
-  for (int64_t e = tid; e < a.B_pad * np; e += nthr) {
-    const int64_t q = e / np;
-    const int i = (int)(e - q * np);
-    float v = 0.f;
-    if (q < a.B && i < a.n) v = a.x[q * a.n + i] - a.cf[i];
-    a.y[0][e] = v;
-    a.u[0][e] = v;
-    // the first operand: the FP16 split of y (MIXED; SPLIT with l2), of
-    // r^0 = y + lambda y (SPLIT), or BF16 r^0 (BF16 form)
-    float o = v;
-    if (a.form == FORM_SPLIT && a.h_kind != H_L2) o = v + lam * v;
-    if (a.form != FORM_BF16) {
-      const __half hi = __float2half_rn(o);
-      a.p1[0][e] = __half_as_ushort(hi);
-      a.p2[0][e] = __half_as_ushort(__float2half_rn((o - __half2float(hi)) * kLoScale));
-    } else {
-      a.p1[0][e] = __bfloat16_as_ushort(__float2bfloat16_rn(v + lam * v));
+  // a warp per row, 8 independent loads in flight per lane: with one CTA per
+  // SM there are too few threads to hide the load latency one element at a time
+  constexpr int U = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = (int64_t)gs * (NT / 32), wid = (int64_t)gr * (NT / 32) + (threadIdx.x >> 5);
+  for (int64_t q = wid; q < a.B_pad; q += nwarp) {
+    const float* xr = q < a.B ? a.x + q * a.n : nullptr;
+    for (int i0 = 0; i0 < np; i0 += 32 * U) {
+      float v[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = i0 + j * 32 + lane;
+        v[j] = (xr && i < a.n) ? xr[i] - a.cf[i] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = i0 + j * 32 + lane;
+        if (i >= np) break;
+        const int64_t e = q * np + i;
+        a.y[0][e] = v[j];
+        a.u[0][e] = v[j];
+        // the first operand: the FP16 split of y (MIXED; SPLIT with l2), of
+        // r^0 = y + lambda y (SPLIT), or BF16 r^0 (BF16 form)
+        float o = v[j];
+        if (a.form == FORM_SPLIT && a.h_kind != H_L2) o = v[j] + lam * v[j];
+        if (a.form != FORM_BF16) {
+          const __half hi = __float2half_rn(o);
+          a.p1[0][e] = __half_as_ushort(hi);
+          a.p2[0][e] = __half_as_ushort(__float2half_rn((o - __half2float(hi)) * kLoScale));
+        } else {
+          a.p1[0][e] = __bfloat16_as_ushort(__float2bfloat16_rn(v[j] + lam * v[j]));
+        }
+      }
     }
   }
   for (int64_t q = tid; q < a.B_pad; q += nthr) {
@@ -1523,11 +1598,11 @@ __device__ void rag_diag_loop(const RaggedArgs& r) {
 
 __global__ void __launch_bounds__(NT, 1) k_ragged(const __grid_constant__ RaggedArgs r) {
   uint8_t* stages;
-  Smem& S = tc_setup(stages);
+  Smem& S = tc_setup<1>(stages);
   ProdState ps;
-  for (int s = 0; s < STAGES; ++s) ps.used[s] = false;
+  for (int s = 0; s < MAX_STAGES; ++s) ps.used[s] = false;
   MmaState ms;
-  for (int s = 0; s < STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * STAGE_BYTES));
+  for (int s = 0; s < Ring<1>::STAGES; ++s) ms.sdesc[s] = smem_desc(sa(stages + (size_t)s * Ring<1>::STAGE_BYTES));
   EpiState es;
   bool alive = true;
   for (int e = r.sched_off[blockIdx.x]; e < r.sched_off[blockIdx.x + 1]; ++e) {
@@ -1537,14 +1612,14 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(const __grid_constant__ Ragged
     if (!alive && threadIdx.x == 0) atomicExch(a.err, ERR_MBAR_TIMEOUT);
     rag_init(d, w.y, w.z);
     bool ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
-    if (ok) ok = solve_instance(a, S, stages, ps, ms, es, w.y, w.z);
+    if (ok) ok = solve_instance<1>(a, S, stages, ps, ms, es, w.y, w.z);
     if (ok) ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
     else __syncthreads();
     rag_finalize(d, w.y, w.z);
     if (S.abort) alive = false;
   }
   if (threadIdx.x < 256) rag_diag_loop(r);
-  tc_teardown(S, ps, ms);
+  tc_teardown<1>(S, ps, ms);
 }
 }  // namespace tc
 
@@ -1561,7 +1636,7 @@ bool tc_encode_f16(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols) 
 }
 
 
-size_t tc_smem_bytes() { return 1024 + (size_t)tc::STAGES * tc::STAGE_BYTES + sizeof(tc::Smem); }
+size_t tc_smem_bytes() { return 1024 + (size_t)tc::RING_BYTES + sizeof(tc::Smem); }
 
 // Raise the kernel's dynamic shared memory limit once (at handle creation, so
 // that later evaluations stay capturable in a CUDA graph).
@@ -1570,29 +1645,33 @@ hopf_status dense_tc_prepare() {
   int dev = 0;
   HOPF_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 256 && !done[dev]) {
-    HOPF_CUDA(cudaFuncSetAttribute(tc::k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+    HOPF_CUDA(cudaFuncSetAttribute(tc::k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+    HOPF_CUDA(cudaFuncSetAttribute(tc::k_dense_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
     done[dev] = true;
   }
   return HOPF_OK;
 }
 
+// cg: CTAs per MMA (the B operand maps copy 128 / cg query rows per tile).
 static hopf_status build_tc_args(hopf_handle h, DenseWs& w, const float* x, float* grad, float* beta, float* xfin,
-                                 int form, tc::TcArgs* out) {
+                                 int form, int cg, tc::TcArgs* out) {
   using namespace tc;
   TcArgs& a = *out;
   memset(&a, 0, sizeof(a));
   const int np = h->n_pad;
+  const int bh = BN / cg;
   bool ok = encode(&a.mAh, h->d_Ah16, np, np, false) && encode(&a.mAl, h->d_Al16, np, np, false) &&
-            encode(&a.mAl2, h->d_Al2, np, np, false) && encode(&a.mP3, w.g, w.B_pad, np, false) &&
+            encode(&a.mAl2, h->d_Al2, np, np, false) && encode(&a.mP3, w.g, w.B_pad, np, false, bh) &&
             encode(&a.mM, h->d_Mbf, np, np, true) &&
-            encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16) && encode(&a.mP2, w.pl, w.B_pad, np, false) &&
-            encode(&a.mP1b, w.ph_b, w.B_pad, np, false) && encode(&a.mP2b, w.pl_b, w.B_pad, np, false) &&
-            encode(&a.mG, w.g, w.B_pad, np, true) && encode_f32(&a.mU[0], w.u, w.B_pad, np) &&
+            encode(&a.mP1, w.ph, w.B_pad, np, form == FORM_BF16, bh) &&
+            encode(&a.mP2, w.pl, w.B_pad, np, false, bh) && encode(&a.mP1b, w.ph_b, w.B_pad, np, false, bh) &&
+            encode(&a.mP2b, w.pl_b, w.B_pad, np, false, bh) && encode(&a.mG, w.g, w.B_pad, np, true, bh) &&
+            encode_f32(&a.mU[0], w.u, w.B_pad, np) &&
             encode_f32(&a.mU[1], form != FORM_BF16 ? w.u_b : w.u, w.B_pad, np);
   if (ok && form == FORM_SPLIT)
     ok = encode(&a.mMh, h->d_Mh16, np, np, false) && encode(&a.mMl, h->d_Ml16, np, np, false) &&
-         encode(&a.mQ1[0], w.qh, w.B_pad, np, false) && encode(&a.mQ2[0], w.ql, w.B_pad, np, false) &&
-         encode(&a.mQ1[1], w.qh_b, w.B_pad, np, false) && encode(&a.mQ2[1], w.ql_b, w.B_pad, np, false);
+         encode(&a.mQ1[0], w.qh, w.B_pad, np, false, bh) && encode(&a.mQ2[0], w.ql, w.B_pad, np, false, bh) &&
+         encode(&a.mQ1[1], w.qh_b, w.B_pad, np, false, bh) && encode(&a.mQ2[1], w.ql_b, w.B_pad, np, false, bh);
   if (!ok) return fail(HOPF_ECUDA, "cuTensorMapEncodeTiled failed");
   a.y[0] = w.y;
   a.y[1] = w.y_b;
@@ -1664,23 +1743,62 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
   k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda, h->h_kind);
   HOPF_CUDA(cudaGetLastError());
 
+  // one CTA per SM (each holds all 512 TMEM columns), and no more CTAs than
+  // tiles: small problems leave the other SMs to concurrent work.  SM pairs
+  // (an even number of 128-row tiles, and room for at least two CTAs) halve
+  // the B operand each CTA brings in per MMA.
+  const int rt = h->n_pad / BM;
+  const int64_t tiles = (int64_t)rt * (w.B_pad / BN);
+  const int sms = h->grid_cap > 0 && h->grid_cap < h->num_sms ? h->grid_cap : h->num_sms;
+  const int cg = h->tc_pairs && rt % 2 == 0 && sms >= 2 && tiles >= 2 ? 2 : 1;
   TcArgs a;
-  s = build_tc_args(h, w, x, grad, beta, xfin, form, &a);
+  s = build_tc_args(h, w, x, grad, beta, xfin, form, cg, &a);
   if (s != HOPF_OK) return s;
-  const int np = h->n_pad;
 
   const size_t smem = tc_smem_bytes();
-  int per_sm = 0;
-  HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc, NT, smem));
-  if (per_sm < 1) return fail(HOPF_ECUDA, "dense tensor-core solver: kernel does not fit on an SM");
-  // one CTA per SM (each holds all 512 TMEM columns), and no more CTAs than
-  // tiles: small problems leave the other SMs to concurrent work
-  const int tiles = a.rt * a.ct;
-  const int sms = h->grid_cap > 0 && h->grid_cap < h->num_sms ? h->grid_cap : h->num_sms;
-  const int grid = tiles < sms ? (tiles > 0 ? tiles : 1) : sms;
-  void* args[] = {&a};
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = cg;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  int grid = (int)(tiles < sms ? (tiles > 0 ? tiles : 1) : sms);
+  if (cg == 1) {
+    int per_sm = 0;
+    HOPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc<1>, NT, smem));
+    if (per_sm < 1) return fail(HOPF_ECUDA, "dense tensor-core solver: kernel does not fit on an SM");
+  } else {
+    // whole clusters of two, as many as fit at once (the grid barrier needs
+    // every CTA resident)
+    static int max_pairs[256] = {};
+    int dev = 0;
+    HOPF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(HOPF_ECUDA, "dense tensor-core solver: device index");
+    if (max_pairs[dev] == 0) {
+      cfg.gridDim = dim3(2 * (h->num_sms / 2));
+      cfg.numAttrs = 1;  // the occupancy query takes the cluster shape alone
+      cfg.attrs = at + 1;
+      int n = 0;
+      HOPF_CUDA(cudaOccupancyMaxActiveClusters(&n, (const void*)k_dense_tc<2>, &cfg));
+      cfg.attrs = at;
+      cfg.numAttrs = 2;
+      max_pairs[dev] = n > 0 ? n : -1;
+    }
+    if (max_pairs[dev] < 0) return fail(HOPF_ECUDA, "dense tensor-core solver: no SM pair fits");
+    grid = grid / 2 < max_pairs[dev] ? grid / 2 : max_pairs[dev];
+    grid = 2 * (grid > 0 ? grid : 1);
+  }
+  cfg.gridDim = dim3(grid);
   if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
-  HOPF_CUDA(cudaLaunchCooperativeKernel((const void*)k_dense_tc, dim3(grid), dim3(NT), args, smem, stream));
+  if (cg == 2) HOPF_CUDA(cudaLaunchKernelEx(&cfg, k_dense_tc<2>, a));
+  else HOPF_CUDA(cudaLaunchKernelEx(&cfg, k_dense_tc<1>, a));
   if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
   return dense_finalize(h, w, phi, dphidt, iters, qstatus, stream);
 }
@@ -1696,7 +1814,7 @@ hopf_status ragged_build_dense(hopf_handle h, DenseWs& w, const float* x, const 
   if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
     return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
   RagDense* d = new (rec) RagDense();
-  hopf_status s = build_tc_args(h, w, x, grad, nullptr, nullptr, form, &d->a);
+  hopf_status s = build_tc_args(h, w, x, grad, nullptr, nullptr, form, 1, &d->a);
   if (s != HOPF_OK) return s;
   d->t = t;
   d->tq = w.tq;

@@ -162,6 +162,13 @@ hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles) {
   return HOPF_OK;
 }
 
+hopf_status hopf_set_tc_pairs(hopf_handle h, int32_t on) {
+  set_error("");
+  if (!h) return fail(HOPF_EINVAL, "hopf_set_tc_pairs: null handle");
+  h->tc_pairs = on ? 1 : 0;
+  return HOPF_OK;
+}
+
 hopf_status hopf_set_allocator(hopf_alloc_fn alloc, hopf_free_fn release, void* ctx) {
   set_error("");
   return set_allocator(alloc, release, ctx);

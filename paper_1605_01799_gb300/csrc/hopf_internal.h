@@ -55,6 +55,7 @@ struct hopf_handle_s {
   cudaEvent_t prof_start = nullptr, prof_stop = nullptr;  // optional instrumentation
   int compact = 1;  // tensor-core path: pack active queries as others converge
   long long wait_limit = 0;  // clock cycles of the dense solvers' bounded waits (0: the default)
+  int tc_pairs = 0;  // tensor-core path: SM pairs (cta_group::2) when the row tiles pair up (off: measured slower)
   Allocator alloc = {nullptr, nullptr, nullptr};  // the allocator this handle's memory came from
 };
 

@@ -90,6 +90,56 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+// ---- SM pairs (cta_group::2): one MMA over two CTAs of a cluster of two.
+// The pair's M = 256 rows are the two CTAs' 128-row A tiles (at the same
+// shared-memory offset in each), B's N columns are split in halves between
+// them, and each CTA's TMEM receives its own 128 rows of D.  One thread of
+// the even CTA issues; commits arrive on the mbarrier at the same offset in
+// both CTAs.
+template <int CG>
+__device__ __forceinline__ void mma_f16_cg(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (CG == 1) {
+    mma_f16(d, a, b, idesc, acc);
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+template <int CG>
+__device__ __forceinline__ void mma_commit_cg(uint32_t bar) {
+  if constexpr (CG == 1) {
+    mma_commit(bar);
+  } else {
+    const uint16_t both = 3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(both)
+        : "memory");
+  }
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs of the cluster (reached unconditionally).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Arrive on the mbarrier at the same offset in CTA `rank` of the cluster.
+// Default (CTA-scope) release: what the arrival publishes is ordered by the
+// tcgen05 fence before it (TMEM reads done) or is a completed TMA copy; a
+// cluster-scope release would also hold the thread until its own global
+// stores were visible.
+__device__ __forceinline__ void mbar_arrive_rank(uint32_t bar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(rank));
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 

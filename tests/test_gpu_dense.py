@@ -201,6 +201,56 @@ def test_compaction_does_not_change_results(hg, orc, precision, h_kind):
     assert (np.abs(phi - ref["phi"]) / np.maximum(1, np.abs(ref["phi"]))).max() <= PHI_TOL
 
 
+@pytest.mark.parametrize("precision,h_kind,n", [("MIXED", 1, 256), ("MIXED", 0, 512), ("SPLIT", 1, 256),
+                                                ("SPLIT", 2, 512), ("BF16", 1, 256)])
+def test_sm_pairs_match_single_ctas(hg, orc, precision, h_kind, n):
+    """An SM pair (two CTAs, one M = 256 MMA per K step over both CTAs' A
+    tiles and the two halves of the query tile) forms every product from the
+    same operands in the same K order as two CTAs with one 128-row tile each:
+    the outputs agree bit for bit, through compactions and the final pass.
+    The row-tile count is even here (2 or 4); with an odd count (n = 384)
+    the pair switch keeps single CTAs (test_sm_pairs_odd_row_tiles)."""
+    import torch
+    B = 2000
+    A, Q, s = wl.spd_matrix(11811 + n, 11812 + n, n)
+    w = wl.uniform(11813, n, 0.5, 1.5)
+    x = wl.normal(11814, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(11815, B, 0.1, 3.0).astype(np.float32)
+    t[::7] = 0.0
+    wk = w if h_kind == 1 else None
+    outs = []
+    for pairs in (True, False):
+        h = hg.Hopf(A, h_kind, w=wk, tol=TOL if precision != "BF16" else 1e-6, max_iter=3000,
+                    precision=getattr(hg, "P_" + precision))
+        h.set_tc_pairs(pairs)
+        outs.append(h.eval(_cuda(x), _cuda(t)))
+    torch.cuda.synchronize()
+    for key in ("phi", "grad", "iters", "status", "dphidt"):
+        assert torch.equal(outs[0][key], outs[1][key]), key
+    if precision == "BF16":
+        return
+    ref = orc.Problem(A, h_kind, w=wk, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
+        x[:64].astype(np.float64), t[:64].astype(np.float64))
+    ephi, eg = _errors({k: v[:64] for k, v in outs[0].items()}, ref)
+    gmax, _ = GRAD_BARS[precision]
+    assert ephi.max() <= PHI_TOL and eg.max() <= gmax, (ephi.max(), eg.max())
+
+
+def test_sm_pairs_odd_row_tiles(hg, orc):
+    """Pairs switched on for n = 384 (three 128-row tiles, which do not pair
+    up) and for n = 200 with one query (two row tiles, one column tile: the
+    smallest pair grid): results within the oracle bars."""
+    import torch
+    for n, B, h_kind in ((384, 257, 0), (200, 1, 1)):
+        A, w, x, t, ref = _case(orc, n, B, h_kind, 11000 + n + h_kind)
+        h = hg.Hopf(A, h_kind, w=w, tol=TOL, max_iter=3000, precision=hg.P_MIXED)
+        h.set_tc_pairs(True)
+        out = h.eval(_cuda(x), _cuda(t))
+        torch.cuda.synchronize()
+        ephi, eg = _errors(out, ref)
+        assert ephi.max() <= PHI_TOL and eg.max() <= GRAD_MAX, (n, ephi.max(), eg.max())
+
+
 def test_batch_beyond_the_compaction_table(hg, orc):
     """More column tiles (1,094 for 140,000 queries) than the shared-memory
     table of packing offsets holds (1,024): the solver runs without packing
