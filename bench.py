@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-arms", action="store_true", help="time the chosen form only (no FP32 / SPLIT arms)")
+    p.add_argument("--split-start", type=float, default=-1.0,
+                   help="MIXED form: SPLIT iterations down to this squared relative change first "
+                        "(-1: the library default, ten times the tolerance; 0: off)")
     p.add_argument("--tc-pairs", type=int, default=0, choices=[0, 1],
                    help="dense tensor-core forms: SM pairs (cta_group::2) on (1) or off (0, the default)")
     p.add_argument("--ragged-mode", type=int, default=0, choices=[0, 1, 2],
@@ -1131,6 +1134,8 @@ def main():
         workload; the solver kernel alone is timed by the handle's events."""
         h = hg.Hopf(A, hg.H_WL1, w=w, tol=tol, max_iter=MAX_ITER, precision=PREC[variant])
         h.set_tc_pairs(args.tc_pairs)
+        if variant == "mixed" and args.split_start >= 0:
+            h.set_split_start(args.split_start)
         wsbuf = h.workspace(B)
         out = None
         for _ in range(warmup):
@@ -1171,6 +1176,8 @@ def main():
 
     # the headline: the MIXED tensor-core form, clocks sampled while it runs
     main_variant = args.variant
+    # the two-stage MIXED solve's switch (the library's default: ten times the tolerance)
+    split_start = (args.split_start if args.split_start >= 0 else 10.0 * tol) if main_variant == "mixed" else 0.0
     hd = arm(main_variant, args.steps, args.warmup, clocks_too=True)
     h, wsbuf, out, ms, kern_ms, clocks = hd["h"], hd["ws"], hd["out"], hd["ms"], hd["kern_ms"], hd["clocks"]
     K, status = hd["iters"], hd["status"]
@@ -1212,6 +1219,7 @@ def main():
     def roofline(variant, K_, kms):
         form = {"mixed": "mixed", "split": "split", "fp32": "fp32", "bf16": "bf16"}[variant]
         flops, f_exec = dense_work(n, K_, form)
+        staged = variant == "mixed" and split_start != 0
         if variant == "fp32":
             peak = fp32_peak
             r = {"bound": "alu", "peak_source": "FP32 FMA chains measured in-process (hopf_measure_pipes)"}
@@ -1224,6 +1232,13 @@ def main():
                   "kernel_ms": kms, "algorithmic_flops_per_launch": flops,
                   "algorithmic_flops_per_query": "2 n^2 (K_q + 2)",
                   "executed_flops_per_launch": f_exec, "executed": executed, "executed_frac": executed / peak})
+        if staged:
+            # SPLIT iterations (3 MMA passes) then MIXED ones (4): the split of
+            # K_q between the stages is not reported, so give the range
+            f_lo = dense_work(n, K_, "split")[1]
+            r.update({"executed_flops_per_launch": None, "executed": None, "executed_frac": None,
+                      "executed_frac_range": [f_lo / (kms * 1e-3) / 1e12 / peak, executed / peak],
+                      "kernel_ms_covers": "both stages of the two-stage MIXED solve and the set-up between"})
         return r
 
     roof = roofline(main_variant, K, kern_ms)
@@ -1280,6 +1295,7 @@ def main():
                 "config": {"workload": "dense_wl1_n%d_b%d" % (n, B), "n": n, "batch_per_gpu": B,
                            "variant": main_variant, "tol_urel": tol, "max_iter": MAX_ITER,
                            "sm_pairs": bool(args.tc_pairs),
+                           "split_start": split_start,
                            "parallelism": "replicas" if ws == 1 else "dp%d (independent query shards)" % ws,
                            "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
                 "iters": {"mean": float(K.mean()), "max": int(K.max()), "min": int(K.min())},

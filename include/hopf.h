@@ -89,9 +89,14 @@ enum { HOPF_H_L1 = 0, HOPF_H_WL1 = 1, HOPF_H_L2 = 2, HOPF_H_LINF = 3, HOPF_H_DNO
  *          g = y - A p - lambda (u - p), A p from a two-term FP16 split with
  *          an exactly scaled correction accumulator, M g in BF16.  Its fixed
  *          point depends only on the accuracy of g: FP32-class results, two
- *          phases (four MMAs) per iteration.
- * SPLIT and MIXED reach the same accuracy at the same tolerance; SPLIT does
- * three n x n MMA passes per iteration where MIXED does four.
+ *          phases (four MMAs) per iteration.  With H = l1 or weighted l1 it
+ *          starts with SPLIT iterations (hopf_set_split_start).
+ * SPLIT does three n x n MMA passes per iteration in one phase, MIXED four in
+ * two.  The tensor cores' FP32 accumulation truncates; in SPLIT that error
+ * reaches the fixed point amplified by |A + lambda I|, in MIXED it enters
+ * through g alone, so at the same tolerance SPLIT's gradient is a few times
+ * less accurate (about 1e-5 against 3e-6 relative for a condition number of
+ * 100 at n = 1024).
  */
 enum { HOPF_P_FP64 = 0, HOPF_P_FP32 = 1, HOPF_P_BF16 = 2, HOPF_P_SPLIT = 4, HOPF_P_MIXED = 5 };
 
@@ -380,6 +385,23 @@ hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles);
  * next evaluation; ragged batches always use single CTAs.  (The paper has no
  * counterpart.) */
 hopf_status hopf_set_tc_pairs(hopf_handle h, int32_t on);
+
+/* HOPF_P_MIXED with H = l1 or weighted l1 solves in two stages: the
+ * HOPF_P_SPLIT iteration (one tensor-core phase per iteration) until each
+ * query's squared relative change |u^k - u^{k-1}|^2 / max(1, |u^k|^2) is at
+ * most tol_switch, then the defect correction (two phases per iteration) from
+ * where that query stopped until the handle's tolerance.  The defect
+ * correction's fixed point (g = 0) does not depend on its start, so the
+ * results keep the MIXED form's accuracy; the second stage corrects the
+ * SPLIT fixed point's bias.  Reported iterations count both stages, and
+ * max_iter caps their sum.  tol_switch = 0 runs the defect correction alone;
+ * the default is ten times the handle's tolerance.  A workspace must be sized
+ * (hopf_workspace_size) after the last call: the first stage needs the SPLIT
+ * form's operand planes.  Ragged batches run the defect correction alone.
+ * Errors: HOPF_EINVAL for a null handle or a negative or non-finite
+ * tol_switch; HOPF_EUNSUPPORTED for tol_switch > 0 with another precision or
+ * H.  (The switch is this library's; the paper's iteration is unchanged.) */
+hopf_status hopf_set_split_start(hopf_handle h, double tol_switch);
 
 /* Device allocator for the memory hopf_create and hopf_batch_create keep (the
  * handle's copies of A, M and the weights, and their set-up scratch).

@@ -33,7 +33,7 @@ EXPORTS = ["hopf_create", "hopf_destroy", "hopf_workspace_size", "hopf_eval", "h
            "hopf_profile_events", "hopf_set_compaction", "hopf_batch_create", "hopf_batch_destroy",
            "hopf_batch_workspace_size", "hopf_batch_eval", "hopf_batch_info", "hopf_batch_set_mode",
            "hopf_eval_control", "hopf_maxH_eval",
-           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_tc_pairs",
+           "hopf_measure_pipes_scratch", "hopf_measure_pipes", "hopf_set_wait_limit", "hopf_set_tc_pairs", "hopf_set_split_start",
            "hopf_set_allocator", "hopf_last_error", "hopf_version"]
 
 
@@ -90,6 +90,7 @@ def lib():
             "hopf_maxH_eval": ([_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
             "hopf_set_wait_limit": ([_vp, _i64], ctypes.c_int),
             "hopf_set_tc_pairs": ([_vp, ctypes.c_int32], ctypes.c_int),
+            "hopf_set_split_start": ([_vp, ctypes.c_double], ctypes.c_int),
             "hopf_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
             "hopf_measure_pipes_scratch": ([], _sz),
             "hopf_measure_pipes": ([_vp, _sz, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -244,6 +245,12 @@ class Hopf:
     def set_wait_limit(self, cycles):
         """Clock-cycle limit of the dense solvers' bounded waits (0: default)."""
         _check(lib().hopf_set_wait_limit(self.handle, int(cycles)))
+
+    def set_split_start(self, tol_switch):
+        """MIXED form (l1, weighted l1): SPLIT iterations until each query's
+        squared relative change is within tol_switch, then the defect
+        correction to the tolerance; 0 runs the defect correction alone."""
+        _check(lib().hopf_set_split_start(self.handle, float(tol_switch)))
 
     def set_tc_pairs(self, on):
         """Dense tensor-core path: SM pairs (cta_group::2) on or off."""

@@ -384,6 +384,7 @@ hopf_status batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out,
       free_batch(b);
       return fail(st, msg);
     }
+    h->split_start = 0.0;  // the persistent schedule runs the one-stage MIXED form; both schedules agree
     b->inst.push_back(h);
   }
 #define B_CALL(call)                     \

@@ -6,10 +6,17 @@
 //   the whole split Bregman state after the first step.  The start
 //   v^0 = d^0 = y, b^0 = 0 (Section 3.1) is u^0 = d^0 = y with the first step
 //   taking p^0 = y instead of prox(u^0).
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "hopf_internal.h"
 
 namespace hopf {
+
+// The MIXED form starts with SPLIT iterations (l1 and weighted l1).
+bool two_stage(const hopf_handle h) {
+  return h->precision == HOPF_P_MIXED && h->split_start > 0.0 && h->h_kind != HOPF_H_L2;
+}
 
 static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 */) {
   const int64_t B_pad = round_up(batch > 0 ? batch : 1, 256);
@@ -43,10 +50,11 @@ static size_t carve_sizes(const hopf_handle h, int64_t batch, size_t* out /* 32 
   s[23] = tc ? B_pad * np * 4 : 0;       // ufin
   s[24] = B_pad * 4;                     // sfin
   s[25] = 2 * B_pad * 4;                 // taus
-  const bool split = h->precision == HOPF_P_SPLIT;
+  const bool split = h->precision == HOPF_P_SPLIT || two_stage(h);
   for (int i = 26; i < 30; ++i) s[i] = split ? B_pad * np * 2 : 0;  // qh, ql, qh_b, ql_b
+  s[30] = tc ? B_pad * 4 : 0;            // qiter0 (two-stage solve: iterations of the first stage)
   size_t total = 0;
-  for (int i = 0; i < 30; ++i) {
+  for (int i = 0; i < 31; ++i) {
     if (out) out[i] = total;
     total += round_up(s[i], 256);
   }
@@ -90,11 +98,12 @@ hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_
   d->ufin = tc ? (float*)(p + off[23]) : nullptr;
   d->sfin = (float*)(p + off[24]);
   d->taus = (float*)(p + off[25]);
-  const bool split = h->precision == HOPF_P_SPLIT;
+  const bool split = h->precision == HOPF_P_SPLIT || two_stage(h);
   d->qh = split ? (uint16_t*)(p + off[26]) : nullptr;
   d->ql = split ? (uint16_t*)(p + off[27]) : nullptr;
   d->qh_b = split ? (uint16_t*)(p + off[28]) : nullptr;
   d->ql_b = split ? (uint16_t*)(p + off[29]) : nullptr;
+  d->qiter0 = tc ? (int*)(p + off[30]) : nullptr;
   return HOPF_OK;
 }
 
@@ -122,6 +131,60 @@ __global__ void k_dense_init(const float* __restrict__ x, const float* __restric
     qdone[q] = q < B ? 0 : 1;
     sq[q] = (int)q;  // slot q starts with query q
   }
+}
+
+// Second stage of the two-stage solve: every slot plane is rebuilt from the
+// query-indexed results of the first (whose compactions moved the slots):
+// y = x - c, u = the query's last u, the operand planes the FP16 split of
+// p = prox(u) (l1 and weighted l1 shrink by (t / lambda) w), slot q holding
+// query q.  The first stage's iteration count moves to qiter0; a query it
+// stopped at max_iter stays stopped (qdone 2, its count kept).
+__global__ void k_dense_init_warm(const float* __restrict__ x, const float* __restrict__ t,
+                                  const float* __restrict__ c, const float* __restrict__ wt,
+                                  const float* __restrict__ ufin, int n, int np, int64_t B, int64_t B_pad, float lam,
+                                  int max_iter, float* __restrict__ y, float* __restrict__ u, uint16_t* __restrict__ ph,
+                                  uint16_t* __restrict__ pl, float* __restrict__ tau, float* __restrict__ tq,
+                                  int* __restrict__ qiter, int* __restrict__ qiter0, int* __restrict__ qdone,
+                                  int* __restrict__ sq, float* __restrict__ taus) {
+  const int64_t q = blockIdx.x;  // one CTA per query
+  if (q >= B_pad) return;
+  const float tt = q < B ? t[q] : 0.f;
+  const float tl = tt / lam;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    float yv = 0.f, uv = 0.f;
+    if (q < B && i < n) {
+      yv = x[q * n + i] - c[i];
+      uv = ufin[q * np + i];
+    }
+    const float pv = shrink1(uv, tl * wt[i]);
+    const __half hi = __float2half_rn(pv);
+    y[q * np + i] = yv;
+    u[q * np + i] = uv;
+    ph[q * np + i] = __half_as_ushort(hi);
+    pl[q * np + i] = __half_as_ushort(__float2half_rn((pv - __half2float(hi)) * 2048.f));
+  }
+  if (threadIdx.x == 0) {
+    const int k1 = q < B ? qiter[q] : 0;
+    const bool capped = q < B && k1 >= max_iter;
+    tq[q] = tt;
+    tau[q] = tl;
+    taus[q] = tl;
+    qiter0[q] = k1;
+    qiter[q] = capped ? k1 : 0;
+    qdone[q] = q >= B ? 1 : capped ? 2 : 0;
+    sq[q] = (int)q;
+  }
+}
+
+hopf_status dense_init_warm(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s) {
+  // the error word carries over: a first stage that gave up aborts the second
+  HOPF_CUDA(cudaMemsetAsync(w.bar, 0, 64, s));
+  HOPF_CUDA(cudaMemsetAsync(w.tile_act, 0, (size_t)2 * (w.B_pad / 128) * 4, s));
+  k_dense_init_warm<<<(unsigned)w.B_pad, 256, 0, s>>>(x, t, h->d_cf, h->d_wf, w.ufin, h->n, h->n_pad, w.B, w.B_pad,
+                                                      (float)h->lambda, h->max_iter, w.y, w.u, w.ph, w.pl, w.tau,
+                                                      w.tq, w.qiter, w.qiter0, w.qdone, w.sq, w.taus);
+  HOPF_CUDA(cudaGetLastError());
+  return HOPF_OK;
 }
 
 hopf_status dense_init(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s) {

@@ -64,6 +64,7 @@
 namespace hopf {
 
 hopf_status dense_init(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s);
+hopf_status dense_init_warm(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s);
 hopf_status dense_finalize(hopf_handle h, DenseWs& w, double* phi, float* dphidt, int32_t* iters, uint8_t* qstatus,
                            cudaStream_t s);
 
@@ -141,6 +142,13 @@ struct TcArgs {
   int n, np, rt, ct, h_kind, max_iter, form, compact;
   float lam, tol;
   long long wait_limit;  // clock cycles of every bounded wait
+  // Two-stage solve (SPLIT iterations, then MIXED from where each query left
+  // off): the first stage skips the final pass (no_final); the second starts
+  // warm (u from that stage, no first-iteration rule, a stop allowed from the
+  // first decision) and counts on from iter_base[q] iterations (also against
+  // max_iter).  Both zero / null for a one-stage solve.
+  int warm, no_final;
+  const int* iter_base;
 };
 
 // Per-CTA view of the slot layout; every CTA updates it identically.
@@ -553,7 +561,8 @@ __device__ __forceinline__ void slot_data(const TcArgs& a, const Ctx& x, int ph,
     return;
   }
   if (x.k == 1) {
-    act = qid < a.B ? 1 : 0;
+    // a warm start leaves out the queries the first stage stopped at max_iter
+    act = qid < a.B && (!a.warm || a.qdone[qid] == 0) ? 1 : 0;
     return;
   }
   // every load issued before any is used (one memory latency)
@@ -580,8 +589,9 @@ __device__ __forceinline__ void slot_data(const TcArgs& a, const Ctx& x, int ph,
   if (prev != 1) return;
   sc = shrink2_scale(sqrtf(nu2), tau);
   const int kprev = x.k - 1;
-  if (kprev >= 2 && du2 <= a.tol * fmaxf(1.f, nu2)) act = 2;
-  else if (kprev >= a.max_iter) act = 3;
+  const int done_before = a.iter_base ? a.iter_base[qid] : 0;
+  if (kprev >= 2 - a.warm && du2 <= a.tol * fmaxf(1.f, nu2)) act = 2;
+  else if (kprev + done_before >= a.max_iter) act = 3;
   else act = 1;
 }
 
@@ -655,7 +665,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
         a.qact[cb][x.par][sl] = pf_act >= 2 ? 2 : pf_act;
         if (pf_act >= 2) {
           a.qdone[pf_qid] = pf_act == 2 ? 1 : 2;
-          a.qiter[pf_qid] = pf_act == 2 ? k - 1 : a.max_iter;
+          a.qiter[pf_qid] = pf_act == 2 ? k - 1 + (a.iter_base ? a.iter_base[pf_qid] : 0) : a.max_iter;
           a.sfin[pf_qid] = pf_sc;
         }
         const int cnt = __reduce_add_sync(0xffffffffu, pf_act == 1 ? 1 : 0);
@@ -682,7 +692,7 @@ __device__ void epilogue_phase(const TcArgs& a, Smem& S, int k, const Ctx& x, Ep
     const int row = r * BM + rloc;
     const float wr = a.w[row];
     const uint32_t tbase = S.tmem_base + ((uint32_t)(qd * 32) << 16) + buf * 256;
-    const bool first = k == 1;
+    const bool first = k == 1 && !a.warm;
     // The state a chunk reads from global memory does not depend on this
     // item's products: the first chunk's loads go out before the wait for
     // the accumulator, each later chunk's when its predecessor is done.
@@ -1250,12 +1260,12 @@ __device__ bool solve_instance(const TcArgs& a, Smem& S, uint8_t* stages, ProdSt
       cx.fresh = 0;
     }
   }
-  if (ok) {
+  if (ok && !a.no_final) {
     if (warp >= 2) prep_final_operand(a, cx);
     proxy_fence_global();
     ok = grid_barrier(a.bar, gs, a.err, a.wait_limit);
+    if (ok) run(PH_F, 0);
   }
-  if (ok) run(PH_F, 0);
   return ok;
 }
 
@@ -1730,31 +1740,11 @@ static hopf_status build_tc_args(hopf_handle h, DenseWs& w, const float* x, floa
   return HOPF_OK;
 }
 
-hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
-                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
-                          float* xfin) {
+// One launch of the persistent solver for the arguments a (built for cg CTAs
+// per MMA), on one CTA per SM and no more CTAs than tiles: small problems
+// leave the other SMs to concurrent work.
+static hopf_status launch_tc(hopf_handle h, const tc::TcArgs& a, int cg, int64_t tiles, int sms, cudaStream_t stream) {
   using namespace tc;
-  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
-  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
-    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
-  hopf_status s = dense_init(h, w, x, t, stream);
-  if (s != HOPF_OK) return s;
-  const int64_t total = w.B_pad * h->n_pad;
-  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form, (float)h->lambda, h->h_kind);
-  HOPF_CUDA(cudaGetLastError());
-
-  // one CTA per SM (each holds all 512 TMEM columns), and no more CTAs than
-  // tiles: small problems leave the other SMs to concurrent work.  SM pairs
-  // (an even number of 128-row tiles, and room for at least two CTAs) halve
-  // the B operand each CTA brings in per MMA.
-  const int rt = h->n_pad / BM;
-  const int64_t tiles = (int64_t)rt * (w.B_pad / BN);
-  const int sms = h->grid_cap > 0 && h->grid_cap < h->num_sms ? h->grid_cap : h->num_sms;
-  const int cg = h->tc_pairs && rt % 2 == 0 && sms >= 2 && tiles >= 2 ? 2 : 1;
-  TcArgs a;
-  s = build_tc_args(h, w, x, grad, beta, xfin, form, cg, &a);
-  if (s != HOPF_OK) return s;
-
   const size_t smem = tc_smem_bytes();
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[2];
@@ -1796,9 +1786,55 @@ hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float
     grid = 2 * (grid > 0 ? grid : 1);
   }
   cfg.gridDim = dim3(grid);
-  if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
   if (cg == 2) HOPF_CUDA(cudaLaunchKernelEx(&cfg, k_dense_tc<2>, a));
   else HOPF_CUDA(cudaLaunchKernelEx(&cfg, k_dense_tc<1>, a));
+  return HOPF_OK;
+}
+
+hopf_status dense_eval_tc(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
+                          float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta,
+                          float* xfin) {
+  using namespace tc;
+  const int form = h->precision == HOPF_P_MIXED ? FORM_MIXED : h->precision == HOPF_P_SPLIT ? FORM_SPLIT : FORM_BF16;
+  if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
+    return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
+  // MIXED in two stages: the SPLIT form (one phase per iteration) until each
+  // query's squared relative change is within split_start, then the defect
+  // correction from where it stopped to the tolerance (its fixed point, g = 0,
+  // does not depend on the start)
+  const bool staged = form == FORM_MIXED && two_stage(h) && w.qh && w.qiter0 && h->d_Mh16;
+  const int form1 = staged ? FORM_SPLIT : form;
+  hopf_status s = dense_init(h, w, x, t, stream);
+  if (s != HOPF_OK) return s;
+  const int64_t total = w.B_pad * h->n_pad;
+  k_tc_init_operand<<<1024, 256, 0, stream>>>(w.y, w.ph, w.pl, total, form1, (float)h->lambda, h->h_kind);
+  HOPF_CUDA(cudaGetLastError());
+
+  // SM pairs: an even number of 128-row tiles, and room for at least two CTAs
+  const int rt = h->n_pad / BM;
+  const int64_t tiles = (int64_t)rt * (w.B_pad / BN);
+  const int sms = h->grid_cap > 0 && h->grid_cap < h->num_sms ? h->grid_cap : h->num_sms;
+  const int cg = h->tc_pairs && rt % 2 == 0 && sms >= 2 && tiles >= 2 ? 2 : 1;
+  TcArgs a;
+  s = build_tc_args(h, w, x, grad, beta, xfin, form1, cg, &a);
+  if (s != HOPF_OK) return s;
+  if (staged) {
+    a.tol = (float)h->split_start;
+    a.no_final = 1;
+  }
+  if (h->prof_start) HOPF_CUDA(cudaEventRecord(h->prof_start, stream));
+  s = launch_tc(h, a, cg, tiles, sms, stream);
+  if (s != HOPF_OK) return s;
+  if (staged) {
+    s = dense_init_warm(h, w, x, t, stream);
+    if (s != HOPF_OK) return s;
+    s = build_tc_args(h, w, x, grad, beta, xfin, FORM_MIXED, cg, &a);
+    if (s != HOPF_OK) return s;
+    a.warm = 1;
+    a.iter_base = w.qiter0;
+    s = launch_tc(h, a, cg, tiles, sms, stream);
+    if (s != HOPF_OK) return s;
+  }
   if (h->prof_stop) HOPF_CUDA(cudaEventRecord(h->prof_stop, stream));
   return dense_finalize(h, w, phi, dphidt, iters, qstatus, stream);
 }

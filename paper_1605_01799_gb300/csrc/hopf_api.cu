@@ -162,6 +162,17 @@ hopf_status hopf_set_wait_limit(hopf_handle h, int64_t cycles) {
   return HOPF_OK;
 }
 
+hopf_status hopf_set_split_start(hopf_handle h, double tol_switch) {
+  set_error("");
+  if (!h) return fail(HOPF_EINVAL, "hopf_set_split_start: null handle");
+  if (!(tol_switch >= 0.0) || !std::isfinite(tol_switch))
+    return fail(HOPF_EINVAL, "hopf_set_split_start: tol_switch must be finite and >= 0");
+  if (tol_switch > 0.0 && (h->precision != HOPF_P_MIXED || h->h_kind == HOPF_H_L2))
+    return fail(HOPF_EUNSUPPORTED, "hopf_set_split_start: MIXED precision with H = l1 or weighted l1 only");
+  h->split_start = tol_switch;
+  return HOPF_OK;
+}
+
 hopf_status hopf_set_tc_pairs(hopf_handle h, int32_t on) {
   set_error("");
   if (!h) return fail(HOPF_EINVAL, "hopf_set_tc_pairs: null handle");
@@ -273,6 +284,9 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
   h->c0 = d.c0;
   h->lambda = d.lambda;
   h->tol = d.tol;
+  // MIXED, l1 / weighted l1: SPLIT iterations until the change is within ten
+  // times the tolerance, then the defect correction to the tolerance
+  h->split_start = d.precision == HOPF_P_MIXED && d.h_kind != HOPF_H_L2 ? 10.0 * d.tol : 0.0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
     free_handle(h);

@@ -56,6 +56,7 @@ struct hopf_handle_s {
   int compact = 1;  // tensor-core path: pack active queries as others converge
   long long wait_limit = 0;  // clock cycles of the dense solvers' bounded waits (0: the default)
   int tc_pairs = 0;  // tensor-core path: SM pairs (cta_group::2) when the row tiles pair up (off: measured slower)
+  double split_start = 0.0;  // MIXED form, l1 / weighted l1: SPLIT iterations down to this change first (0: off)
   Allocator alloc = {nullptr, nullptr, nullptr};  // the allocator this handle's memory came from
 };
 
@@ -137,10 +138,13 @@ struct DenseWs {
   uint16_t* ql = nullptr;
   uint16_t* qh_b = nullptr;
   uint16_t* ql_b = nullptr;
+  int* qiter0 = nullptr;     // [B_pad] two-stage solve: iterations of the first stage
   unsigned* bar = nullptr;   // [4] grid barrier + counters
   int* err = nullptr;        // [1]
 };
 size_t dense_workspace(const hopf_handle h, int64_t batch);
+bool two_stage(const hopf_handle h);
+hopf_status dense_init_warm(hopf_handle h, DenseWs& w, const float* x, const float* t, cudaStream_t s);
 hopf_status dense_carve(const hopf_handle h, int64_t batch, void* ws, size_t ws_bytes, DenseWs* d);
 hopf_status dense_eval_simt(hopf_handle h, DenseWs& w, const float* x, const float* t, double* phi, float* grad,
                             float* dphidt, int32_t* iters, uint8_t* qstatus, cudaStream_t stream, float* beta = nullptr,

@@ -336,7 +336,9 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
     S_ALLOC(h->d_Al2, pp * sizeof(uint16_t));
     S_ALLOC(h->d_Abf, pp * sizeof(uint16_t));
   }
-  if (h->precision == HOPF_P_SPLIT) {
+  // the FP16 split of M: the SPLIT form, and the SPLIT first stage of MIXED
+  // (l1, weighted l1)
+  if (h->precision == HOPF_P_SPLIT || (h->precision == HOPF_P_MIXED && h->h_kind != HOPF_H_L2)) {
     S_ALLOC(h->d_Mh16, pp * sizeof(uint16_t));
     S_ALLOC(h->d_Ml16, pp * sizeof(uint16_t));
   }

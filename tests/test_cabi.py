@@ -207,6 +207,8 @@ def test_allocator_and_wait_limit_arguments(hg):
     assert L.hopf_set_wait_limit(None, 100) == hg.HOPF_EINVAL
     assert L.hopf_set_tc_pairs(None, 1) == hg.HOPF_EINVAL
     assert b"hopf_set_tc_pairs" in L.hopf_last_error()
+    assert L.hopf_set_split_start(None, 1e-12) == hg.HOPF_EINVAL
+    assert b"hopf_set_split_start" in L.hopf_last_error()
 
 
 def test_backward_params_null_handle(hg):

@@ -164,6 +164,74 @@ def test_dense_t_zero_and_not_converged(hg, orc):
     assert (out["iters"].cpu().numpy() == 3).all()
 
 
+@pytest.mark.parametrize("n,B,h_kind", [(384, 1000, 1), (256, 700, 0)])
+def test_two_stage_mixed(hg, orc, n, B, h_kind):
+    """MIXED with l1 / weighted l1 runs SPLIT iterations until each query's
+    squared relative change is within ten times the tolerance, then the
+    defect correction from there: both stages' results sit within the MIXED
+    bars of the oracle (the second stage removes the SPLIT fixed point's
+    bias), and the total iteration counts follow the one-stage solve's,
+    including those of the t = 0 queries (prox the identity: the iteration
+    contracts at lambda / (lambda + s_min), some 120 steps here)."""
+    import torch
+    A, Q, s = wl.spd_matrix(11821 + n, 11822 + n, n)
+    w = wl.uniform(11823, n, 0.5, 1.5) if h_kind == 1 else None
+    x = wl.normal(11824, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = wl.uniform(11825, B, 0.1, 3.0).astype(np.float32)
+    t[::9] = 0.0
+    outs = {}
+    for sw in (None, 0.0):
+        h = hg.Hopf(A, h_kind, w=w, tol=TOL, max_iter=3000, precision=hg.P_MIXED)
+        if sw is not None:
+            h.set_split_start(sw)
+        outs[sw] = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    idx = np.r_[0:40, B - 24:B]
+    ref = orc.Problem(A, h_kind, w=w, tol=1e-28, max_iter=50000, stop_rule=orc.STOP_UREL).eval(
+        x[idx].astype(np.float64), t[idx].astype(np.float64))
+    for sw, out in outs.items():
+        assert (out["status"].cpu().numpy() == hg.Q_OK).all(), sw
+        ephi, eg = _errors({k: v[idx] for k, v in out.items()}, ref)
+        assert ephi.max() <= PHI_TOL, (sw, ephi.max())
+        assert eg.max() <= GRAD_MAX and np.median(eg) <= GRAD_MED, (sw, eg.max(), np.median(eg))
+    k2 = outs[None]["iters"].cpu().numpy().astype(np.int64)
+    k1 = outs[0.0]["iters"].cpu().numpy().astype(np.int64)
+    assert np.median(np.abs(k2 - k1)) <= 2 and np.abs(k2 - k1).max() <= 15, (np.abs(k2 - k1).max())
+
+
+def test_two_stage_mixed_max_iter(hg):
+    """max_iter caps the two stages' sum: a cap below the first stage's need
+    reports NOT_CONVERGED with iters = max_iter, as the one-stage solve does;
+    a cap between the stages' needs lets the defect correction finish within
+    it.  The switch accepts 0 and rejects a negative value or another form."""
+    import torch
+    n, B = 256, 300
+    A, Q, s = wl.spd_matrix(11831, 11832, n)
+    x = wl.normal(11834, B * n, 2.0).reshape(B, n).astype(np.float32)
+    t = np.full(B, 1.0, np.float32)
+    h = hg.Hopf(A, 0, tol=TOL, max_iter=5, precision=hg.P_MIXED)
+    out = h.eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == hg.Q_NOT_CONVERGED).all()
+    assert (out["iters"].cpu().numpy() == 5).all()
+    full = hg.Hopf(A, 0, tol=TOL, max_iter=3000, precision=hg.P_MIXED).eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    need = full["iters"].cpu().numpy()
+    cap = int(need.max()) + 2
+    out = hg.Hopf(A, 0, tol=TOL, max_iter=cap, precision=hg.P_MIXED).eval(_cuda(x), _cuda(t))
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == hg.Q_OK).all()
+    assert torch.equal(out["iters"], full["iters"])
+    with pytest.raises(hg.HopfError) as e:
+        h.set_split_start(-1.0)
+    assert e.value.status == hg.HOPF_EINVAL
+    h2 = hg.Hopf(A, 2, tol=TOL, max_iter=10, precision=hg.P_MIXED)  # l2: one stage
+    with pytest.raises(hg.HopfError) as e:
+        h2.set_split_start(1e-10)
+    assert e.value.status == hg.HOPF_EUNSUPPORTED
+    h2.set_split_start(0.0)
+
+
 def test_dense_not_spd(hg):
     A = np.eye(64)
     A[3, 3] = -5.0
