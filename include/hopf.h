@@ -332,9 +332,9 @@ hopf_status hopf_backward_params(hopf_handle h, int64_t batch, const float* g_ph
  * The first hopf_batch_eval call tunes the schedule: it captures and times
  * the persistent schedule with 4 to 32 lanes, wide instances on the whole GPU
  * or on lanes too, some SMs starting on the diagonal instances, and the stream
- * schedule with the best lane count, and keeps
- * the fastest (so it synchronises `stream`; its results are complete when it
- * returns); hopf_batch_info reports the choice.  Instances with FP64 precision are not accepted.
+ * schedule with 8 and 16 lanes, and keeps the fastest (so it synchronises
+ * `stream`; its results are complete when it returns); hopf_batch_info
+ * reports the choice.  Instances with FP64 precision are not accepted.
  * hopf_batch_create keeps a pinned host copy of the persistent schedule
  * (O(instances x SMs) bytes). */
 typedef struct hopf_batch_s* hopf_batch;
@@ -397,7 +397,8 @@ hopf_status hopf_set_tc_pairs(hopf_handle h, int32_t on);
  * max_iter caps their sum.  tol_switch = 0 runs the defect correction alone;
  * the default is ten times the handle's tolerance.  A workspace must be sized
  * (hopf_workspace_size) after the last call: the first stage needs the SPLIT
- * form's operand planes.  Ragged batches run the defect correction alone.
+ * form's operand planes.  Ragged batches run their MIXED instances the same
+ * way (both schedules), with each instance's switch as created.
  * Errors: HOPF_EINVAL for a null handle or a negative or non-finite
  * tol_switch; HOPF_EUNSUPPORTED for tol_switch > 0 with another precision or
  * H.  (The switch is this library's; the paper's iteration is unchanged.) */

@@ -384,7 +384,6 @@ hopf_status batch_create(const hopf_desc* descs, int32_t count, hopf_batch* out,
       free_batch(b);
       return fail(st, msg);
     }
-    h->split_start = 0.0;  // the persistent schedule runs the one-stage MIXED form; both schedules agree
     b->inst.push_back(h);
   }
 #define B_CALL(call)                     \
@@ -444,7 +443,7 @@ hopf_status batch_eval(hopf_batch b, const int64_t* counts, const float* x, cons
     // instances on the whole grid), with 8 and 16 lanes and 8 or 16 CTAs
     // starting on the diagonal work list, and with 8 lanes taking every
     // dense instance (so that the instances' last iterations overlap); then
-    // the stream schedule with the best lane count; keep the fastest
+    // the stream schedule with 8 and 16 lanes; keep the fastest
     struct Cand {
       int ns;
       bool persistent, wide_on_lanes;
@@ -494,8 +493,13 @@ hopf_status batch_eval(hopf_batch b, const int64_t* counts, const float* x, cons
       if (st != HOPF_OK) return st;
     }
     if (b->mode == 0) {
-      hopf_status st = trial(Cand{std::min(b->nstreams, 16), false, false, 0}, &b->streams_ms);
+      // the stream schedule at 8 and 16 lanes (its best lane count need not be
+      // the persistent schedule's)
+      float ms8 = 0.f, ms16 = 0.f;
+      hopf_status st = trial(Cand{8, false, false, 0}, &ms8);
+      if (st == HOPF_OK) st = trial(Cand{16, false, false, 0}, &ms16);
       if (st != HOPF_OK) return st;
+      b->streams_ms = ms8 < ms16 ? ms8 : ms16;
     }
     if (b->chosen == 1) {
       // the persistent graph copies its schedule from the staging buffer,

@@ -148,7 +148,7 @@ struct TcArgs {
   // first decision) and counts on from iter_base[q] iterations (also against
   // max_iter).  Both zero / null for a one-stage solve.
   int warm, no_final;
-  const int* iter_base;
+  int* iter_base;  // (the ragged kernel's in-kernel set-up of a second stage writes it)
 };
 
 // Per-CTA view of the slot layout; every CTA updates it identically.
@@ -1457,6 +1457,8 @@ __global__ void k_tc_init_operand(const float* __restrict__ y, uint16_t* __restr
 // picks for the instance's n, so again the results are the same.
 struct alignas(128) RagDense {
   TcArgs a;
+  TcArgs a2;          // staged MIXED (staged != 0): the defect-correction stage after a's SPLIT one
+  int staged;
   const float* t;     // the caller's t for the instance
   float* tq;          // [B_pad] t by query
   double* phi;
@@ -1533,6 +1535,66 @@ __device__ void rag_init(const RagDense& d, int gr, int gs) {
     a.tile_k[c] = 0;
     a.tile_cnt[c] = 0;
   }
+  proxy_fence_global();  // the operand planes are read by TMA
+}
+
+// The second stage of a staged instance, set up in-kernel by its group (what
+// k_dense_init_warm does for hopf_eval, in the same arithmetic): every slot
+// plane rebuilt from the first stage's query-indexed results, the iteration
+// counts so far kept in qiter0, the tile and decision counters cleared.
+__device__ void rag_init_warm(const RagDense& d, int gr, int gs) {
+  const TcArgs& a = d.a2;
+  const int64_t nthr = (int64_t)gs * NT, tid = (int64_t)gr * NT + threadIdx.x;
+  const int np = a.np;
+  const float lam = a.lam;
+  constexpr int U = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = (int64_t)gs * (NT / 32), wid = (int64_t)gr * (NT / 32) + (threadIdx.x >> 5);
+  for (int64_t q = wid; q < a.B_pad; q += nwarp) {
+    const bool live = q < a.B;
+    const float tl = (live ? d.t[q] : 0.f) / lam;
+    const float* xr = live ? a.x + q * a.n : nullptr;
+    const float* ur = a.ufin + q * np;
+    for (int i0 = 0; i0 < np; i0 += 32 * U) {
+      float yv[U], uv[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = i0 + j * 32 + lane;
+        const bool in = xr && i < a.n;
+        yv[j] = in ? xr[i] - a.cf[i] : 0.f;
+        uv[j] = in ? ur[i] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = i0 + j * 32 + lane;
+        if (i >= np) break;
+        const int64_t e = q * np + i;
+        const float pv = shrink1(uv[j], tl * a.w[i]);
+        const __half hi = __float2half_rn(pv);
+        a.y[0][e] = yv[j];
+        a.u[0][e] = uv[j];
+        a.p1[0][e] = __half_as_ushort(hi);
+        a.p2[0][e] = __half_as_ushort(__float2half_rn((pv - __half2float(hi)) * kLoScale));
+      }
+    }
+  }
+  for (int64_t q = tid; q < a.B_pad; q += nthr) {
+    const int k1 = q < a.B ? a.qiter[q] : 0;
+    const bool capped = q < a.B && k1 >= a.max_iter;
+    const float tl = (q < a.B ? d.t[q] : 0.f) / lam;
+    a.tau[q] = tl;
+    a.taus[0][q] = tl;
+    a.iter_base[q] = k1;
+    a.qiter[q] = capped ? k1 : 0;
+    a.qdone[q] = q >= a.B ? 1 : capped ? 2 : 0;
+    a.sq[0][q] = (int)q;
+  }
+  for (int64_t c = tid; c < a.B_pad / BN; c += nthr) {
+    a.tile_k[c] = 0;
+    a.tile_cnt[c] = 0;
+  }
+  if (gr == 0 && threadIdx.x == 0)
+    for (int j = 2; j < 5; ++j) atomicExch(a.bar + j, 0u);  // the decision counts (not the barrier's own words)
   proxy_fence_global();  // the operand planes are read by TMA
 }
 
@@ -1623,6 +1685,12 @@ __global__ void __launch_bounds__(NT, 1) k_ragged(const __grid_constant__ Ragged
     rag_init(d, w.y, w.z);
     bool ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
     if (ok) ok = solve_instance<1>(a, S, stages, ps, ms, es, w.y, w.z);
+    if (d.staged) {
+      if (ok) ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
+      if (ok) rag_init_warm(d, w.y, w.z);
+      if (ok) ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
+      if (ok) ok = solve_instance<1>(d.a2, S, stages, ps, ms, es, w.y, w.z);
+    }
     if (ok) ok = grid_barrier(a.bar, w.z, a.err, a.wait_limit);
     else __syncthreads();
     rag_finalize(d, w.y, w.z);
@@ -1850,8 +1918,20 @@ hopf_status ragged_build_dense(hopf_handle h, DenseWs& w, const float* x, const 
   if (form == FORM_BF16 && h->h_kind == HOPF_H_L2)
     return fail(HOPF_EUNSUPPORTED, "dense BF16 form: H = l2 needs the MIXED form");
   RagDense* d = new (rec) RagDense();
-  hopf_status s = build_tc_args(h, w, x, grad, nullptr, nullptr, form, 1, &d->a);
+  // MIXED in two stages, as hopf_eval runs it: the SPLIT stage in a, the
+  // defect correction (warm) in a2
+  const bool staged = form == FORM_MIXED && two_stage(h) && w.qh && w.qiter0 && h->d_Mh16;
+  hopf_status s = build_tc_args(h, w, x, grad, nullptr, nullptr, staged ? FORM_SPLIT : form, 1, &d->a);
   if (s != HOPF_OK) return s;
+  if (staged) {
+    d->a.tol = (float)h->split_start;
+    d->a.no_final = 1;
+    s = build_tc_args(h, w, x, grad, nullptr, nullptr, FORM_MIXED, 1, &d->a2);
+    if (s != HOPF_OK) return s;
+    d->a2.warm = 1;
+    d->a2.iter_base = w.qiter0;
+    d->staged = 1;
+  }
   d->t = t;
   d->tq = w.tq;
   d->phi = phi;
