@@ -47,9 +47,9 @@ METRIC = ("Hopf evals/s (phi at 1e-6 rel, grad phi at 6e-6 rel) n=1024 batch 64K
 # two-stage MIXED solve), from the ncu capture summarised in
 # profiles/k_dense_tc_n1024_b65536.md; reported only while the kernel source
 # still has the hash it had at capture and the switch is the default.
-MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "8571261505ce3851",
-                              "bytes": 128.74e9, "n": 1024, "batch": 65536,
-                              "per": "step: both launches of the two-stage solve (103.08 + 25.66 GB)"}}
+MEASURED_TRAFFIC = {"mixed": {"file": "paper_1605_01799_gb300/csrc/dense_tc.cu", "sha256_prefix": "18504a21e361a8cd",
+                              "bytes": 128.58e9, "n": 1024, "batch": 65536,
+                              "per": "step: both launches of the two-stage solve (102.92 + 25.66 GB)"}}
 TOL = 1e-13
 MAX_ITER = 1000
 
