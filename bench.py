@@ -670,7 +670,9 @@ def run_grad(args):
                 "config": {"workload": "dense_l1_grad_n2048_b32768", "n": n, "batch_per_gpu": B, "tol_urel": TOL,
                            "l2": "inputs larger than L2 (x is %d MiB per step)" % (d["x"].nbytes >> 20)},
                 "iters": {"mean": float(iters.mean()), "max": int(iters.max())},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clocks, "gpu_launches": 6 * args.steps}
+                # forward: set-up, operand, two solver launches, warm set-up, write-out;
+                # backward: g_x and g_t, then the tensor-core g_A (scale, splits, SYRK, reduce)
+                "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clocks, "gpu_launches": 11 * args.steps}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -752,7 +754,8 @@ def run_control(args):
                 "config": {"workload": "dense_wl1_n%d_b%d_control" % (n, B), "n": n, "batch_per_gpu": B,
                            "tol_urel": TOL, "l2": "inputs larger than L2 (x is %d MiB per step)" % (x.nbytes >> 20)},
                 "iters": {"mean": float(iters.mean()), "max": int(iters.max())},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * args.steps}
+                # set-up, operand, two solver launches (two-stage MIXED), warm set-up, write-out
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 6 * args.steps}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -1325,7 +1328,10 @@ def main():
                 "iters": {"mean": float(K.mean()), "max": int(K.max()), "min": int(K.min())},
                 "status_ok_frac": float((status == 0).mean()),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": (3 if main_variant == "fp32" else 4) * args.steps, "accuracy": accuracy,
+                # set-up, (operand), solver, write-out; the two-stage MIXED solve adds
+                # a second solver launch and the warm set-up between
+                "gpu_launches": (3 if main_variant == "fp32" else 6 if split_start != 0 else 4) * args.steps,
+                "accuracy": accuracy,
                 "arms": others,
                 "tc_over_fp32": (value / others["fp32"]["value"]) if "fp32" in others else None,
                 "pipes_measured": pipes}
