@@ -161,7 +161,7 @@ __global__ void k_dense_init_warm(const float* __restrict__ x, const float* __re
     y[q * np + i] = yv;
     u[q * np + i] = uv;
     ph[q * np + i] = __half_as_ushort(hi);
-    pl[q * np + i] = __half_as_ushort(__float2half_rn((pv - __half2float(hi)) * 2048.f));
+    pl[q * np + i] = __half_as_ushort(__float2half_rn((pv - __half2float(hi)) * 2048.f));  // 2^11: the split's scale
   }
   if (threadIdx.x == 0) {
     const int k1 = q < B ? qiter[q] : 0;
