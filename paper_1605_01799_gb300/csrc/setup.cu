@@ -74,6 +74,25 @@ __global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restric
     // the new values stay in registers until every thread has read the old)
     constexpr int R = kSB * kSB / 256;
     double nv[R];
+    if (nb == kSB) {
+      // a full block: entry e is row (tid >> 6) + 4 r, column tid & 63, so
+      // no index arithmetic runs per pivot (the same operations as below)
+      const int j = threadIdx.x & (kSB - 1), i0 = threadIdx.x >> 6;
+      const double bkj = B[k][j];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = i0 + 4 * r;
+        if (i == k && j == k) nv[r] = -inv;
+        else if (i == k) nv[r] = bkj * inv;
+        else if (j == k) nv[r] = B[i][k] * inv;
+        else nv[r] = B[i][j] - B[i][k] * bkj * inv;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < R; ++r) B[i0 + 4 * r][j] = nv[r];
+      __syncthreads();
+      continue;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int e = threadIdx.x + 256 * r;
