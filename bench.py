@@ -1043,8 +1043,8 @@ def run_fit(args):
     """Differentiation in use: 100 Adam steps fitting diag(A) of the n = 2048
     workload to target phi values (A = A0 + diag(delta), targets from a hidden
     delta* ~ U[0, 0.5], delta >= -0.05 lambda_min(A0) keeps A SPD), 32,768
-    queries, H = l1.  A step is hopf_create at the current A (the FP64 inverse
-    of A + lambda I), the MIXED forward and the envelope-theorem backward
+    queries, H = l1.  A step is hopf_create at the current A (the inverse of
+    A + lambda I, in FP32 for the MIXED form), the MIXED forward and the envelope-theorem backward
     through HopfFn.  Reports the loss and |delta - delta*| at every step."""
     import torch
     import paper_1605_01799_gb300 as hg
@@ -1100,7 +1100,7 @@ def run_fit(args):
                           "n=2048, 32,768 queries, dense A, l1",
                 "value": steps / total, "unit": "steps/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * total / steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16+f16 forward and f16 x3 backward (fp32 accumulate), f64 set-up",
+                "vs_baseline": None, "dtype": "bf16+f16 forward and f16 x3 backward (fp32 accumulate), f32 set-up",
                 "data": "synthetic",
                 "config": {"workload": "fit_diag_A_n2048_b32768", "n": n, "batch_per_gpu": B, "tol_urel": TOL,
                            "optimizer": "Adam lr 0.02", "delta_star": "U[0, 0.5]^n (seed 5009)"},

@@ -150,10 +150,13 @@ typedef struct {
 } hopf_desc;
 
 /* Build a handle: copies A, c, w to the device and, for dense A, forms
- * M = (A + lambda I)^{-1} in FP64 on the GPU (the prox of the quadratic J*,
+ * M = (A + lambda I)^{-1} on the GPU (the prox of the quadratic J*,
  * Section 3.1 / Section 4.1: (I + alpha A)^{-1}) with the casts the chosen
- * precision needs.  Returns HOPF_ENOTSPD when a pivot of A + lambda I is not
- * positive.  The handle is immutable afterwards: hopf_eval may run on several
+ * precision needs: in FP64 for HOPF_P_FP32 and HOPF_P_SPLIT, which apply M
+ * as the v-update; in FP32 for HOPF_P_MIXED, where M only preconditions the
+ * defect correction (whose fixed point uses A itself), and HOPF_P_BF16, which
+ * rounds M to BF16.  Returns HOPF_ENOTSPD when a pivot of A + lambda I is not
+ * positive (an FP32 pivot that is not is checked again in FP64).  The handle is immutable afterwards: hopf_eval may run on several
  * streams at once with distinct workspaces.  Synchronises `stream`. */
 hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t stream);
 

@@ -1,5 +1,7 @@
-// Dense setup, once per handle: M = (A + lambda I)^{-1} in FP64 on the GPU,
-// then the padded copies each precision needs.
+// Dense setup, once per handle: M = (A + lambda I)^{-1} on the GPU (FP64 for
+// the forms that apply it as the paper's v-update, FP32 where it only
+// preconditions the defect correction), then the padded copies each precision
+// needs.
 //
 // The v-update of eq. 3.4(a) is the prox of the quadratic J*: with
 // J*(v) = 1/2 v^T A v + <c,v> + c0 it solves (A + lambda I) v = y + lambda (d - b)
@@ -27,13 +29,14 @@
 
 namespace hopf {
 
-__global__ void k_load_shifted(const double* __restrict__ A, double* __restrict__ S, int n, double lam) {
+template <typename T>
+__global__ void k_load_shifted(const double* __restrict__ A, T* __restrict__ S, int n, double lam) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
   int i = (int)(idx / n), j = (int)(idx % n);
   // symmetrise the input: the method assumes A symmetric
   double a = 0.5 * (A[(int64_t)i * n + j] + A[(int64_t)j * n + i]);
-  S[idx] = a + (i == j ? lam : 0.0);
+  S[idx] = (T)(a + (i == j ? lam : 0.0));
 }
 
 // ---- blocked sweep ----------------------------------------------------------
@@ -49,9 +52,10 @@ constexpr int kSB = 64;  // pivots per block = tile edge of the update
 
 // Sweep the pivots of the diagonal block K = [k0, k0 + nb) in shared memory;
 // out = -S_KK^{-1} (nb x nb, leading dimension kSB).
-__global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restrict__ S, int n, int k0, int nb,
-                                                         double* __restrict__ out, int* err) {
-  __shared__ double B[kSB][kSB + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_block_inv(const T* __restrict__ S, int n, int k0, int nb,
+                                                         T* __restrict__ out, int* err) {
+  __shared__ T B[kSB][kSB + 1];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e % nb;
     B[i][j] = S[(int64_t)(k0 + i) * n + k0 + j];
@@ -61,24 +65,24 @@ __global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restric
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < nb; ++k) {
-    const double dkk = B[k][k];
-    if (!(dkk > 0.0)) {  // a Schur-complement pivot of A + lambda I: not SPD
+    const T dkk = B[k][k];
+    if (!(dkk > T(0))) {  // a Schur-complement pivot of A + lambda I: not SPD
       if (threadIdx.x == 0) {
         bad = 1;
         atomicExch(err, ERR_NOT_SPD);
       }
       break;  // dkk is the same for every thread: all leave together
     }
-    const double inv = 1.0 / dkk;
+    const T inv = T(1) / dkk;
     // each thread owns the entries e = threadIdx.x + 256 r (static indices:
     // the new values stay in registers until every thread has read the old)
     constexpr int R = kSB * kSB / 256;
-    double nv[R];
+    T nv[R];
     if (nb == kSB) {
       // a full block: entry e is row (tid >> 6) + 4 r, column tid & 63, so
       // no index arithmetic runs per pivot (the same operations as below)
       const int j = threadIdx.x & (kSB - 1), i0 = threadIdx.x >> 6;
-      const double bkj = B[k][j];
+      const T bkj = B[k][j];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = i0 + 4 * r;
@@ -96,7 +100,7 @@ __global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restric
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int e = threadIdx.x + 256 * r;
-      nv[r] = 0.0;
+      nv[r] = T(0);
       if (e < nb * nb) {
         const int i = e / nb, j = e % nb;
         if (i == k && j == k) nv[r] = -inv;
@@ -119,16 +123,17 @@ __global__ void __launch_bounds__(256) k_sweep_block_inv(const double* __restric
 
 // T[:, J] = -Kneg S[K, J] for one 64-column tile J (T = S_KK^{-1} S_K:), and the
 // old rows of K kept in Sold.  Both nb x n, leading dimension n.
-__global__ void __launch_bounds__(256) k_sweep_block_T(const double* __restrict__ S, int n, int k0, int nb,
-                                                       const double* __restrict__ Kneg, double* __restrict__ T,
-                                                       double* __restrict__ Sold, const int* err) {
+template <typename E>
+__global__ void __launch_bounds__(256) k_sweep_block_T(const E* __restrict__ S, int n, int k0, int nb,
+                                                       const E* __restrict__ Kneg, E* __restrict__ T,
+                                                       E* __restrict__ Sold, const int* err) {
   if (*((volatile const int*)err) != ERR_NONE) return;
-  __shared__ double Sk[kSB][kSB + 1];
+  __shared__ E Sk[kSB][kSB + 1];
   const int j0 = blockIdx.x * kSB;
   const int w = min(kSB, n - j0);
   for (int e = threadIdx.x; e < nb * kSB; e += blockDim.x) {
     const int k = e / kSB, j = e % kSB;
-    const double v = j < w ? S[(int64_t)(k0 + k) * n + j0 + j] : 0.0;
+    const E v = j < w ? S[(int64_t)(k0 + k) * n + j0 + j] : E(0);
     Sk[k][j] = v;
     if (j < w) Sold[(int64_t)k * n + j0 + j] = v;
   }
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(256) k_sweep_block_T(const double* __restrict_
   for (int e = threadIdx.x; e < nb * kSB; e += blockDim.x) {
     const int i = e / kSB, j = e % kSB;
     if (j >= w) continue;
-    double acc = 0.0;
+    E acc = E(0);
     for (int k = 0; k < nb; ++k) acc += __ldg(Kneg + i * kSB + k) * Sk[k][j];
     T[(int64_t)i * n + j0 + j] = -acc;
   }
@@ -146,10 +151,11 @@ __global__ void __launch_bounds__(256) k_sweep_block_T(const double* __restrict_
 //   I, J != K:  S_IJ -= Sold_K,I^T T_K,J
 //   J == K:     S_IK = T_K,I^T  (I != K);  S_KK = Kneg
 // Each thread owns a 4 x 4 block of the tile.
-__global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__ S, int n, int kt, int nb,
-                                                            const double* __restrict__ Kneg,
-                                                            const double* __restrict__ T,
-                                                            const double* __restrict__ Sold, const int* err) {
+template <typename E>
+__global__ void __launch_bounds__(256) k_sweep_block_update(E* __restrict__ S, int n, int kt, int nb,
+                                                            const E* __restrict__ Kneg,
+                                                            const E* __restrict__ T,
+                                                            const E* __restrict__ Sold, const int* err) {
   if (*((volatile const int*)err) != ERR_NONE) return;
   // blockIdx.x enumerates the tiles on and above the diagonal, row by row
   const int nt = (n + kSB - 1) / kSB;
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__
   const int i0 = I * kSB, j0 = J * kSB;
   const int hi = min(kSB, n - i0), wj = min(kSB, n - j0);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  double out[4][4];
+  E out[4][4];
   if (I == kt || J == kt) {
     // row / column block K: copies of T (or -S_KK^{-1} on the diagonal)
 #pragma unroll
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int i = 4 * ty + r, j = 4 * tx + c;
-        double v = 0.0;
+        E v = E(0);
         if (i < hi && j < wj) {
           if (I == kt && J == kt) v = Kneg[i * kSB + j];
           else if (I == kt) v = T[(int64_t)i * n + j0 + j];  // S_KJ = T_KJ
@@ -180,26 +186,26 @@ __global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__
       }
   } else {
     constexpr int KC = 32;            // k rows staged per round (32 KB of shared memory)
-    __shared__ double As[KC][kSB];    // As[k][i] = Sold[kc + k][i0 + i]
-    __shared__ double Bs[KC][kSB];    // Bs[k][j] = T[kc + k][j0 + j]
+    __shared__ E As[KC][kSB];    // As[k][i] = Sold[kc + k][i0 + i]
+    __shared__ E Bs[KC][kSB];    // Bs[k][j] = T[kc + k][j0 + j]
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int i = 4 * ty + r, j = 4 * tx + c;
-        out[r][c] = (i < hi && j < wj) ? S[(int64_t)(i0 + i) * n + j0 + j] : 0.0;
+        out[r][c] = (i < hi && j < wj) ? S[(int64_t)(i0 + i) * n + j0 + j] : E(0);
       }
     for (int kc = 0; kc < nb; kc += KC) {
       __syncthreads();
       for (int e = threadIdx.x; e < KC * kSB; e += blockDim.x) {
         const int k = e / kSB, c = e % kSB;
         const bool kin = kc + k < nb;
-        As[k][c] = (kin && c < hi) ? Sold[(int64_t)(kc + k) * n + i0 + c] : 0.0;
-        Bs[k][c] = (kin && c < wj) ? T[(int64_t)(kc + k) * n + j0 + c] : 0.0;
+        As[k][c] = (kin && c < hi) ? Sold[(int64_t)(kc + k) * n + i0 + c] : E(0);
+        Bs[k][c] = (kin && c < wj) ? T[(int64_t)(kc + k) * n + j0 + c] : E(0);
       }
       __syncthreads();
       for (int k = 0; k < KC; ++k) {
-        double a[4], b[4];
+        E a[4], b[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) a[r] = As[k][4 * ty + r];
 #pragma unroll
@@ -226,14 +232,15 @@ __global__ void __launch_bounds__(256) k_sweep_block_update(double* __restrict__
 // M = -(swept) symmetrised, padded to np x np with zeros; FP32/BF16 copies
 // and (SPLIT form) the two-term FP16 split M = hi + lo * 2^-11 with
 // hi = fp16(M), lo = fp16((M - hi) 2^11).
-__global__ void k_finish_inverse(const double* __restrict__ S, double* __restrict__ M64, float* __restrict__ M32,
+template <typename T>
+__global__ void k_finish_inverse(const T* __restrict__ S, double* __restrict__ M64, float* __restrict__ M32,
                                  uint16_t* __restrict__ Mbf, uint16_t* __restrict__ Mh, uint16_t* __restrict__ Ml,
                                  int n, int np) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)np * np) return;
   int i = (int)(idx / np), j = (int)(idx % np);
   double m = 0.0;
-  if (i < n && j < n) m = -0.5 * (S[(int64_t)i * n + j] + S[(int64_t)j * n + i]);
+  if (i < n && j < n) m = -0.5 * ((double)S[(int64_t)i * n + j] + (double)S[(int64_t)j * n + i]);
   if (M64) M64[idx] = m;
   if (M32) M32[idx] = (float)m;
   if (Mbf) Mbf[idx] = __bfloat16_as_ushort(__double2bfloat16(m));
@@ -296,6 +303,29 @@ void dev_free(const Allocator& a, void* p) {
   else cudaFree(p);
 }
 
+// The block sweep of A + lambda I in element type T into S (n x n); err
+// receives ERR_NOT_SPD at a non-positive pivot.  Buffers as in dense_setup.
+template <typename T>
+static cudaError_t sweep_inverse(const double* dA, int n, double lam, void* S, void* Tm, void* Sold, void* Kneg,
+                                 int* err, cudaStream_t stream) {
+  const size_t nn = (size_t)n * n;
+  const int tb = 256;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k_load_shifted<T><<<(unsigned)((nn + tb - 1) / tb), tb, 0, stream>>>(dA, (T*)S, n, lam);
+  const int nt = (n + kSB - 1) / kSB;
+  const unsigned upper = (unsigned)(nt * (nt + 1) / 2);
+  for (int kt = 0; kt < nt; ++kt) {
+    const int k0 = kt * kSB, nb = n - k0 < kSB ? n - k0 : kSB;
+    k_sweep_block_inv<T><<<1, 256, 0, stream>>>((const T*)S, n, k0, nb, (T*)Kneg, err);
+    k_sweep_block_T<T><<<(unsigned)nt, 256, 0, stream>>>((const T*)S, n, k0, nb, (const T*)Kneg, (T*)Tm, (T*)Sold,
+                                                         err);
+    k_sweep_block_update<T><<<upper, 256, 0, stream>>>((T*)S, n, kt, nb, (const T*)Kneg, (const T*)Tm,
+                                                       (const T*)Sold, err);
+  }
+  return cudaGetLastError();
+}
+
 hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream) {
   const int n = h->n, np = h->n_pad;
   const size_t nn = (size_t)n * n, pp = (size_t)np * np;
@@ -326,25 +356,26 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
   S_ALLOC(Sold, (size_t)kSB * n * sizeof(double));
   S_ALLOC(Kneg, (size_t)kSB * kSB * sizeof(double));
   S_ALLOC(err, sizeof(int));
-  S_CALL(cudaMemsetAsync(err, 0, sizeof(int), stream));
-  const int tb = 256;
-  k_load_shifted<<<(unsigned)((nn + tb - 1) / tb), tb, 0, stream>>>(h->d_A, S0, n, h->lambda);
-  const int nt = (n + kSB - 1) / kSB;
-  const unsigned upper = (unsigned)(nt * (nt + 1) / 2);
-  for (int kt = 0; kt < nt; ++kt) {
-    const int k0 = kt * kSB, nb = n - k0 < kSB ? n - k0 : kSB;
-    k_sweep_block_inv<<<1, 256, 0, stream>>>(S0, n, k0, nb, Kneg, err);
-    k_sweep_block_T<<<(unsigned)nt, 256, 0, stream>>>(S0, n, k0, nb, Kneg, Tm, Sold, err);
-    k_sweep_block_update<<<upper, 256, 0, stream>>>(S0, n, kt, nb, Kneg, Tm, Sold, err);
-  }
-  S_CALL(cudaGetLastError());
+  // M in FP32 where it only preconditions: the MIXED form's fixed point
+  // (g = y - A p - lambda (u - p) = 0) uses A itself, and the BF16 form
+  // rounds M to BF16; the FP32 and SPLIT forms apply M as the paper's
+  // v-update, so their M comes from the FP64 sweep.  A non-positive FP32
+  // pivot is checked again in FP64 before the handle reports HOPF_ENOTSPD.
+  bool f32 = h->precision == HOPF_P_MIXED || h->precision == HOPF_P_BF16;
   int herr = 0;
-  S_CALL(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-  S_CALL(cudaStreamSynchronize(stream));
+  for (;;) {
+    S_CALL(f32 ? sweep_inverse<float>(h->d_A, n, h->lambda, S0, Tm, Sold, Kneg, err, stream)
+               : sweep_inverse<double>(h->d_A, n, h->lambda, S0, Tm, Sold, Kneg, err, stream));
+    S_CALL(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    S_CALL(cudaStreamSynchronize(stream));
+    if (herr != ERR_NOT_SPD || !f32) break;
+    f32 = false;
+  }
   if (herr == ERR_NOT_SPD) {
     cleanup();
     return fail(HOPF_ENOTSPD, "hopf_create: A + lambda I is not symmetric positive definite");
   }
+  const int tb = 256;
   const bool simt = h->precision == HOPF_P_FP32;
   S_ALLOC(h->d_M32, pp * sizeof(float));
   S_ALLOC(h->d_A32, pp * sizeof(float));
@@ -361,8 +392,12 @@ hopf_status dense_setup(hopf_handle h, const double* A_host, cudaStream_t stream
     S_ALLOC(h->d_Mh16, pp * sizeof(uint16_t));
     S_ALLOC(h->d_Ml16, pp * sizeof(uint16_t));
   }
-  k_finish_inverse<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf, h->d_Mh16,
-                                                                       h->d_Ml16, n, np);
+  if (f32)
+    k_finish_inverse<float><<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>((const float*)S0, nullptr, h->d_M32,
+                                                                              h->d_Mbf, h->d_Mh16, h->d_Ml16, n, np);
+  else
+    k_finish_inverse<double><<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(S0, nullptr, h->d_M32, h->d_Mbf,
+                                                                               h->d_Mh16, h->d_Ml16, n, np);
   k_cast_A<<<(unsigned)((pp + tb - 1) / tb), tb, 0, stream>>>(h->d_A, h->d_A32, h->d_Abf, h->d_Ah16, h->d_Al16,
                                                                h->d_Al2, n, np);
   S_CALL(cudaGetLastError());
