@@ -232,12 +232,19 @@ def test_two_stage_mixed_max_iter(hg):
     h2.set_split_start(0.0)
 
 
-def test_dense_not_spd(hg):
-    A = np.eye(64)
+@pytest.mark.parametrize("precision", ["FP32", "SPLIT", "MIXED", "BF16"])
+def test_dense_not_spd(hg, precision):
+    """A + lambda I with a negative eigenvalue is refused for every dense form:
+    MIXED and BF16 sweep in FP32 and confirm a non-positive pivot in FP64,
+    the others sweep in FP64.  An SPD matrix whose FP32 sweep is accurate
+    enough is accepted by all (n = 200: a ragged last pivot block)."""
+    A = np.eye(200)
     A[3, 3] = -5.0
     with pytest.raises(hg.HopfError) as e:
-        hg.Hopf(A, 0, tol=1e-12, max_iter=10, precision=hg.P_FP32)
+        hg.Hopf(A, 0, tol=1e-12, max_iter=10, precision=getattr(hg, "P_" + precision))
     assert e.value.status == hg.HOPF_ENOTSPD
+    A[3, 3] = 0.5
+    hg.Hopf(A, 0, tol=1e-12, max_iter=10, precision=getattr(hg, "P_" + precision))
 
 
 @pytest.mark.parametrize("precision,h_kind", [("MIXED", 1), ("SPLIT", 1), ("SPLIT", 2)])
