@@ -164,7 +164,9 @@ hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t st
 void hopf_destroy(hopf_handle h);
 
 /* Bytes of device workspace hopf_eval / hopf_eval_f64 need for `batch`
- * queries (256-byte aligned pointer expected). */
+ * queries (256-byte aligned pointer expected), with the handle's current
+ * settings (the two-stage MIXED solve, hopf_set_split_start, needs the SPLIT
+ * form's operand planes too). */
 hopf_status hopf_workspace_size(hopf_handle h, int64_t batch, size_t* bytes);
 
 /* Evaluate `batch` queries (FP32 interface; any precision but FP64).
