@@ -18,7 +18,12 @@ J(x_T) = phi, and brute-force minimisation at n = 2 of the Hopf formula with
 the Hamiltonian min_i H_i, the new proxes against numerical minimisation of
 their definitions, closed forms through Hopf-Lax projections for J = 1/2|x|^2
 with H = l_inf and sqrt(sum w p^2), and brute-force Hopf objectives at n = 2
-for the non-quadratic initial data (with lambda != 1).  Parity unpinned: iteration counts (the paper prints none).
+for the non-quadratic initial data (with lambda != 1), and the iteration
+counts of both stop rules against exact rational iterates (l1 and weighted
+l1, diagonal and dense A).  Parity unpinned: iteration counts with the
+Hamiltonians whose proxes take square roots or roots of piecewise functions
+(l2, l_inf, the D- and A-norms), which no exact rational run reproduces; the
+paper prints no counts.
 ``tests/test_oracle_mutants.py`` plants plausible mistakes one at a time in a
 scratch copy of the C source and checks that the pins named for each fail.
 """

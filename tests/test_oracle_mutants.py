@@ -130,6 +130,12 @@ MUTANTS = [
      "test_weighted_l1_with_centre"),
     ("terminal_point_sign", "x_T[q * n + i] = xi - t[q] * b;", "x_T[q * n + i] = xi + t[q] * b;",
      "test_control_is_a_subgradient_and_the_hopf_lax_minimiser"),
+    ("urel_not_relative", "ru = du / (un > 1.0 ? un : 1.0);", "ru = du;", "test_relative_stop_rule_exact_iterations"),
+    ("urel_no_floor", "ru = du / (un > 1.0 ? un : 1.0);", "ru = du / un;",
+     "test_relative_stop_rule_exact_iterations"),
+    ("urel_previous_u_from_v", "double uold = d[i] + b[i];", "double uold = vprev[i] + b[i];",
+     "test_relative_stop_rule_exact_iterations"),
+    ("urel_norm_of_v", "un += u * u;", "un += v[i] * v[i];", "test_relative_stop_rule_exact_iterations"),
 ]
 
 

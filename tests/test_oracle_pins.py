@@ -880,3 +880,86 @@ def test_paper_stop_rule_exact_iterations(orc, case):
     P = orc.Problem(af, orc.H_L1, c0=0.5, lam=float(lam), tol=float(tol), max_iter=500, stop_rule=orc.STOP_PAPER)
     r = P.eval(yf, np.array([float(t)]))
     assert int(r["iters"][0]) == K, (int(r["iters"][0]), K)
+
+
+def _solve_exact(S, r):
+    """x with S x = r by Gauss-Jordan elimination on exact rationals."""
+    n = len(r)
+    M = [list(S[i]) + [r[i]] for i in range(n)]
+    for c in range(n):
+        p = next(i for i in range(c, n) if M[i][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for i in range(n):
+            if i != c and M[i][c] != 0:
+                f = M[i][c] / M[c][c]
+                M[i] = [M[i][j] - f * M[c][j] for j in range(n + 1)]
+    return [M[i][n] / M[i][i] for i in range(n)]
+
+
+def _relative_rule_iterations_exact(A, w, y, t, lam, tol, max_iter):
+    """Split Bregman (eq. 3.4(a)-(c)) for a dense A and H = weighted l1 in
+    exact rational arithmetic, stopped by the relative change of the d-update
+    argument u^k = v^k + b^{k-1}: the first k >= 2 with
+    |u^k - u^{k-1}|^2 <= tol max(1, |u^k|^2), where u^0 = y (v^0 = d^0 = y,
+    b^0 = 0, Section 3.1).  u^{k-1} is kept from the previous step, not
+    rebuilt from d and b.  Returns k and (ratio to tol, |u|^2) at k - 1 and k."""
+    n = len(y)
+    S = [[A[i][j] + (lam if i == j else 0) for j in range(n)] for i in range(n)]
+    tau = t / lam
+    d, b, u_prev = list(y), [0] * n, list(y)
+    prev = None
+    for k in range(1, max_iter + 1):
+        v = _solve_exact(S, [y[i] + lam * (d[i] - b[i]) for i in range(n)])
+        u = [v[i] + b[i] for i in range(n)]
+        un = sum(e * e for e in u)
+        ru = sum((u[i] - u_prev[i]) ** 2 for i in range(n)) / max(un, 1)
+        if k >= 2 and ru <= tol:
+            return k, prev, (ru / tol, un)
+        prev = (ru / tol, un)
+        d = [_shrink_exact(u[i], tau * w[i]) for i in range(n)]
+        b = [u[i] - d[i] for i in range(n)]
+        u_prev = u
+    return None, prev, None
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_relative_stop_rule_exact_iterations(orc, case):
+    """The oracle's iteration count under the relative-change rule (the rule
+    of every dense solve) equals the first k at which the exact (rational)
+    iterates meet it: dense and diagonal A, l1 and weighted l1, |u|^2 above 1
+    (the division counts) and below 1 (the floor counts), with the crossing
+    at a margin of at least 10 % (FP64 rounding moves the ratio by ~1e-10)."""
+    from fractions import Fraction as F
+    A1 = [[F(2), F(1, 2), F(0)], [F(1, 2), F(3, 2), F(1, 4)], [F(0), F(1, 4), F(1)]]
+    D4 = [[F(3, 2), 0, 0, 0], [0, F(5, 4), 0, 0], [0, 0, F(7, 8), 0], [0, 0, 0, F(2)]]
+    one3, one4 = [F(1)] * 3, [F(1)] * 4
+    cases = [  # (A, w, y, t, lam, tol)
+        (A1, one3, [F(9, 8), F(-5, 4), F(3, 16)], F(3, 4), F(1), F(1, 10 ** 10)),
+        (A1, one3, [F(5, 2), F(-3), F(7, 4)], F(1, 2), F(1), F(1, 10 ** 10)),
+        (A1, one3, [F(1, 4), F(-1, 8), F(3, 16)], F(1, 8), F(1), F(1, 10 ** 10)),
+        (A1, [F(1, 2), F(3, 2), F(1)], [F(5, 2), F(-3), F(7, 4)], F(1, 2), F(1, 2), F(1, 10 ** 12)),
+        (D4, one4, [F(9, 8), F(-5, 4), F(3, 16), F(-7, 2)], F(3, 4), F(1), F(2, 10 ** 10)),
+        # a coordinate inside the shrink's dead zone (b there follows u, so
+        # u^{k-1} differs from v^{k-1} + b^{k-1}) and a crossing between the
+        # two
+        (A1, one3, [F(9, 8), F(-5, 4), F(3, 16)], F(3, 4), F(1), F(2, 10 ** 10)),
+    ]
+    A, w, y, t, lam, tol = cases[case]
+    K, before, at = _relative_rule_iterations_exact(A, w, y, t, lam, tol, 400)
+    assert K is not None and K >= 3
+    assert at[0] <= F(9, 10) and before[0] >= F(11, 10)
+    n = len(y)
+    if case == 4:
+        Af = np.array([float(A[i][i]) for i in range(n)])
+    else:
+        Af = np.array([[float(e) for e in row] for row in A])
+    hk = orc.H_L1 if all(e == 1 for e in w) else orc.H_WL1
+    P = orc.Problem(Af, hk, w=np.array([float(e) for e in w]), c0=0.5, lam=float(lam), tol=float(tol),
+                    max_iter=400, stop_rule=orc.STOP_UREL)
+    r = P.eval(np.array([[float(e) for e in y]]), np.array([float(t)]))
+    assert int(r["iters"][0]) == K, (int(r["iters"][0]), K)
+    # the two regimes of the floor are both exercised
+    if case == 2:
+        assert at[1] < F(1, 2)
+    if case == 1:
+        assert at[1] > 4
