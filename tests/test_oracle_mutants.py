@@ -136,6 +136,21 @@ MUTANTS = [
     ("urel_previous_u_from_v", "double uold = d[i] + b[i];", "double uold = vprev[i] + b[i];",
      "test_relative_stop_rule_exact_iterations"),
     ("urel_norm_of_v", "un += u * u;", "un += v[i] * v[i];", "test_relative_stop_rule_exact_iterations"),
+    ("cholesky_no_sqrt", "L[(int64_t)i * n + i] = sqrt(s);", "L[(int64_t)i * n + i] = s;",
+     "test_dense_wl1_kkt_certificate"),
+    ("forward_solve_transposed", "for (int k = 0; k < i; ++k) s -= L[(int64_t)i * n + k] * v[k];",
+     "for (int k = 0; k < i; ++k) s -= L[(int64_t)k * n + i] * v[k];", "test_dense_wl1_kkt_certificate"),
+    ("factor_inner_transposed", "s -= L[(int64_t)i * n + k] * L[(int64_t)j * n + k];",
+     "s -= L[(int64_t)i * n + k] * L[(int64_t)k * n + j];", "test_dense_wl1_kkt_certificate"),
+    ("solve_centre_dropped", "for (int i = 0; i < n; ++i) y[i] = x[i] - (p->c ? p->c[i] : 0.0);",
+     "for (int i = 0; i < n; ++i) y[i] = x[i];", "test_weighted_l1_with_centre"),
+    ("prox_argument_drops_b", "double u = v[i] + b[i];", "double u = v[i];", "test_workload1_closed_form"),
+    ("dense_quad_diagonal_only", "for (int j = 0; j < p->n; ++j) r += p->A[(int64_t)i * p->n + j] * v[j];",
+     "r += p->A[(int64_t)i * p->n + i] * v[i];", "test_dense_duality_gap"),
+    ("l2_H_not_rooted", "for (int i = 0; i < n; ++i) s += q[i] * q[i];\n        return sqrt(s);",
+     "for (int i = 0; i < n; ++i) s += q[i] * q[i];\n        return s;", "test_paper_example_sphere"),
+    ("anorm_H_not_rooted", "return sqrt(s > 0.0 ? s : 0.0);", "return s > 0.0 ? s : 0.0;",
+     "test_anorm_l2sq_initial_data_closed_form or test_anorm_bruteforce_n2"),
 ]
 
 
