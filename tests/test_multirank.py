@@ -105,3 +105,26 @@ def test_dense_work_counts():
     assert exe == 2.0 * n * n * (4 * K + 3).sum()
     assert bench.dense_work(n, K, "bf16") == (alg, 2.0 * n * n * (K + 3).sum())
     assert bench.dense_work(n, K, "fp32") == (alg, 2.0 * n * n * (K + 1).sum())
+
+
+def test_clock_record_parsing(tmp_path):
+    """The clocks record of a timed region (nvidia-smi CSV, no units): the
+    median SM clock and the max clock of the benchmarked GPU only, every
+    throttle reason seen active at least once, lines from other GPUs and
+    malformed lines ignored, and "unsampled" when nothing was read."""
+    sys.path.insert(0, ROOT)
+    import bench
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join([
+        "0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1, 1200, 2070, 300.0, 0x0000000000000020, Not Active, Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+        "0, 2040, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+    ]) + "\n")
+    r = bench.read_clocks(str(p), 0)
+    assert r == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    r1 = bench.read_clocks(str(p), 1)
+    assert r1["sm_mhz"] == 1200.0 and r1["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.read_clocks(str(tmp_path / "missing.csv"), 0)["reasons"] == ["unsampled"]
