@@ -243,3 +243,92 @@ def test_header_is_plain_c_and_links(hg, tmp_path):
         [os.path.dirname(lib), os.environ.get("LD_LIBRARY_PATH", "")]))
     r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "%d entry points" % len(names), (r.stdout, r.stderr)
+
+
+_OPAQUE = {"hopf_handle", "hopf_batch", "cudaStream_t", "cudaEvent_t", "hopf_alloc_fn", "hopf_free_fn"}
+_SCALAR = {"int64_t": "i64", "int32_t": "i32", "float": "f32", "double": "f64", "size_t": "sz",
+           "hopf_status": "i32", "void": None}
+
+
+def _c_kind(decl):
+    """Argument or return category of a C declaration (without its name)."""
+    decl = decl.replace("const", " ").strip()
+    if "*" in decl:
+        return "ptr"
+    base = decl.split()[0]
+    if base in _OPAQUE:
+        return "ptr"
+    return _SCALAR[base]
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return None
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    return {ctypes.c_int64: "i64", ctypes.c_int32: "i32", ctypes.c_float: "f32", ctypes.c_double: "f64",
+            ctypes.c_size_t: "sz"}[t]
+
+
+def declared_prototypes():
+    src = open(os.path.join(ROOT, "include", "hopf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w \*]*?)\s*\b(hopf_\w+)\s*\(([^)]*)\)\s*;", src):
+        ret, name, args = m.group(1).strip(), m.group(2), " ".join(m.group(3).split())
+        kinds = []
+        if args != "void":
+            for a in args.split(","):
+                a = a.strip()
+                # drop the parameter name (the last identifier), keep the type and any '*'
+                kinds.append(_c_kind(re.sub(r"\b\w+$", "", a)))
+        out[name] = (_c_kind(ret), kinds)
+    return out
+
+
+def test_binding_signatures_match_the_header(hg):
+    """Every entry point's ctypes signature in the binding has the header's
+    arity and, argument by argument, the same width and kind (pointer,
+    int32, int64, size_t, float, double), and the same return type: a
+    mismatch would pass wrong values across the boundary without an error."""
+    protos = declared_prototypes()
+    assert set(protos) == set(hg.EXPORTS)
+    L = hg.lib()
+    for name, (ret, kinds) in protos.items():
+        f = getattr(L, name)
+        got = [_ctypes_kind(t) for t in f.argtypes]
+        assert got == kinds, (name, got, kinds)
+        r = _ctypes_kind(f.restype)
+        if name in ("hopf_last_error", "hopf_version"):
+            assert f.restype is ctypes.c_char_p, name
+        elif ret == "i32":
+            assert f.restype is ctypes.c_int, name
+        else:
+            assert r == ret, (name, r, ret)
+
+
+def test_descriptor_layout_matches_c(hg, tmp_path):
+    """hopf_desc has the same size and field offsets in the binding as in C
+    (compiled from the header with gcc)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not on PATH")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    c_names = ["n", "a_kind", "A", "centre", "c0", "h_kind", "w", "lambda", "tol", "max_iter", "precision",
+               "stop_rule"]
+    py_names = [f[0] for f in hg.hopf_desc._fields_]
+    assert len(py_names) == len(c_names)
+    src = tmp_path / "layout.c"
+    src.write_text('#include "hopf.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void) {\n'
+                   '    printf("%zu", sizeof(hopf_desc));\n' +
+                   "".join('    printf(" %%zu", offsetof(hopf_desc, %s));\n' % c for c in c_names) +
+                   '    printf("\\n");\n    return 0;\n}\n')
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"), "-I" + cuda_inc,
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.split()]
+    assert vals[0] == ctypes.sizeof(hg.hopf_desc)
+    assert vals[1:] == [getattr(hg.hopf_desc, p).offset for p in py_names]
