@@ -151,6 +151,8 @@ MUTANTS = [
      "for (int i = 0; i < n; ++i) s += q[i] * q[i];\n        return s;", "test_paper_example_sphere"),
     ("anorm_H_not_rooted", "return sqrt(s > 0.0 ? s : 0.0);", "return s > 0.0 ? s : 0.0;",
      "test_anorm_l2sq_initial_data_closed_form or test_anorm_bruteforce_n2"),
+    ("gradient_negated", "for (int i = 0; i < n; ++i) grad[i] = d[i];", "for (int i = 0; i < n; ++i) grad[i] = -d[i];",
+     "test_phi_convex_in_x_with_supporting_gradient"),
 ]
 
 

@@ -963,3 +963,36 @@ def test_relative_stop_rule_exact_iterations(orc, case):
         assert at[1] < F(1, 2)
     if case == 1:
         assert at[1] > 4
+
+
+@pytest.mark.parametrize("h", ["l1", "wl1", "l2"])
+def test_phi_convex_in_x_with_supporting_gradient(orc, h):
+    """phi(., t) is a Legendre transform (eq. 3.3: the supremum over v of
+    affine functions of x), hence convex, and grad_x phi = d^K is a
+    subgradient: phi(x2) >= phi(x1) + <grad phi(x1), x2 - x1> for every pair,
+    and phi on the segment lies below the chord."""
+    n, m = 12, 10
+    A, _ = _dense(n, 7401)
+    w = wl.uniform(7403, n, 0.5, 1.5) if h == "wl1" else None
+    x = wl.normal(7404, m * n, 2.0).reshape(m, n)
+    t = np.full(m, 0.7)
+    kind = {"l1": orc.H_L1, "wl1": orc.H_WL1, "l2": orc.H_L2}[h]
+    P = orc.Problem(A, kind, w=w, tol=1e-28, max_iter=20000, stop_rule=orc.STOP_UREL)
+    r = P.eval(x, t)
+    phi, g = r["phi"], r["grad"]
+    for i in range(m):
+        for j in range(m):
+            if i == j:
+                continue
+            lin = phi[i] + g[i] @ (x[j] - x[i])
+            slack = 1e-9 * (abs(phi[j]) + abs(lin) + 1)
+            assert phi[j] >= lin - slack, (i, j, phi[j], lin)
+    # midpoints of consecutive pairs, three interior points each
+    th = np.array([0.25, 0.5, 0.75])
+    for i in range(m - 1):
+        xs = th[:, None] * x[i] + (1 - th[:, None]) * x[i + 1]
+        mid = P.eval(xs, np.full(3, 0.7))["phi"]
+        chord = th * phi[i] + (1 - th) * phi[i + 1]
+        assert (mid <= chord + 1e-9 * (np.abs(chord) + 1)).all(), (i, mid, chord)
+    # and the gap is not vacuous: strict convexity shows along some segment
+    assert max(abs(phi[j] - phi[i] - g[i] @ (x[j] - x[i])) for i in range(m) for j in range(m)) > 1e-3
