@@ -128,3 +128,34 @@ def test_clock_record_parsing(tmp_path):
     r1 = bench.read_clocks(str(p), 1)
     assert r1["sm_mhz"] == 1200.0 and r1["reasons"] == ["hw_thermal_slowdown"]
     assert bench.read_clocks(str(tmp_path / "missing.csv"), 0)["reasons"] == ["unsampled"]
+
+
+def test_splitmix64_matches_its_definition():
+    """The input generator is SplitMix64 (Steele, Lea & Flood 2014): the
+    counter form used here equals the sequential definition (state advanced
+    by the golden-ratio increment modulo 2^64, then the two xor-shift-multiply
+    rounds) written out with Python integers, at any offset; seed 1234567
+    gives the widely published first outputs; uniforms are the top 53 bits."""
+    sys.path.insert(0, ROOT)
+    import workloads as wl
+    mask = (1 << 64) - 1
+
+    def sequential(seed, count):
+        s, out = seed & mask, []
+        for _ in range(count):
+            s = (s + 0x9E3779B97F4A7C15) & mask
+            z = s
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+            out.append(z ^ (z >> 31))
+        return out
+
+    for seed in (0, 1, 1234567, 2004, (1 << 64) - 1):
+        ref = sequential(seed, 300)
+        assert [int(v) for v in wl.splitmix64(seed, 300)] == ref
+        assert [int(v) for v in wl.splitmix64(seed, 50, offset=123)] == ref[123:173]
+        u = wl.uniform(seed, 300)
+        assert np.array_equal(u, np.array([(v >> 11) / 2.0 ** 53 for v in ref]))
+        assert (u >= 0).all() and (u < 1).all()
+    assert [int(v) for v in wl.splitmix64(1234567, 5)] == [
+        6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431, 16408922859458223821]
