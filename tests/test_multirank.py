@@ -159,3 +159,27 @@ def test_splitmix64_matches_its_definition():
         assert (u >= 0).all() and (u < 1).all()
     assert [int(v) for v in wl.splitmix64(1234567, 5)] == [
         6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431, 16408922859458223821]
+
+
+def test_matrix_and_normal_generators():
+    """The workloads' dense A = Q diag(s) Q^T: symmetric, Q orthogonal, the
+    spectrum exactly the drawn s (within FP64 rounding), so cond(A) is
+    bounded by s_hi / s_lo; Haar Q: E[Q_ij^2] = 1/n over many draws.  The
+    Box-Muller normals have mean 0 and variance std^2 (5-sigma bounds)."""
+    sys.path.insert(0, ROOT)
+    import workloads as wl
+    n = 64
+    A, Q, s = wl.spd_matrix(9101, 9102, n)
+    assert np.array_equal(A, A.T)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-13
+    ev = np.linalg.eigvalsh(A)
+    assert np.allclose(ev, np.sort(s), rtol=1e-12, atol=1e-13)
+    assert s.min() >= 0.1 and s.max() <= 10.0
+    # a Haar row is uniform on the sphere: E[x_j^2] = 1/m, Var = (2m - 2) / (m^2 (m + 2))
+    m, draws = 8, 400
+    sq = np.mean([wl.haar_orthogonal(9200 + k, m)[0] ** 2 for k in range(draws)], axis=0)
+    sd = np.sqrt((2 * m - 2) / (m * m * (m + 2)) / draws)
+    assert np.abs(sq - 1 / m).max() < 5 * sd
+    z = wl.normal(9301, 200000, std=2.0)
+    assert abs(z.mean()) < 5 * 2.0 / np.sqrt(z.size)
+    assert abs(z.var() / 4.0 - 1) < 5 * np.sqrt(2.0 / z.size)
