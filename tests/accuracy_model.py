@@ -1,0 +1,129 @@
+"""A numpy model of the dense tensor-core forms' arithmetic (test support).
+
+It derives the gradient tolerances of the dense parity tests from the
+arithmetic: it runs the split Bregman iteration (eq. 3.4(a)-(c), in the
+u-form u^k = v^k + b^{k-1}) with the number formats and the accumulation
+order that the tensor-core kernels use, and compares the returned gradient
+d^K with the FP64 oracle's.
+
+- Operands: FP16 (RN) with the two-term split x ~ hi + 2^-11 lo',
+  lo' = fp16((x - hi) 2^11); BF16 (RN) for the defect-correction step.
+- Products: one MMA multiplies K = 16 pairs; the 16 products and their sum
+  are taken exactly (FP16 x FP16 products are exact in FP32), then added to
+  an FP32 accumulator, either rounded to nearest ("rn") or truncated toward
+  zero ("rz").  Accumulators sum the n / 16 K steps in order; the correction
+  terms of a split product share one accumulator, interleaved per K step,
+  and the BF16 product alternates K steps between two accumulators.
+- Elementwise work (prox, b, g, the state) in FP32.
+
+SPLIT:  v^{k+1} = M r^k with both M and r^k = y + lam (2 p^k - u^k) split;
+        u^{k+1} = v^{k+1} + u^k - p^k.
+MIXED:  g^k = y - A p^k - lam (u^k - p^k) with A p^k split (g stored in
+        BF16), u^{k+1} = u^k + bf16(M) g^k; the fixed point g = 0 does not
+        depend on the rounding of M.
+Both stop at the first k >= 2 with |u^k - u^{k-1}|^2 <= tol max(1, |u^k|^2).
+
+This is a model of the hardware's arithmetic, not of the kernels' code:
+the parity tests on the GPU measure the kernels themselves.  Only ``tests/``
+uses it.
+"""
+import numpy as np
+
+K_STEP = 16
+LO_SCALE = np.float32(2048.0)
+
+
+def round_f32(s, mode):
+    """FP64 values to FP32, rounded to nearest ("rn") or toward zero ("rz")."""
+    f = s.astype(np.float32)
+    if mode == "rz":
+        over = np.abs(f.astype(np.float64)) > np.abs(s)
+        f[over] = np.nextafter(f[over], np.float32(0))
+    return f
+
+
+def to_bf16(x):
+    """FP32 to BF16 (round to nearest, ties to even), returned as FP32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + (((b >> 16) & 1) + 0x7FFF)) & 0xFFFF0000).astype(np.uint32)
+    return b.view(np.float32)
+
+
+def split_fp16(x):
+    """Two-term FP16 split (hi, lo') of an FP32 array, returned as FP32."""
+    hi = x.astype(np.float16).astype(np.float32)
+    lo = ((x - hi) * LO_SCALE).astype(np.float16).astype(np.float32)
+    return hi, lo
+
+
+def k_step_products(A, B):
+    """P[k] = A[:, 16k:16k+16] @ B[16k:16k+16, :], exact in FP64."""
+    nk = A.shape[1] // K_STEP
+    Ar = A.astype(np.float64).reshape(A.shape[0], nk, K_STEP).transpose(1, 0, 2)
+    return np.matmul(Ar, B.astype(np.float64).reshape(nk, K_STEP, B.shape[1]))
+
+
+def accumulate(products, mode):
+    """One FP32 accumulator over the K steps of each product array in
+    ``products`` (issued in turn within each K step)."""
+    acc = None
+    for k in range(products[0].shape[0]):
+        for P in products:
+            acc = round_f32(P[k] if acc is None else acc.astype(np.float64) + P[k], mode)
+    return acc
+
+
+def split_product(Xh, Xl, Yh, Yl, mode):
+    """X Y ~ D1 + 2^-11 D2, D1 = Xh Yh, D2 = Xh Yl' + Xl' Yh."""
+    d1 = accumulate([k_step_products(Xh, Yh)], mode)
+    d2 = accumulate([k_step_products(Xh, Yl), k_step_products(Xl, Yh)], mode)
+    return d1 + d2 / LO_SCALE
+
+
+def _iterate(step, y, thr, tol, max_iter):
+    """Run ``step(u, p) -> u_next`` per query until the relative rule stops it."""
+    q = y.shape[1]
+    u, p = y.copy(), y.copy()
+    iters, done = np.zeros(q, np.int64), np.zeros(q, bool)
+    for k in range(1, max_iter + 1):
+        un = step(u, p)
+        du = (un - u).astype(np.float64)
+        ru = (du * du).sum(0) / np.maximum(1.0, (un.astype(np.float64) ** 2).sum(0))
+        act = ~done
+        pn = (np.sign(un) * np.maximum(np.abs(un) - thr, 0)).astype(np.float32)
+        u[:, act], p[:, act] = un[:, act], pn[:, act]
+        iters[act] = k
+        if k >= 2:
+            done |= ru <= tol
+        if done.all():
+            break
+    return p, iters
+
+
+def solve(form, A, lam, y, thr, tol, mode, max_iter=3000):
+    """Gradients d^K (n x q, FP32) and iteration counts of the weighted-l1
+    problem with J*(v) = 1/2 v^T A v and thresholds thr = (t / lam) w
+    (n x q), for y = x - c given as n x q columns."""
+    n = A.shape[0]
+    M = np.linalg.inv(A + lam * np.eye(n)).astype(np.float32)
+    lam32 = np.float32(lam)
+    if form == "split":
+        Mh, Ml = split_fp16(M)
+
+        def step(u, p):
+            r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)
+            v = split_product(Mh, Ml, *split_fp16(r), mode)
+            return (v + (u - p)).astype(np.float32)
+    elif form == "mixed":
+        Ah, Al = split_fp16(A.astype(np.float32))
+        Mb = to_bf16(M)
+
+        def step(u, p):
+            ap = split_product(Ah, Al, *split_fp16(p), mode)
+            g = to_bf16(y - ap - lam32 * (u - p))
+            P = k_step_products(Mb, g)
+            du = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
+            return (u + du).astype(np.float32)
+    else:
+        raise ValueError(form)
+    return _iterate(step, y, thr, tol, max_iter)

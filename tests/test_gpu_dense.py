@@ -7,7 +7,9 @@ errors sit at 1-3e-6 (l2 cases at the top: their minimiser solves
 (A + mu I) v = y).  phi is stationary in v at the minimiser, so its error is
 second order and FP64 accumulation keeps it below 1e-6 relative.  Bars:
 phi <= 1e-6 relative (floor 1) for every query; gradient <= 6e-6 relative
-(floor 1) for every query and <= 3e-6 at the median.
+(floor 1) for every query and <= 3e-6 at the median.  tests/accuracy_model.py
+models the tensor-core forms' arithmetic (FP16 / BF16 operands, FP32
+accumulators) and checks these bars against the oracle on the CPU.
 """
 import numpy as np
 import pytest
