@@ -22,6 +22,9 @@ MIXED:  g^k = y - A p^k - lam (u^k - p^k) with A p^k split (g stored in
         BF16), u^{k+1} = u^k + bf16(M) g^k; the fixed point g = 0 does not
         depend on the rounding of M.
 Both stop at the first k >= 2 with |u^k - u^{k-1}|^2 <= tol max(1, |u^k|^2).
+Two stages: SPLIT down to a looser tolerance, then MIXED from each query's
+last u (a stop allowed from its first step), as the library's default MIXED
+solve for l1 and weighted l1 does.
 
 This is a model of the hardware's arithmetic, not of the kernels' code:
 the parity tests on the GPU measure the kernels themselves.  Only ``tests/``
@@ -80,30 +83,51 @@ def split_product(Xh, Xl, Yh, Yl, mode):
     return d1 + d2 / LO_SCALE
 
 
-def _iterate(step, y, thr, tol, max_iter):
-    """Run ``step(u, p) -> u_next`` per query until the relative rule stops it."""
+def _prox(u, thr):
+    return (np.sign(u) * np.maximum(np.abs(u) - thr, 0)).astype(np.float32)
+
+
+def _iterate(step, y, thr, tol, max_iter, u0=None, k_min=2):
+    """Run ``step(u, p) -> u_next`` per query until the relative rule stops
+    it (from k >= k_min).  The start is u = p = y (v^0 = d^0 = y, b^0 = 0),
+    or u = u0 with p = prox(u0) for a warm start.  Returns (p, iters, u)."""
     q = y.shape[1]
-    u, p = y.copy(), y.copy()
+    if u0 is None:
+        u, p = y.copy(), y.copy()
+    else:
+        u, p = u0.copy(), _prox(u0, thr)
     iters, done = np.zeros(q, np.int64), np.zeros(q, bool)
     for k in range(1, max_iter + 1):
         un = step(u, p)
         du = (un - u).astype(np.float64)
         ru = (du * du).sum(0) / np.maximum(1.0, (un.astype(np.float64) ** 2).sum(0))
         act = ~done
-        pn = (np.sign(un) * np.maximum(np.abs(un) - thr, 0)).astype(np.float32)
+        pn = _prox(un, thr)
         u[:, act], p[:, act] = un[:, act], pn[:, act]
         iters[act] = k
-        if k >= 2:
+        if k >= k_min:
             done |= ru <= tol
         if done.all():
             break
+    return p, iters, u
+
+
+def solve(form, A, lam, y, thr, tol, mode, max_iter=3000, split_start=None):
+    """Gradients d^K (n x q, FP32) and iteration counts of the weighted-l1
+    problem with J*(v) = 1/2 v^T A v and thresholds thr = (t / lam) w
+    (n x q), for y = x - c given as n x q columns.  form "two_stage": SPLIT
+    iterations down to split_start (default 10 tol), then MIXED ones from
+    each query's last u, stopping from their first step on; the counts add."""
+    if form == "two_stage":
+        s = 10 * tol if split_start is None else split_start
+        _, it1, u1 = _iterate(_step("split", A, lam, y, mode), y, thr, s, max_iter)
+        p, it2, _ = _iterate(_step("mixed", A, lam, y, mode), y, thr, tol, max_iter, u0=u1, k_min=1)
+        return p, it1 + it2
+    p, iters, _ = _iterate(_step(form, A, lam, y, mode), y, thr, tol, max_iter)
     return p, iters
 
 
-def solve(form, A, lam, y, thr, tol, mode, max_iter=3000):
-    """Gradients d^K (n x q, FP32) and iteration counts of the weighted-l1
-    problem with J*(v) = 1/2 v^T A v and thresholds thr = (t / lam) w
-    (n x q), for y = x - c given as n x q columns."""
+def _step(form, A, lam, y, mode):
     n = A.shape[0]
     M = np.linalg.inv(A + lam * np.eye(n)).astype(np.float32)
     lam32 = np.float32(lam)
@@ -126,4 +150,4 @@ def solve(form, A, lam, y, thr, tol, mode, max_iter=3000):
             return (u + du).astype(np.float32)
     else:
         raise ValueError(form)
-    return _iterate(step, y, thr, tol, max_iter)
+    return step

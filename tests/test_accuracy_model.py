@@ -63,3 +63,15 @@ def test_split_bar_and_truncation(problem):
 def test_mixed_truncation_floor(problem):
     rz = _err(problem, "mixed", 1e-15, "rz")
     assert rz[1] > 1e-6, rz
+
+
+def test_two_stage_keeps_mixed_accuracy(problem):
+    """SPLIT down to 10 tol, then MIXED from each query's last u: the defect
+    correction's fixed point does not depend on its start, so the two stages
+    keep MIXED's bars, at about the same total number of iterations."""
+    A, y, thr, ref = problem
+    p2, it2 = am.solve("two_stage", A, 1.0, y, thr, 1e-13, "rz")
+    p1, it1 = am.solve("mixed", A, 1.0, y, thr, 1e-13, "rz")
+    e = np.linalg.norm(p2.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
+    assert e.max() <= 6e-6 and np.median(e) <= 3e-6, e
+    assert abs(it2.mean() - it1.mean()) <= 5 and np.abs(it2 - it1).max() <= 15, (it1, it2)
