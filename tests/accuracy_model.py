@@ -127,6 +127,46 @@ def solve(form, A, lam, y, thr, tol, mode, max_iter=3000, split_start=None):
     return p, iters
 
 
+def two_stage_scheduled(A, lam, y, thr, tol, mode, theta, max_iter=3000):
+    """The two-stage solve with a precision schedule in its SPLIT stage, for
+    one column tile (all columns of y): the tile takes v = M_hi r_hi (one
+    MMA per K step) until the largest squared relative change among its
+    active queries is within theta, the three-term product after; queries
+    stop (at 10 tol) only once the tile is precise.  Returns (p, total
+    iterations per query, the tile's SPLIT iterations, how many of them
+    were one-term)."""
+    n, q = y.shape
+    M = np.linalg.inv(A + lam * np.eye(n)).astype(np.float32)
+    Mh, Ml = split_fp16(M)
+    lam32 = np.float32(lam)
+    u, p = y.copy(), y.copy()
+    it1, done = np.zeros(q, np.int64), np.zeros(q, bool)
+    precise, cheap = False, 0
+    for k in range(1, max_iter + 1):
+        r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)
+        rh, rl = split_fp16(r)
+        if precise:
+            v = split_product(Mh, Ml, rh, rl, mode)
+        else:
+            v = accumulate([k_step_products(Mh, rh)], mode)
+            cheap += 1
+        un = (v + (u - p)).astype(np.float32)
+        du = (un - u).astype(np.float64)
+        ru = (du * du).sum(0) / np.maximum(1.0, (un.astype(np.float64) ** 2).sum(0))
+        act = ~done
+        u[:, act], p[:, act] = un[:, act], _prox(un, thr)[:, act]
+        it1[act] = k
+        if k >= 2:
+            if precise:
+                done |= ru <= 10 * tol
+            else:
+                precise = ru[act].max() <= theta
+        if done.all():
+            break
+    p, it2, _ = _iterate(_step("mixed", A, lam, y, mode), y, thr, tol, max_iter, u0=u, k_min=1)
+    return p, it1 + it2, int(it1.max()), cheap
+
+
 def _step(form, A, lam, y, mode):
     n = A.shape[0]
     M = np.linalg.inv(A + lam * np.eye(n)).astype(np.float32)

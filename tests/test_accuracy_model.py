@@ -75,3 +75,18 @@ def test_two_stage_keeps_mixed_accuracy(problem):
     e = np.linalg.norm(p2.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
     assert e.max() <= 6e-6 and np.median(e) <= 3e-6, e
     assert abs(it2.mean() - it1.mean()) <= 5 and np.abs(it2 - it1).max() <= 15, (it1, it2)
+
+
+def test_split_stage_precision_schedule(problem):
+    """A next-step design, checked in the model before any kernel: on a tile
+    of the 8 queries, a one-term SPLIT product (M_hi r_hi) while the tile's
+    largest squared relative change exceeds 1e-5 takes over a quarter of the
+    tile's SPLIT iterations at under one extra iteration per query and keeps
+    the two-stage solve's gradient bars."""
+    A, y, thr, ref = problem
+    p, it, tile_iters, cheap = am.two_stage_scheduled(A, 1.0, y, thr, 1e-13, "rz", 1e-5)
+    _, it0, _, cheap0 = am.two_stage_scheduled(A, 1.0, y, thr, 1e-13, "rz", np.inf)
+    assert cheap0 <= 2 and cheap >= 0.25 * tile_iters, (cheap0, cheap, tile_iters)
+    assert it.mean() - it0.mean() <= 1.0, (it.mean(), it0.mean())
+    e = np.linalg.norm(p.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
+    assert e.max() <= 6e-6 and np.median(e) <= 3e-6, e
