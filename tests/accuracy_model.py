@@ -15,6 +15,8 @@ d^K with the FP64 oracle's.
   terms of a split product share one accumulator, interleaved per K step,
   and the BF16 product alternates K steps between two accumulators.
 - Elementwise work (prox, b, g, the state) in FP32.
+- The CUDA-core form ("fp32"): v = M r with FP32 M and r, one fused
+  multiply-add per term in order, rounded to nearest.
 
 SPLIT:  v^{k+1} = M r^k with both M and r^k = y + lam (2 p^k - u^k) split;
         u^{k+1} = v^{k+1} + u^k - p^k.
@@ -188,6 +190,20 @@ def _step(form, A, lam, y, mode):
             P = k_step_products(Mb, g)
             du = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
             return (u + du).astype(np.float32)
+    elif form == "fp32":
+        def step(u, p):
+            r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)
+            return (fma_chain(M, r) + (u - p)).astype(np.float32)
     else:
         raise ValueError(form)
     return step
+
+
+def fma_chain(X, Y):
+    """X Y as one FP32 fused multiply-add per term, in order over K (the
+    CUDA-core form's accumulation): each step rounds acc + x y once."""
+    Xd, Yd = X.astype(np.float64), Y.astype(np.float64)
+    acc = np.zeros((X.shape[0], Y.shape[1]), np.float32)
+    for k in range(X.shape[1]):
+        acc = round_f32(acc.astype(np.float64) + Xd[:, k:k + 1] * Yd[k:k + 1, :], "rn")
+    return acc

@@ -90,3 +90,13 @@ def test_split_stage_precision_schedule(problem):
     assert it.mean() - it0.mean() <= 1.0, (it.mean(), it0.mean())
     e = np.linalg.norm(p.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
     assert e.max() <= 6e-6 and np.median(e) <= 3e-6, e
+
+
+def test_fp32_form_at_the_same_accuracy(problem):
+    """The CUDA-core FP32 form (v = M r, FMA chains rounded to nearest) meets
+    the same bars, and MIXED's gradient error is within a factor 1.5 of it:
+    the metric compares the two forms at one tolerance."""
+    fp32 = _err(problem, "fp32", 1e-13, "rn")
+    mixed = _err(problem, "mixed", 1e-13, "rz")
+    assert fp32[0] <= 6e-6 and fp32[1] <= 3e-6, fp32
+    assert 1 / 1.5 <= mixed[0] / fp32[0] <= 1.5, (mixed, fp32)
