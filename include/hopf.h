@@ -156,8 +156,9 @@ typedef struct {
  * as the v-update; in FP32 for HOPF_P_MIXED, where M only preconditions the
  * defect correction (whose fixed point uses A itself), and HOPF_P_BF16, which
  * rounds M to BF16.  Returns HOPF_ENOTSPD when a pivot of A + lambda I is not
- * positive (an FP32 pivot that is not is checked again in FP64).  The handle is immutable afterwards: hopf_eval may run on several
- * streams at once with distinct workspaces.  Synchronises `stream`. */
+ * positive (an FP32 pivot that is not is checked again in FP64).  The handle
+ * is immutable afterwards: hopf_eval may run on several streams at once with
+ * distinct workspaces.  Synchronises `stream`. */
 hopf_status hopf_create(const hopf_desc* desc, hopf_handle* out, cudaStream_t stream);
 
 /* Release the handle and its device memory (NULL is a no-op). */
