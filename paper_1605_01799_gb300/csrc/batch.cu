@@ -14,9 +14,12 @@
 //     instance, forked onto worker streams and joined back.
 // Instances the persistent solver does not take (dense FP32 CUDA-core, the
 // diagonal runtime kinds, diagonal n > 4096) run their own launches beside
-// it.  The autotuner on the first call captures and times the persistent
-// schedule with 1, 2, 4, 8 and 16 lanes and the stream schedule, and keeps
-// the fastest.  Later calls with the same buffers and counts replay it.
+// it.  The autotuner on the first call captures and times candidate graphs
+// (the persistent schedule with 4 to 32 lanes, with some CTAs starting on the
+// diagonal work list, or with every dense instance on lanes; the stream
+// schedule with 8 and 16 lanes, or with 1 to 16 when only streams are
+// allowed) and keeps the fastest.  Later calls with the same buffers and
+// counts replay it.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
