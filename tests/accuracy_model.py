@@ -15,6 +15,8 @@ d^K with the FP64 oracle's.
   terms of a split product share one accumulator, interleaved per K step,
   and the BF16 product alternates K steps between two accumulators.
 - Elementwise work (prox, b, g, the state) in FP32.
+- BF16 ("bf16"): v = bf16(M) bf16(r), the paper's form in one MMA per K
+  step (alternating accumulators).
 - The CUDA-core form ("fp32"): v = M r with FP32 M and r, one fused
   multiply-add per term in order, rounded to nearest.
 
@@ -190,6 +192,14 @@ def _step(form, A, lam, y, mode):
             P = k_step_products(Mb, g)
             du = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
             return (u + du).astype(np.float32)
+    elif form == "bf16":
+        Mb = to_bf16(M)
+
+        def step(u, p):
+            r = to_bf16(y + lam32 * (np.float32(2) * p - u))
+            P = k_step_products(Mb, r)
+            v = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
+            return (v + (u - p)).astype(np.float32)
     elif form == "fp32":
         def step(u, p):
             r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)

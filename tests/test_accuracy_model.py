@@ -100,3 +100,12 @@ def test_fp32_form_at_the_same_accuracy(problem):
     mixed = _err(problem, "mixed", 1e-13, "rz")
     assert fp32[0] <= 6e-6 and fp32[1] <= 3e-6, fp32
     assert 1 / 1.5 <= mixed[0] / fp32[0] <= 1.5, (mixed, fp32)
+
+
+def test_bf16_form_is_a_comparison_row(problem):
+    """The paper's v-update in BF16 alone (one MMA per K step) stops at its
+    own fixed point, ~1e-2 from the FP64 one (BF16's 2^-9 relative rounding
+    of M and r, amplified through A + lam I): the form is kept for
+    comparison, not for the metric's accuracy."""
+    e = _err(problem, "bf16", 1e-6, "rz")
+    assert 1e-3 <= e[1] and e[0] <= 5e-2, e
