@@ -17,6 +17,9 @@ d^K with the FP64 oracle's.
 - Elementwise work (prox, b, g, the state) in FP32.
 - BF16 ("bf16"): v = bf16(M) bf16(r), the paper's form in one MMA per K
   step (alternating accumulators).
+- Forms not built, for comparison: TF32 ("tf32": v = tf32(M) tf32(r), K = 8
+  per MMA) and the BF16 hi/lo split ("bf16x3": x = bf16(x) + bf16(x - hi),
+  three MMAs per K step, ~2^-16).
 - The CUDA-core form ("fp32"): v = M r with FP32 M and r, one fused
   multiply-add per term in order, rounded to nearest.
 
@@ -63,11 +66,19 @@ def split_fp16(x):
     return hi, lo
 
 
-def k_step_products(A, B):
-    """P[k] = A[:, 16k:16k+16] @ B[16k:16k+16, :], exact in FP64."""
-    nk = A.shape[1] // K_STEP
-    Ar = A.astype(np.float64).reshape(A.shape[0], nk, K_STEP).transpose(1, 0, 2)
-    return np.matmul(Ar, B.astype(np.float64).reshape(nk, K_STEP, B.shape[1]))
+def to_tf32(x):
+    """FP32 to TF32 (10 explicit mantissa bits, round to nearest even), as FP32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + (((b >> 13) & 1) + 0xFFF)) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32)
+
+
+def k_step_products(A, B, ks=K_STEP):
+    """P[k] = A[:, ks k:ks (k+1)] @ B[ks k:ks (k+1), :], exact in FP64
+    (ks = 16 for FP16 / BF16 MMAs, 8 for TF32)."""
+    nk = A.shape[1] // ks
+    Ar = A.astype(np.float64).reshape(A.shape[0], nk, ks).transpose(1, 0, 2)
+    return np.matmul(Ar, B.astype(np.float64).reshape(nk, ks, B.shape[1]))
 
 
 def accumulate(products, mode):
@@ -200,6 +211,25 @@ def _step(form, A, lam, y, mode):
             P = k_step_products(Mb, r)
             v = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
             return (v + (u - p)).astype(np.float32)
+    elif form == "tf32":
+        Mt = to_tf32(M)
+
+        def step(u, p):
+            r = to_tf32(y + lam32 * (np.float32(2) * p - u))
+            P = k_step_products(Mt, r, 8)
+            v = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
+            return (v + (u - p)).astype(np.float32)
+    elif form == "bf16x3":
+        Mh = to_bf16(M)
+        Ml = to_bf16(M - Mh)
+
+        def step(u, p):
+            r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)
+            rh = to_bf16(r)
+            rl = to_bf16(r - rh)
+            d1 = accumulate([k_step_products(Mh, rh)], mode)
+            d2 = accumulate([k_step_products(Mh, rl), k_step_products(Ml, rh)], mode)
+            return (d1 + d2 + (u - p)).astype(np.float32)
     elif form == "fp32":
         def step(u, p):
             r = (y + lam32 * (np.float32(2) * p - u)).astype(np.float32)
