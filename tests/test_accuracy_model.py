@@ -39,9 +39,21 @@ def problem(orc):
     return A, y, thr, ref["grad"]
 
 
+_RUNS = {}
+
+
+def _solve(problem, form, tol, mode):
+    """am.solve on the module's queries, each (form, tol, mode) run once."""
+    key = (form, tol, mode)
+    if key not in _RUNS:
+        A, y, thr, _ = problem
+        _RUNS[key] = am.solve(form, A, 1.0, y, thr, tol, mode)
+    return _RUNS[key]
+
+
 def _err(problem, form, tol, mode):
-    A, y, thr, ref = problem
-    p, iters = am.solve(form, A, 1.0, y, thr, tol, mode)
+    ref = problem[3]
+    p, iters = _solve(problem, form, tol, mode)
     assert (iters < 3000).all()
     e = np.linalg.norm(p.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
     return e.max(), np.median(e)
@@ -71,7 +83,7 @@ def test_two_stage_keeps_mixed_accuracy(problem):
     keep MIXED's bars, at about the same total number of iterations."""
     A, y, thr, ref = problem
     p2, it2 = am.solve("two_stage", A, 1.0, y, thr, 1e-13, "rz")
-    p1, it1 = am.solve("mixed", A, 1.0, y, thr, 1e-13, "rz")
+    _, it1 = _solve(problem, "mixed", 1e-13, "rz")
     e = np.linalg.norm(p2.T - ref, axis=1) / np.maximum(1, np.linalg.norm(ref, axis=1))
     assert e.max() <= 6e-6 and np.median(e) <= 3e-6, e
     assert abs(it2.mean() - it1.mean()) <= 5 and np.abs(it2 - it1).max() <= 15, (it1, it2)
