@@ -247,3 +247,25 @@ def fma_chain(X, Y):
     for k in range(X.shape[1]):
         acc = round_f32(acc.astype(np.float64) + Xd[:, k:k + 1] * Yd[k:k + 1, :], "rn")
     return acc
+
+
+def syrk_tile(X, Y, chunk_q, range_q, mode="rz"):
+    """One tile of the backward contraction X^T Y over the queries (X, Y:
+    [B][128] FP32, query-major), as the tensor-core SYRK forms it: two-term
+    FP16 splits, X_hi Y_hi accumulated chunk_q queries at a time and promoted
+    into FP32 registers, X_hi Y_lo' + X_lo' Y_hi in a correction accumulator
+    over each range of range_q queries, the ranges summed in FP64."""
+    B = X.shape[0]
+    Xh, Xl = split_fp16(X)
+    Yh, Yl = split_fp16(Y)
+    total = np.zeros((X.shape[1], Y.shape[1]))
+    for r0 in range(0, B, range_q):
+        r1 = min(B, r0 + range_q)
+        acc = np.zeros((X.shape[1], Y.shape[1]), np.float32)
+        for c0 in range(r0, r1, chunk_q):
+            c1 = min(r1, c0 + chunk_q)
+            acc = (acc + accumulate([k_step_products(Xh[c0:c1].T, Yh[c0:c1])], mode)).astype(np.float32)
+        corr = accumulate([k_step_products(Xh[r0:r1].T, Yl[r0:r1]), k_step_products(Xl[r0:r1].T, Yh[r0:r1])],
+                          mode)
+        total += (acc + corr / LO_SCALE).astype(np.float32).astype(np.float64)
+    return total

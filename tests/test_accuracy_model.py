@@ -134,3 +134,24 @@ def test_unbuilt_tf32_and_bf16x3_forms(problem):
     bf3 = _err(problem, "bf16x3", 1e-11, "rz")
     split = _err(problem, "split", 1e-13, "rz")
     assert bf3[0] >= 1.5 * split[0] and bf3[0] > 2.5e-5, (bf3, split)
+
+
+def test_backward_syrk_promotion():
+    """The tensor-core g_A (n = 2048, 32,768 queries) in the model, on one
+    off-diagonal 128 x 128 tile with shrink-sparse minimisers: promoting the
+    main product every 512 queries and summing 4,096-query ranges in FP64
+    keeps the error an order of magnitude inside the test bar (1e-5 of
+    max |g_A|); one truncating accumulator over all the queries would not."""
+    B, n = 32768, 256
+    z = wl.normal(7001, B * n, 2.0).reshape(B, n)
+    thr = wl.uniform(7002, B, 0.1, 3.0)[:, None]
+    V = (np.sign(z) * np.maximum(np.abs(z) - thr, 0)).astype(np.float32)
+    g = wl.normal(7003, B, 1.0) * 1e-3
+    gs = (g * 2.0 ** np.floor(np.log2(1000.0 / np.abs(g).max()))).astype(np.float32)  # exact power-of-two scale
+    X, Y = (gs[:, None] * V[:, :128]).astype(np.float32), V[:, 128:]
+    exact = X.astype(np.float64).T @ Y.astype(np.float64)
+    m = np.abs(exact).max()
+    promoted = np.abs(am.syrk_tile(X, Y, 512, 4096) - exact).max() / m
+    single = np.abs(am.syrk_tile(X, Y, B, B) - exact).max() / m
+    assert promoted <= 2e-6, promoted
+    assert single >= 2e-5, single
