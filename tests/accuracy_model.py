@@ -33,6 +33,10 @@ Two stages: SPLIT down to a looser tolerance, then MIXED from each query's
 last u (a stop allowed from its first step), as the library's default MIXED
 solve for l1 and weighted l1 does.
 
+The backward contraction g_A = -1/2 V^T diag(g) V (syrk_tile): the same
+splits, the main product promoted to FP32 registers every chunk of queries,
+the ranges of queries summed in FP64.
+
 This is a model of the hardware's arithmetic, not of the kernels' code:
 the parity tests on the GPU measure the kernels themselves.  Only ``tests/``
 uses it.
