@@ -80,6 +80,17 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["cpu_baseline"]["kind"] == "oracle"
     # the same workload name as the GPU arm's line at these sizes
     assert line["config"]["workload"] == "dense_wl1_n64_b65536"
+    # the line's contract: the GPU arm's keys, a cpu_baseline describing this
+    # run and an e2e of the line's own value with no device copies
+    for key in ("metric", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling", "dtype",
+                "data", "vs_baseline"):
+        assert key in line, key
+    assert line["higher_is_better"] is True and line["unit"] == "evals/s"
+    cb = line["cpu_baseline"]
+    assert cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
 def test_generator_offsets_slice_one_stream():
