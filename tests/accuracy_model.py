@@ -273,3 +273,39 @@ def syrk_tile(X, Y, chunk_q, range_q, mode="rz"):
                           mode)
         total += (acc + corr / LO_SCALE).astype(np.float32).astype(np.float64)
     return total
+
+
+def mixed_l2(A, lam, y, tau, tol, mode, max_iter=3000):
+    """The MIXED form with H = l2 (one stage): p = s u with
+    s = max(0, 1 - tau / |u|) (shrink_2), the operand planes hold u and
+    A p = s (A u); the first product takes p = y.  tau: (1, q) FP32."""
+    n, q = y.shape
+    M = np.linalg.inv(A + lam * np.eye(n)).astype(np.float32)
+    Ah, Al = split_fp16(A.astype(np.float32))
+    Mb = to_bf16(M)
+    lam32 = np.float32(lam)
+
+    def prox(u):
+        nrm = np.sqrt((u.astype(np.float64) ** 2).sum(0)).astype(np.float32)
+        s = np.where(nrm > tau[0], 1 - tau[0] / np.maximum(nrm, np.float32(1e-30)), 0).astype(np.float32)
+        return (u * s[None, :]).astype(np.float32), s
+
+    u, p, s = y.copy(), y.copy(), np.ones(q, np.float32)
+    iters, done = np.zeros(q, np.int64), np.zeros(q, bool)
+    for k in range(1, max_iter + 1):
+        au = split_product(Ah, Al, *split_fp16(u if k > 1 else y), mode)
+        ap = au * s[None, :] if k > 1 else au
+        g = to_bf16(y - ap - lam32 * (u - p))
+        P = k_step_products(Mb, g)
+        du = accumulate([P[0::2]], mode) + accumulate([P[1::2]], mode)
+        un = (u + du).astype(np.float32)
+        ru = (du.astype(np.float64) ** 2).sum(0) / np.maximum(1.0, (un.astype(np.float64) ** 2).sum(0))
+        act = ~done
+        pn, sn = prox(un)
+        u[:, act], p[:, act], s[act] = un[:, act], pn[:, act], sn[act]
+        iters[act] = k
+        if k >= 2:
+            done |= ru <= tol
+        if done.all():
+            break
+    return p, iters
